@@ -1,0 +1,149 @@
+"""Pins of the oracle's WQ steps (paper Sec. 4).
+
+* Table 2: the min-max rule gives 2x2 regular, 4x4 boundary, 4x4 irregular and
+  3x3 non-enriched transition points on the valence-5 disk;
+* well-posedness r_i >= n_i for every test function (Sec. 4.2);
+* TSVD weights: planted SVD with known rank; full rank => Eq. w0 / Eq. QR;
+  exactness A w = b; KKT (Z^-2 w in range(V_t)); brute force in rationals;
+* assembly: c = 1 gives the Gauss matrix (the exactness constraints, which is
+  what Sec. 6 measures to ~1e-12), c = k gives k times it, stiffness row sums
+  vanish for any coefficient, and sum_j M_ij = sum_q w_iq c_q.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from wq_synth import meshes
+from oracle.basis import Basis
+from oracle.topology import TYPE_NAMES
+from oracle import wq, gq
+
+HERE = os.path.dirname(__file__)
+
+
+@pytest.fixture(scope="module")
+def disk_rule():
+    B = Basis(meshes.disk(mu=5, n=6))
+    R = wq.Rule(B, ["N", "x", "y", "lap"])
+    R.compute_weights()
+    return R
+
+
+def test_table2_counts_on_disk(disk_rule):
+    R = disk_rule
+    tab = {}
+    for line in open(os.path.join(HERE, "golden", "table2_points.txt")):
+        if line[0] == "#" or not line.strip():
+            continue
+        t, s, _ = line.split()
+        tab[t] = {int(v) for v in s.split("/")}
+    seen = {}
+    for e in range(R.basis.E):
+        seen.setdefault(TYPE_NAMES[R.basis.etype[e]], set()).add(int(R.side[e]))
+    assert seen["regular"] == {2} and seen["boundary"] == {4} and seen["irregular"] == {4}
+    assert seen["transition"] == {3}
+    for t, s in seen.items():
+        assert s <= tab[t]
+
+
+@pytest.mark.parametrize("make", [lambda: meshes.disk(mu=5, n=6), lambda: meshes.disk(mu=7, n=5, levels=1),
+                                  lambda: meshes.rotated(levels=1), lambda: meshes.disk(mu=3, n=5, levels=2)])
+def test_well_posed(make):
+    B = Basis(make())
+    rp, _ = gq.pattern(B)
+    side = wq.point_counts(B, rp)
+    for i in range(B.n):
+        assert sum(int(side[k]) ** 2 for k in B.supp[i]) >= rp[i + 1] - rp[i]
+
+
+def test_tsvd_planted():
+    rng = np.random.Generator(np.random.PCG64(1))
+    n, r = 7, 12
+    U, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    V, _ = np.linalg.qr(rng.normal(size=(r, r)))
+    sig = np.array([3.0, 1.0, 0.1, 1e-3, 1e-6, 1e-15, 1e-17])
+    A = U @ np.diag(sig) @ V[:, :n].T
+    z = rng.uniform(0.2, 1.0, size=r)
+    b = U[:, :5] @ rng.normal(size=5)         # in range of the kept part
+    w, t = wq.tsvd_weights(A, z, b)
+    assert t == 5
+    Vt = V[:, :5]
+    Z2 = np.diag(z ** 2)
+    ref = Z2 @ Vt @ np.linalg.inv(Vt.T @ Z2 @ Vt) @ np.diag(1 / sig[:5]) @ U[:, :5].T @ b
+    assert np.max(np.abs(w - ref)) < 1e-9 * np.max(np.abs(ref))
+    # kept condition number s_1/s_5 = 3e6: residual bound ~ 3e6 * eps
+    assert np.max(np.abs(A @ w - b)) < 1e-10 * np.max(np.abs(b))
+
+
+def test_tsvd_full_rank_equals_w0_and_qr():
+    rng = np.random.Generator(np.random.PCG64(2))
+    A = rng.normal(size=(6, 10))
+    z = rng.uniform(0.3, 1.0, size=10)
+    b = rng.normal(size=6)
+    w, t = wq.tsvd_weights(A, z, b)
+    assert t == 6
+    Z2 = np.diag(z ** 2)
+    w0 = Z2 @ A.T @ np.linalg.solve(A @ Z2 @ A.T, b)                   # Eq. w0
+    Q, R = np.linalg.qr((A * z).T)
+    wqr = z * (Q @ np.linalg.solve(R.T, b))                            # Eq. QR (Z read for Z^-1)
+    assert np.max(np.abs(w - w0)) < 1e-12 * np.max(np.abs(w0))
+    assert np.max(np.abs(w - wqr)) < 1e-12 * np.max(np.abs(w0))
+
+
+def test_tsvd_brute_force_rationals():
+    """Tiny full-rank case: KKT system of min |Z^-1 w|^2 s.t. A w = b solved exactly."""
+    A = [[1, 2, 0, 1], [0, 1, 3, 1]]
+    z = [1, Fraction(1, 2), 2, 1]
+    b = [1, 2]
+    n, r = 2, 4
+    # KKT: Z^-2 w = A^T lam, A w = b  ->  (A Z^2 A^T) lam = b
+    M = [[sum(Fraction(A[i][q]) * z[q] ** 2 * A[j][q] for q in range(r)) for j in range(n)] for i in range(n)]
+    det = M[0][0] * M[1][1] - M[0][1] * M[1][0]
+    lam = [(M[1][1] * b[0] - M[0][1] * b[1]) / det, (M[0][0] * b[1] - M[1][0] * b[0]) / det]
+    wex = [z[q] ** 2 * sum(A[i][q] * lam[i] for i in range(n)) for q in range(r)]
+    w, t = wq.tsvd_weights(np.array(A, float), np.array([float(x) for x in z]), np.array(b, float))
+    assert t == 2
+    assert np.max(np.abs(w - np.array([float(x) for x in wex]))) < 1e-14
+
+
+def test_exactness_and_kkt(disk_rule):
+    R = disk_rule
+    for c in R.comps:
+        for i in range(0, R.basis.n, 7):
+            A, z = R.local_system(i, c)
+            b = R.moments[c][R.row_ptr[i]:R.row_ptr[i + 1]]
+            w = R.weights[c][R.w_ptr[i]:R.w_ptr[i + 1]]
+            assert np.max(np.abs(A @ w - b)) <= 1e-12 * np.max(np.abs(b)) + 1e-18
+            if np.all(z != 0):
+                _, S, Vt = np.linalg.svd(A, full_matrices=False)
+                t = R.rank[c][i]
+                y = w / z ** 2
+                resid = y - Vt[:t].T @ (Vt[:t] @ y)
+                assert np.max(np.abs(resid)) < 1e-8 * np.max(np.abs(y))
+
+
+def test_assembly_constant_coefficient_is_gauss(disk_rule):
+    R = disk_rule
+    ones = np.ones(R.Q)
+    for c in R.comps:
+        G = R.moments[c]
+        A1 = R.assemble([(c, ones)])
+        assert np.max(np.abs(A1 - G)) <= 1e-12 * np.max(np.abs(G))
+        A3 = R.assemble([(c, 3.0 * ones)])
+        assert np.max(np.abs(A3 - 3 * G)) <= 1e-12 * np.max(np.abs(G))
+
+
+def test_assembly_rowsums_and_mass_sums(disk_rule):
+    R = disk_rule
+    kap = meshes.kappa_sines(R.x)
+    K = R.assemble([("x", kap), ("y", kap)])
+    rs = np.add.reduceat(K, R.row_ptr[:-1])
+    assert np.max(np.abs(rs)) < 1e-12 * np.max(np.abs(K))
+    Mw = R.assemble([("N", kap)])
+    for i in range(0, R.basis.n, 5):
+        q = R.row_points(i)
+        lhs = Mw[R.row_ptr[i]:R.row_ptr[i + 1]].sum()
+        rhs = R.weights["N"][R.w_ptr[i]:R.w_ptr[i + 1]] @ kap[q]
+        assert abs(lhs - rhs) < 1e-14
