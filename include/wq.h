@@ -1,0 +1,217 @@
+/*
+ * wq.h -- C ABI of the GB300 weighted-quadrature (WQ) library.
+ *
+ * Weighted quadrature on bicubic unstructured splines (Sheng, Wei, Chen,
+ * "Weighted Quadrature on Unstructured Splines"): per test function N_i a
+ * quadrature rule with points in the physical domain and weights fitted to the
+ * Gauss-integrated moments by a truncated SVD (Sec. 4), then row-wise assembly
+ *      A_ij = sum_q sum_c w^c_iq coef^c(x_q) D_c N_j(x_q)          (Eqs. 9, 11, 12)
+ * into CSR.  Everything after wq_build_basis runs in hand-written CUDA kernels
+ * for sm_103a on one GPU.
+ *
+ * Conventions
+ *   - Every call returns wq_status; WQ_OK == 0.  On failure a message is
+ *     available from wq_last_error(ctx) (valid until the next call on ctx).
+ *     The library never traps or aborts; device-side problems (a Jacobi sweep
+ *     cap, a non-finite value) come back as status codes.
+ *   - Pointers named h_* are host memory, d_* device memory of the context's
+ *     device.  The library copies host inputs; it never keeps or frees caller
+ *     pointers.  Device views returned by the library (d_x, d_row_ptr, ...)
+ *     stay valid until the owning handle is destroyed.
+ *   - Indices are 0-based; CSR columns are sorted; the pattern of row i is the
+ *     exactness set S_i (Eq. 10), numerically zero entries are kept.
+ *   - Streams are passed as void* (a cudaStream_t; NULL = legacy default stream).
+ *   - Handles are not thread-safe; use one context per host thread.
+ */
+#ifndef WQ_H
+#define WQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WQ_OK = 0,
+    WQ_ERR_ARG = 1,            /* bad pointer, size or option */
+    WQ_ERR_MESH = 2,           /* non-quad / non-manifold mesh, EP in the boundary 1-ring, folded map */
+    WQ_ERR_ILLPOSED = 3,       /* r_i < n_i after the min-max repair (Sec. 4.2) */
+    WQ_ERR_NOT_CONVERGED = 4,  /* a Jacobi SVD hit its sweep cap (Sec. 4.3 solve) */
+    WQ_ERR_NONFINITE = 5,      /* NaN/Inf met on the device */
+    WQ_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+    WQ_ERR_OOM = 7,            /* device allocation failed */
+    WQ_ERR_NO_DEVICE = 8       /* the context was created without a device */
+} wq_status;
+
+/* Operators (Eqs. 9, 11, 12 and the symmetric heat tangent, Eq. S). */
+typedef enum {
+    WQ_OP_MASS = 0,    /* sum_q w_iq c_q N_j(x_q)                                     */
+    WQ_OP_STIFF = 1,   /* sum_q c_q sum_d w^d_iq d_d N_j(x_q), d over x,y (,z)         */
+    WQ_OP_BIHARM = 2,  /* sum_q w^lap_iq c_q lap N_j(x_q)                              */
+    WQ_OP_HEAT_S = 3   /* alpha * MASS(c = 1) + STIFF(c), alpha = 1/(theta dt)           */
+} wq_op;
+
+/* Weight / table components. */
+typedef enum { WQ_COMP_N = 0, WQ_COMP_X = 1, WQ_COMP_Y = 2, WQ_COMP_Z = 3, WQ_COMP_LAP = 4 } wq_comp;
+
+/* Precision of the assembly contraction. */
+typedef enum {
+    WQ_PREC_F64 = 0,   /* FP64 weights, tables and accumulation; CSR values double */
+    WQ_PREC_F32 = 1    /* FP32 split (hi/lo) products, FP32 accumulation; CSR values float */
+} wq_prec;
+
+/* Point-count rule (Sec. 4.2). */
+typedef enum { WQ_COUNT_MINMAX = 0 } wq_count_mode;
+
+typedef struct wq_ctx wq_ctx;
+typedef struct wq_basis wq_basis;
+typedef struct wq_rule wq_rule;
+
+/* Control mesh (host arrays, copied by wq_build_basis).
+ *   dim          2 = planar domain (z ignored), 3 = surface in R^3
+ *   xyz          [n_vertices][3] control points of the vertex-based functions
+ *   quads        [n_faces][4] vertex ids, counter-clockwise
+ *   level0_face  [n_faces] index of the initial-mesh face each face descends
+ *                from (-1: none), or NULL when the mesh is itself the initial
+ *                mesh.  Enriched elements = descendants of initial irregular
+ *                faces (Sec. 3 terminology). */
+typedef struct {
+    int32_t dim;
+    int64_t n_vertices;
+    const double* xyz;
+    int64_t n_faces;
+    const int32_t* quads;
+    const int32_t* level0_face;
+} wq_mesh_desc;
+
+typedef struct {
+    int64_t n_functions;      /* n: spline functions with support on active elements */
+    int64_t n_elements;       /* E: active (non-passive) elements */
+    int64_t n_irregular;      /* split 2x2 elements */
+    int64_t nnz;              /* sum_i n_i = #S_i summed (Eq. 10) */
+    int32_t max_m;            /* max functions on one element */
+    int32_t max_n_i;          /* max #S_i */
+    int64_t type_count[7];    /* passive, boundary, irregular, enriched transition,
+                                 transition, enriched regular, regular (faces) */
+} wq_basis_info;
+
+typedef struct {
+    uint32_t comps;           /* bit mask of (1 << wq_comp) weight sets to build */
+    int32_t count_mode;       /* wq_count_mode */
+    double tsvd_rel_tol;      /* keep sigma_k >= tol * sigma_max (paper: tiny sigma dropped); 1e-12 */
+    int32_t max_sweeps;       /* Jacobi sweep cap (default 40 when 0) */
+    void* stream;             /* stream for the build (NULL: legacy default) */
+} wq_rule_opts;
+
+typedef struct {
+    int64_t n_points;         /* Q: WQ points (Sec. 4.1 placement) */
+    int64_t n_gauss;          /* Gauss points (4x4 per element, 4x4x4 per irregular element) */
+    int64_t sum_r;            /* sum_i r_i (weights per component) */
+    int32_t max_r;            /* max r_i */
+    int32_t n_truncated[5];   /* per component: systems with t < n_i (rank-deficient) */
+    int32_t n_z_identity[5];  /* per component: systems that used Z = I (N_i vanishes on a sub-element) */
+    double setup_ms;          /* device time of the rule build */
+} wq_rule_info;
+
+/* --- context ------------------------------------------------------------ */
+
+/* device >= 0: bind the context to that CUDA device.  device = -1: host-only
+ * context (basis construction and host queries; rule builds return
+ * WQ_ERR_NO_DEVICE).  *out receives the handle. */
+wq_status wq_create(int device, wq_ctx** out);
+void wq_destroy(wq_ctx* ctx);
+const char* wq_last_error(const wq_ctx* ctx);
+
+/* --- spline space (host, Sec. 3) ------------------------------------------ */
+
+/* Classify the mesh (Sec. 3 terminology and assumptions), build the bicubic
+ * unstructured spline space element by element (Bezier extraction with
+ * face-based enrichment, truncation, 2x2 split and D-patch treatment at EPs,
+ * Sec. 3 / Fig. 2) and the exactness-set pattern (Eq. 10).  Host only.
+ * Errors: WQ_ERR_ARG (null/size), WQ_ERR_MESH (assumptions violated). */
+wq_status wq_build_basis(wq_ctx* ctx, const wq_mesh_desc* mesh, wq_basis** out);
+void wq_basis_destroy(wq_basis* basis);
+wq_status wq_basis_info_get(const wq_basis* basis, wq_basis_info* info);
+
+/* Element e (0 <= e < E) as host arrays: its face id, type (wq_basis_info order),
+ * m (functions), nsub (1 or 4); fns [m] function ids ascending; coef
+ * [m][nsub][4][4] Bernstein coefficients (index i along corner0->corner1,
+ * j along corner0->corner3; sub-element s = su + 2 sv).  Pass NULL for arrays
+ * not wanted; call once with NULL arrays to learn m and nsub. */
+wq_status wq_basis_element(const wq_basis* basis, int64_t e, int32_t* face, int32_t* type,
+                           int32_t* m, int32_t* nsub, int32_t* h_fns, double* h_coef);
+
+/* Host copies: control points [n][3]; pattern row_ptr [n+1], col [nnz]. */
+wq_status wq_basis_ctrl(const wq_basis* basis, double* h_xyz);
+wq_status wq_basis_pattern(const wq_basis* basis, int64_t* h_row_ptr, int32_t* h_col);
+
+/* Min-max point counts (Sec. 4.2, Eq. qp_allocation): side s_e of the s x s
+ * grid of every element, h_side [E].  Host only. */
+wq_status wq_point_counts(const wq_basis* basis, int32_t count_mode, int32_t* h_side);
+
+/* --- quadrature rule (device, Sec. 4) ---------------------------------------- */
+
+/* Place the points (Sec. 4.1), evaluate the functions and their physical /
+ * surface derivatives at WQ and Gauss points (Eqs. 13-17), build the Gauss
+ * moments (Sec. 2: b precomputed) and solve every truncated-SVD weight system
+ * (Sec. 4.3) on the device.  The basis must outlive the rule.
+ * Errors: WQ_ERR_NO_DEVICE, WQ_ERR_OOM, WQ_ERR_CUDA, WQ_ERR_ILLPOSED,
+ * WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE. */
+wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out);
+void wq_rule_destroy(wq_rule* rule);
+wq_status wq_rule_info_get(const wq_rule* rule, wq_rule_info* info);
+
+/* Device views: WQ point coordinates [Q][3] (caller evaluates c(x_q) there),
+ * Gauss point coordinates [G][3]. */
+wq_status wq_rule_points(const wq_rule* rule, const double** d_x, int64_t* n_points);
+wq_status wq_rule_gauss_points(const wq_rule* rule, const double** d_x, int64_t* n_gauss);
+
+/* Device view of the CSR pattern (int32 row_ptr [n+1], col [nnz]). */
+wq_status wq_pattern(const wq_rule* rule, int64_t* n, int64_t* nnz,
+                     const int32_t** d_row_ptr, const int32_t** d_col);
+
+/* Device view of the weights of component comp: w [sum_r], with row i's
+ * weights at [w_ptr[i], w_ptr[i+1]) ordered by support element (ascending) then
+ * by point (u fastest); w_ptr int64 [n+1]. */
+wq_status wq_rule_weights(const wq_rule* rule, int32_t comp, const double** d_w, const int64_t** d_w_ptr);
+
+/* Device view of the point tables (Sec. 4.1 evaluation): gauss = 0 for the WQ
+ * points, 1 for the Gauss points.  Element e's block starts at table +
+ * off[e] and is laid out [point][comp][m_e] with comp = N, d_x, d_y, (d_z),
+ * lap (ncomp = dim + 2); points of e are [pt_ptr[e], pt_ptr[e+1]); Gauss
+ * weights (w_g times the area element) d_gw [G] (gauss = 1 only). */
+wq_status wq_rule_table(const wq_rule* rule, int32_t gauss, const double** d_table, const int64_t** d_off,
+                        const int64_t** d_pt_ptr, const double** d_gw, int32_t* ncomp);
+
+/* Device copy of the Gauss component matrix G^c (c = 1), the moments b of
+ * component comp (Sec. 2, "entries of b are precomputed"), into d_vals [nnz]. */
+wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* stream);
+
+/* WQ row-wise assembly (Eqs. 9, 11, 12, S):
+ *   d_coef  [Q] coefficient c(x_q) at the WQ points (device)
+ *   alpha   scalar of WQ_OP_HEAT_S (ignored otherwise)
+ *   prec    wq_prec; d_vals [nnz] double (F64) or float (F32), caller-owned.
+ * No allocation, no host synchronisation; asynchronous on stream.
+ * Errors: WQ_ERR_ARG (op not built into this rule, bad precision). */
+wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha,
+                      int32_t prec, void* d_vals, void* stream);
+
+/* Same operator by element-wise 4x4 Gauss quadrature (the paper's reference,
+ * Table 2 right column), coefficient at the Gauss points d_coef [G]. */
+wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha,
+                         int32_t prec, void* d_vals, void* stream);
+
+/* u_h and grad u_h at the WQ points (Sec. 5): d_u [n] -> d_uq [Q], d_grad [Q][3]. */
+wq_status wq_interp(const wq_rule* rule, const double* d_u, double* d_uq, double* d_grad, void* stream);
+
+/* Host-buffer round trip for end-to-end use: copies h_coef [Q] to the device,
+ * assembles, copies the CSR values back to h_vals [nnz] (double or float by
+ * prec), synchronising on stream.  Uses library-owned staging buffers. */
+wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
+                           int32_t prec, void* h_vals, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WQ_H */

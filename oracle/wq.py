@@ -144,7 +144,7 @@ class Rule:
         return np.concatenate(blocks, axis=1), np.concatenate(zs)
 
     # ---------------------------------------------------- 4-5. moments, TSVD
-    def compute_weights(self, gdata=None):
+    def compute_weights(self, gdata=None, driver="gesdd"):
         self.moments = {c: gq_assemble(self.basis, [c], row_ptr=self.row_ptr, col=self.col, gdata=gdata)
                         for c in self.comps}
         self.w_ptr = np.zeros(self.basis.n + 1, dtype=np.int64)
@@ -155,7 +155,7 @@ class Rule:
             for i in range(self.basis.n):
                 A, z = self.local_system(i, c)
                 b = self.moments[c][self.row_ptr[i]:self.row_ptr[i + 1]]
-                w, t = tsvd_weights(A, z, b, self.tol)
+                w, t = tsvd_weights(A, z, b, self.tol, driver)
                 self.weights[c][self.w_ptr[i]:self.w_ptr[i + 1]] = w
                 self.rank[c][i] = t
         return self.weights
@@ -209,13 +209,21 @@ class Rule:
         return R
 
 
-def tsvd_weights(A, z, b, tol=TSVD_TOL):
+def tsvd_weights(A, z, b, tol=TSVD_TOL, driver="gesdd"):
     """Truncated-SVD weights (Sec. 4.3) -> (w, t).
+
+    driver: LAPACK SVD routine (gesdd, numpy's default, or gesvd via scipy);
+    the two give the same weights up to the conditioning of the system, which
+    is how the tests measure the reproducibility floor of FP64 weights.
 
     Reading for a test function that vanishes identically on the sub-element of
     some of its points (z_q == 0 exactly, so V_t^T Z^2 V_t is singular): that
     row uses Z = I, i.e. the plain minimum-norm truncated solution."""
-    U, S, Vt = np.linalg.svd(A, full_matrices=False)
+    if driver == "gesdd":
+        U, S, Vt = np.linalg.svd(A, full_matrices=False)
+    else:
+        import scipy.linalg
+        U, S, Vt = scipy.linalg.svd(A, full_matrices=False, lapack_driver=driver)
     if S.size == 0 or S[0] == 0.0:
         return np.zeros(A.shape[1]), 0
     if np.any(z == 0.0):

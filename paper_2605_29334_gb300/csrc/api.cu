@@ -1,0 +1,641 @@
+// C ABI of the WQ library (include/wq.h): handles, the device rule build
+// (placement, basis tables, Gauss moments, truncated-SVD weights) and the
+// assembly entry points.  Host set-up lives in host.cpp, kernels in k_*.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "wq_internal.h"
+
+struct wq_ctx {
+    int device = -1;
+    std::string err;
+};
+
+struct wq_basis {
+    wq_ctx* ctx = nullptr;
+    wqi::BasisHost B;
+};
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct wq_rule {
+    wq_ctx* ctx = nullptr;
+    const wq_basis* basis = nullptr;
+    int dim = 2, nc = 4;
+    uint32_t comps = 0;
+    int nwc = 0;
+    int wcidx[5] = {-1, -1, -1, -1, -1};
+    int64_t n = 0, E = 0, Q = 0, G = 0, nnz = 0, sum_r = 0, nsupp = 0;
+    int max_n_i = 0, max_r = 0;
+    std::vector<DevBuf> bufs;
+    // device arrays
+    int32_t *d_m = nullptr, *d_nsub = nullptr, *d_side = nullptr, *d_pt_elem = nullptr, *d_gp_elem = nullptr;
+    int64_t *d_coef_ptr = nullptr, *d_sub_ptr = nullptr, *d_pt_ptr = nullptr, *d_gp_ptr = nullptr;
+    int64_t *d_bt_ptr = nullptr, *d_gbt_ptr = nullptr, *d_fn_ptr = nullptr;
+    double *d_coef = nullptr, *d_geom = nullptr, *d_table = nullptr, *d_gtable = nullptr;
+    double *d_x = nullptr, *d_gx = nullptr, *d_gw = nullptr;
+    int32_t *d_row_ptr = nullptr, *d_col = nullptr, *d_supp = nullptr, *d_fns = nullptr;
+    int64_t *d_supp_ptr = nullptr, *d_pos_ptr = nullptr, *d_w_ptr = nullptr;
+    int32_t* d_order = nullptr;
+    uint16_t* d_pos = nullptr;
+    uint8_t* d_il = nullptr;
+    double* d_W = nullptr;                 // [sum_r][nwc]
+    double* d_mom[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float2 *d_table2 = nullptr, *d_W2 = nullptr;
+    unsigned* d_status = nullptr;
+    // staging for wq_assemble_host
+    double* d_coef_stage = nullptr;
+    double* d_vals_stage = nullptr;
+    wqd::Elems el{};
+    wqd::Rows rw{};
+    wq_rule_info info{};
+
+    ~wq_rule() {
+        for (auto& b : bufs)
+            if (b.p) cudaFree(b.p);
+    }
+};
+
+namespace {
+
+wq_status fail(wq_ctx* ctx, wq_status code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+template <class T>
+bool dalloc(wq_rule* R, T*& p, size_t count, wq_status& st) {
+    void* q = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(R->ctx, WQ_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
+                                          cudaGetErrorString(e));
+        return false;
+    }
+    R->bufs.push_back({q, bytes});
+    p = static_cast<T*>(q);
+    return true;
+}
+
+template <class T>
+bool upload(wq_rule* R, T*& p, const std::vector<T>& v, wq_status& st) {
+    if (!dalloc(R, p, v.size(), st)) return false;
+    if (v.empty()) return true;
+    cudaError_t e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        st = fail(R->ctx, WQ_ERR_CUDA, std::string("upload failed: ") + cudaGetErrorString(e));
+        return false;
+    }
+    return true;
+}
+
+#define CUDA_TRY(ctx, call)                                                                        \
+    do {                                                                                           \
+        cudaError_t _e = (call);                                                                   \
+        if (_e != cudaSuccess)                                                                     \
+            return fail(ctx, WQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e));    \
+    } while (0)
+
+wq_status status_to_error(wq_ctx* ctx, unsigned s) {
+    if (s & wqd::ST_BAD_INDEX) return fail(ctx, WQ_ERR_CUDA, "device index check failed");
+    if (s & wqd::ST_GEOMETRY) return fail(ctx, WQ_ERR_MESH, "folded or degenerate geometry map at a quadrature point");
+    if (s & wqd::ST_NOT_CONVERGED) return fail(ctx, WQ_ERR_NOT_CONVERGED, "Jacobi SVD reached its sweep cap");
+    if (s & wqd::ST_NONFINITE) return fail(ctx, WQ_ERR_NONFINITE, "non-finite value in the weight solve");
+    if (s & wqd::ST_ILLPOSED) return fail(ctx, WQ_ERR_ILLPOSED, "ill-posed weight system");
+    return WQ_OK;
+}
+
+int table_comp(const wq_rule* R, int comp) {
+    switch (comp) {
+        case WQ_COMP_N: return 0;
+        case WQ_COMP_X: return 1;
+        case WQ_COMP_Y: return 2;
+        case WQ_COMP_Z: return R->dim == 3 ? 3 : -1;
+        case WQ_COMP_LAP: return R->nc - 1;
+        default: return -1;
+    }
+}
+
+// Terms of an operator; returns false if a needed weight set is missing.
+bool op_terms(const wq_rule* R, int op, double alpha, bool need_weights, wqd::Terms& tm) {
+    tm.nt = 0;
+    auto add = [&](int comp, int use_coef, double scale) -> bool {
+        int tc = table_comp(R, comp);
+        if (tc < 0) return false;
+        int wc = R->wcidx[comp];
+        if (need_weights && wc < 0) return false;
+        tm.t[tm.nt++] = {wc < 0 ? 0 : wc, tc, use_coef, scale};
+        return true;
+    };
+    switch (op) {
+        case WQ_OP_MASS: return add(WQ_COMP_N, 1, 1.0);
+        case WQ_OP_STIFF:
+            if (!add(WQ_COMP_X, 1, 1.0) || !add(WQ_COMP_Y, 1, 1.0)) return false;
+            return R->dim == 3 ? add(WQ_COMP_Z, 1, 1.0) : true;
+        case WQ_OP_BIHARM: return add(WQ_COMP_LAP, 1, 1.0);
+        case WQ_OP_HEAT_S:
+            if (!add(WQ_COMP_N, 0, alpha) || !add(WQ_COMP_X, 1, 1.0) || !add(WQ_COMP_Y, 1, 1.0)) return false;
+            return R->dim == 3 ? add(WQ_COMP_Z, 1, 1.0) : true;
+        default: return false;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+wq_status wq_create(int device, wq_ctx** out) {
+    if (!out) return WQ_ERR_ARG;
+    *out = nullptr;
+    wq_ctx* c = new (std::nothrow) wq_ctx();
+    if (!c) return WQ_ERR_OOM;
+    if (device >= 0) {
+        int nd = 0;
+        cudaError_t e = cudaGetDeviceCount(&nd);
+        if (e != cudaSuccess || device >= nd) {
+            cudaGetLastError();
+            delete c;
+            return WQ_ERR_NO_DEVICE;
+        }
+        e = cudaSetDevice(device);
+        if (e != cudaSuccess) {
+            delete c;
+            return WQ_ERR_CUDA;
+        }
+    }
+    c->device = device;
+    *out = c;
+    return WQ_OK;
+}
+
+void wq_destroy(wq_ctx* ctx) { delete ctx; }
+
+const char* wq_last_error(const wq_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+wq_status wq_build_basis(wq_ctx* ctx, const wq_mesh_desc* mesh, wq_basis** out) {
+    if (!ctx || !mesh || !out) return fail(ctx, WQ_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (mesh->dim != 2 && mesh->dim != 3) return fail(ctx, WQ_ERR_ARG, "dim must be 2 or 3");
+    if (mesh->n_vertices <= 0 || mesh->n_faces <= 0 || !mesh->xyz || !mesh->quads)
+        return fail(ctx, WQ_ERR_ARG, "empty mesh");
+    if (mesh->n_vertices > INT32_MAX || mesh->n_faces > INT32_MAX / 4)
+        return fail(ctx, WQ_ERR_ARG, "mesh too large for 32-bit indices");
+    wq_basis* b = new (std::nothrow) wq_basis();
+    if (!b) return fail(ctx, WQ_ERR_OOM, "host allocation failed");
+    b->ctx = ctx;
+    wqi::Error err{WQ_OK, ""};
+    bool ok = false;
+    try {
+        ok = wqi::build_basis(*mesh, b->B, err);
+    } catch (const std::bad_alloc&) {
+        err = {WQ_ERR_OOM, "host allocation failed"};
+    }
+    if (!ok) {
+        delete b;
+        return fail(ctx, err.code, err.msg);
+    }
+    if (b->B.E == 0) {
+        delete b;
+        return fail(ctx, WQ_ERR_MESH, "mesh has no active element");
+    }
+    *out = b;
+    return WQ_OK;
+}
+
+void wq_basis_destroy(wq_basis* basis) { delete basis; }
+
+wq_status wq_basis_info_get(const wq_basis* basis, wq_basis_info* info) {
+    if (!basis || !info) return WQ_ERR_ARG;
+    const wqi::BasisHost& B = basis->B;
+    info->n_functions = B.n;
+    info->n_elements = B.E;
+    info->n_irregular = B.n_irregular;
+    info->nnz = B.row_ptr.empty() ? 0 : B.row_ptr[B.n];
+    info->max_m = B.max_m;
+    info->max_n_i = B.max_n_i;
+    for (int k = 0; k < 7; ++k) info->type_count[k] = B.type_count[k];
+    return WQ_OK;
+}
+
+wq_status wq_basis_element(const wq_basis* basis, int64_t e, int32_t* face, int32_t* type, int32_t* m,
+                           int32_t* nsub, int32_t* h_fns, double* h_coef) {
+    if (!basis) return WQ_ERR_ARG;
+    const wqi::BasisHost& B = basis->B;
+    if (e < 0 || e >= B.E) return fail(basis->ctx, WQ_ERR_ARG, "element index out of range");
+    if (face) *face = B.elem_face[e];
+    if (type) *type = B.etype[e];
+    if (m) *m = B.m(e);
+    if (nsub) *nsub = B.nsub[e];
+    if (h_fns) std::copy(B.fns.begin() + B.fn_ptr[e], B.fns.begin() + B.fn_ptr[e + 1], h_fns);
+    if (h_coef) std::copy(B.coef.begin() + B.coef_ptr[e], B.coef.begin() + B.coef_ptr[e + 1], h_coef);
+    return WQ_OK;
+}
+
+wq_status wq_basis_ctrl(const wq_basis* basis, double* h_xyz) {
+    if (!basis || !h_xyz) return WQ_ERR_ARG;
+    std::copy(basis->B.ctrl.begin(), basis->B.ctrl.end(), h_xyz);
+    return WQ_OK;
+}
+
+wq_status wq_basis_pattern(const wq_basis* basis, int64_t* h_row_ptr, int32_t* h_col) {
+    if (!basis) return WQ_ERR_ARG;
+    if (h_row_ptr) std::copy(basis->B.row_ptr.begin(), basis->B.row_ptr.end(), h_row_ptr);
+    if (h_col) std::copy(basis->B.col.begin(), basis->B.col.end(), h_col);
+    return WQ_OK;
+}
+
+wq_status wq_point_counts(const wq_basis* basis, int32_t count_mode, int32_t* h_side) {
+    if (!basis || !h_side) return WQ_ERR_ARG;
+    std::vector<int32_t> side;
+    wqi::Error err{WQ_OK, ""};
+    if (!wqi::point_counts(basis->B, count_mode, side, err)) return fail(basis->ctx, err.code, err.msg);
+    std::copy(side.begin(), side.end(), h_side);
+    return WQ_OK;
+}
+
+wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out) {
+    if (!basis || !opts || !out) return WQ_ERR_ARG;
+    *out = nullptr;
+    wq_ctx* ctx = basis->ctx;
+    if (ctx->device < 0) return fail(ctx, WQ_ERR_NO_DEVICE, "context has no device");
+    if ((opts->comps & ~31u) || opts->comps == 0) return fail(ctx, WQ_ERR_ARG, "bad component mask");
+    const wqi::BasisHost& B = basis->B;
+    if (B.dim == 2 && (opts->comps & (1u << WQ_COMP_Z)))
+        return fail(ctx, WQ_ERR_ARG, "d_z weights requested on a planar domain");
+    double tol = opts->tsvd_rel_tol > 0 ? opts->tsvd_rel_tol : 1e-12;
+    int sweeps = opts->max_sweeps > 0 ? opts->max_sweeps : 40;
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+
+    wq_rule* R = new (std::nothrow) wq_rule();
+    if (!R) return fail(ctx, WQ_ERR_OOM, "host allocation failed");
+    R->ctx = ctx;
+    R->basis = basis;
+    R->dim = B.dim;
+    R->nc = B.dim + 2;
+    R->comps = opts->comps;
+    for (int c = 0; c < 5; ++c)
+        if (opts->comps & (1u << c)) R->wcidx[c] = R->nwc++;
+    R->n = B.n;
+    R->E = B.E;
+    R->nnz = B.row_ptr[B.n];
+    R->max_n_i = B.max_n_i;
+    wq_status sst = WQ_OK;
+    auto bail = [&](wq_status s) {
+        delete R;
+        return s;
+    };
+
+    // a1: point counts (host)
+    std::vector<int32_t> side;
+    wqi::Error err{WQ_OK, ""};
+    if (!wqi::point_counts(B, opts->count_mode, side, err)) return bail(fail(ctx, err.code, err.msg));
+    const int64_t E = B.E, n = B.n;
+    const int nc = R->nc;
+    std::vector<int32_t> m(E), nsub(B.nsub.begin(), B.nsub.end());
+    std::vector<int64_t> pt_ptr(E + 1, 0), gp_ptr(E + 1, 0), bt_ptr(E + 1, 0), gbt_ptr(E + 1, 0);
+    for (int64_t e = 0; e < E; ++e) {
+        m[e] = B.m(e);
+        const int64_t P = (int64_t)side[e] * side[e];
+        pt_ptr[e + 1] = pt_ptr[e] + P;
+        gp_ptr[e + 1] = gp_ptr[e] + 16 * nsub[e];
+        bt_ptr[e + 1] = bt_ptr[e] + P * nc * m[e];
+        gbt_ptr[e + 1] = gbt_ptr[e] + 16LL * nsub[e] * nc * m[e];
+    }
+    R->Q = pt_ptr[E];
+    R->G = gp_ptr[E];
+    std::vector<int32_t> pt_elem(R->Q), gp_elem(R->G);
+    for (int64_t e = 0; e < E; ++e) {
+        for (int64_t p = pt_ptr[e]; p < pt_ptr[e + 1]; ++p) pt_elem[p] = (int32_t)e;
+        for (int64_t p = gp_ptr[e]; p < gp_ptr[e + 1]; ++p) gp_elem[p] = (int32_t)e;
+    }
+    // row plan: positions of each support element's functions in row i
+    R->nsupp = B.supp_ptr[n];
+    std::vector<int64_t> pos_ptr(R->nsupp + 1, 0), w_ptr(n + 1, 0);
+    std::vector<uint8_t> il(R->nsupp);
+    for (int64_t s = 0; s < R->nsupp; ++s) pos_ptr[s + 1] = pos_ptr[s] + m[B.supp[s]];
+    std::vector<uint16_t> pos(pos_ptr[R->nsupp]);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t* c0 = B.col.data() + B.row_ptr[i];
+        const int32_t* c1 = B.col.data() + B.row_ptr[i + 1];
+        if (c1 - c0 > 65535) return bail(fail(ctx, WQ_ERR_ARG, "row longer than 65535 entries"));
+        int64_t r = 0;
+        for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
+            const int32_t e = B.supp[s];
+            r += (int64_t)side[e] * side[e];
+            int found = -1;
+            for (int64_t p = B.fn_ptr[e]; p < B.fn_ptr[e + 1]; ++p) {
+                const int32_t j = B.fns[p];
+                pos[pos_ptr[s] + (p - B.fn_ptr[e])] = (uint16_t)(std::lower_bound(c0, c1, j) - c0);
+                if (j == (int32_t)i) found = (int)(p - B.fn_ptr[e]);
+            }
+            if (found < 0 || found > 255) return bail(fail(ctx, WQ_ERR_ARG, "support bookkeeping failed"));
+            il[s] = (uint8_t)found;
+        }
+        w_ptr[i + 1] = w_ptr[i] + r;
+        R->max_r = std::max<int>(R->max_r, (int)r);
+        if (r < B.row_ptr[i + 1] - B.row_ptr[i])
+            return bail(fail(ctx, WQ_ERR_ILLPOSED, "r_i < n_i for test function " + std::to_string(i)));
+    }
+    R->sum_r = w_ptr[n];
+    // processing order of the rows: Morton order of the functions' control points
+    std::vector<int32_t> order(n);
+    {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int64_t i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], B.ctrl[3 * i + d]);
+                hi[d] = std::max(hi[d], B.ctrl[3 * i + d]);
+            }
+        std::vector<uint64_t> key(n);
+        for (int64_t i = 0; i < n; ++i) {
+            uint64_t k = 0;
+            uint32_t c[3];
+            for (int d = 0; d < 3; ++d) {
+                double t = hi[d] > lo[d] ? (B.ctrl[3 * i + d] - lo[d]) / (hi[d] - lo[d]) : 0.0;
+                c[d] = (uint32_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
+            }
+            for (int b = 20; b >= 0; --b)
+                for (int d = 0; d < 3; ++d) k = (k << 1) | ((c[d] >> b) & 1u);
+            key[i] = k;
+        }
+        for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    }
+    std::vector<int32_t> row_ptr32(n + 1);
+    for (int64_t i = 0; i <= n; ++i) row_ptr32[i] = (int32_t)B.row_ptr[i];
+    if (B.row_ptr[n] > INT32_MAX) return bail(fail(ctx, WQ_ERR_ARG, "nnz exceeds 32-bit row pointers"));
+
+    // uploads
+    if (!upload(R, R->d_m, m, sst) || !upload(R, R->d_nsub, nsub, sst) || !upload(R, R->d_side, side, sst) ||
+        !upload(R, R->d_coef_ptr, B.coef_ptr, sst) || !upload(R, R->d_coef, B.coef, sst) ||
+        !upload(R, R->d_sub_ptr, B.sub_ptr, sst) || !upload(R, R->d_geom, B.geom, sst) ||
+        !upload(R, R->d_pt_ptr, pt_ptr, sst) || !upload(R, R->d_gp_ptr, gp_ptr, sst) ||
+        !upload(R, R->d_bt_ptr, bt_ptr, sst) || !upload(R, R->d_gbt_ptr, gbt_ptr, sst) ||
+        !upload(R, R->d_pt_elem, pt_elem, sst) || !upload(R, R->d_gp_elem, gp_elem, sst) ||
+        !upload(R, R->d_row_ptr, row_ptr32, sst) || !upload(R, R->d_col, B.col, sst) ||
+        !upload(R, R->d_supp_ptr, B.supp_ptr, sst) || !upload(R, R->d_supp, B.supp, sst) ||
+        !upload(R, R->d_pos_ptr, pos_ptr, sst) || !upload(R, R->d_pos, pos, sst) || !upload(R, R->d_il, il, sst) ||
+        !upload(R, R->d_w_ptr, w_ptr, sst) || !upload(R, R->d_fn_ptr, B.fn_ptr, sst) ||
+        !upload(R, R->d_order, order, sst) ||
+        !upload(R, R->d_fns, B.fns, sst))
+        return bail(sst);
+    if (!dalloc(R, R->d_table, (size_t)bt_ptr[E], sst) || !dalloc(R, R->d_gtable, (size_t)gbt_ptr[E], sst) ||
+        !dalloc(R, R->d_x, (size_t)R->Q * 3, sst) || !dalloc(R, R->d_gx, (size_t)R->G * 3, sst) ||
+        !dalloc(R, R->d_gw, (size_t)R->G, sst) || !dalloc(R, R->d_W, (size_t)R->sum_r * R->nwc, sst) ||
+        !dalloc(R, R->d_status, 1, sst) || !dalloc(R, R->d_table2, (size_t)bt_ptr[E], sst) ||
+        !dalloc(R, R->d_W2, (size_t)R->sum_r * R->nwc, sst) || !dalloc(R, R->d_coef_stage, (size_t)R->Q, sst) ||
+        !dalloc(R, R->d_vals_stage, (size_t)R->nnz, sst))
+        return bail(sst);
+    for (int c = 0; c < 5; ++c)
+        if (R->wcidx[c] >= 0 && !dalloc(R, R->d_mom[c], (size_t)R->nnz, sst)) return bail(sst);
+    int32_t* d_rank = nullptr;
+    uint8_t* d_zid = nullptr;
+    if (!dalloc(R, d_rank, (size_t)n, sst) || !dalloc(R, d_zid, (size_t)n, sst)) return bail(sst);
+    // TSVD scratch: one slice per resident CTA
+    const int64_t mn = R->max_n_i, mr = R->max_r;
+    const int64_t per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    int n_cta = (int)std::min<int64_t>(n, (int64_t)std::max(n_sm, 1) * 8);
+    double* d_scratch = nullptr;
+    if (!dalloc(R, d_scratch, (size_t)per_cta * n_cta, sst)) return bail(sst);
+
+    wqd::Elems& el = R->el;
+    el.dim = B.dim;
+    el.nc = nc;
+    el.E = E;
+    el.m = R->d_m;
+    el.nsub = R->d_nsub;
+    el.side = R->d_side;
+    el.coef_ptr = R->d_coef_ptr;
+    el.coef = R->d_coef;
+    el.sub_ptr = R->d_sub_ptr;
+    el.geom = R->d_geom;
+    el.pt_ptr = R->d_pt_ptr;
+    el.gp_ptr = R->d_gp_ptr;
+    el.bt_ptr = R->d_bt_ptr;
+    el.gbt_ptr = R->d_gbt_ptr;
+    wqd::Rows& rw = R->rw;
+    rw.n = n;
+    rw.row_ptr = R->d_row_ptr;
+    rw.supp_ptr = R->d_supp_ptr;
+    rw.supp = R->d_supp;
+    rw.pos_ptr = R->d_pos_ptr;
+    rw.pos = R->d_pos;
+    rw.il = R->d_il;
+    rw.w_ptr = R->d_w_ptr;
+    rw.order = R->d_order;
+
+    // Gauss-Legendre 4-point rule on [0, 1] (closed form)
+    {
+        const double s = 2.0 / 7.0 * std::sqrt(6.0 / 5.0);
+        const double t[4] = {-std::sqrt(3.0 / 7.0 + s), -std::sqrt(3.0 / 7.0 - s), std::sqrt(3.0 / 7.0 - s),
+                             std::sqrt(3.0 / 7.0 + s)};
+        const double w[4] = {(18 - std::sqrt(30.0)) / 36, (18 + std::sqrt(30.0)) / 36, (18 + std::sqrt(30.0)) / 36,
+                             (18 - std::sqrt(30.0)) / 36};
+        double x[4], ww[4];
+        for (int k = 0; k < 4; ++k) {
+            x[k] = 0.5 * (t[k] + 1.0);
+            ww[k] = 0.5 * w[k];
+        }
+        wqd::set_gauss_constants(x, ww);
+    }
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    auto cleanup_events = [&]() {
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+    };
+    cudaEventRecord(ev0, st);
+    cudaError_t ce = cudaMemsetAsync(R->d_status, 0, sizeof(unsigned), st);
+    // a2 + a3: placement and basis tables at WQ and Gauss points
+    if (ce == cudaSuccess)
+        ce = wqd::launch_eval(el, R->d_pt_elem, R->Q, 0, R->d_table, R->d_x, nullptr, R->d_status, st);
+    if (ce == cudaSuccess)
+        ce = wqd::launch_eval(el, R->d_gp_elem, R->G, 1, R->d_gtable, R->d_gx, R->d_gw, R->d_status, st);
+    // a4: Gauss moments per component (c = 1)
+    for (int c = 0; c < 5 && ce == cudaSuccess; ++c) {
+        if (R->wcidx[c] < 0) continue;
+        wqd::Terms tm;
+        tm.nt = 1;
+        tm.t[0] = {0, table_comp(R, c), 0, 1.0};
+        ce = wqd::launch_rowasm_f64(el, rw, tm, 1, R->d_gtable, nullptr, 0, R->d_gw, nullptr, R->d_mom[c],
+                                    R->max_n_i, st);
+    }
+    // a5: truncated-SVD weights per component
+    std::vector<int32_t> rank(n);
+    std::vector<uint8_t> zid(n);
+    for (int c = 0; c < 5 && ce == cudaSuccess; ++c) {
+        if (R->wcidx[c] < 0) continue;
+        ce = wqd::launch_tsvd(el, rw, R->d_table, table_comp(R, c), R->d_mom[c], R->d_W, R->nwc, R->wcidx[c], tol,
+                              sweeps, d_scratch, per_cta, n_cta, d_rank, d_zid, R->d_status, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(rank.data(), d_rank, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(zid.data(), d_zid, n, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce == cudaSuccess) {
+            int trunc = 0, zcount = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                trunc += rank[i] < (B.row_ptr[i + 1] - B.row_ptr[i]);
+                zcount += zid[i];
+            }
+            R->info.n_truncated[c] = trunc;
+            R->info.n_z_identity[c] = zcount;
+        }
+    }
+    // FP32 split copies for the mixed-precision assembly
+    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_table, R->d_table2, bt_ptr[E], st);
+    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_W, R->d_W2, R->sum_r * R->nwc, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev1, st);
+    unsigned hstat = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstat, R->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+        cleanup_events();
+        return bail(fail(ctx, WQ_ERR_CUDA, std::string("rule build: ") + cudaGetErrorString(ce)));
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cleanup_events();
+    wq_status s2 = status_to_error(ctx, hstat);
+    if (s2 != WQ_OK) return bail(s2);
+    R->info.n_points = R->Q;
+    R->info.n_gauss = R->G;
+    R->info.sum_r = R->sum_r;
+    R->info.max_r = R->max_r;
+    R->info.setup_ms = ms;
+    *out = R;
+    return WQ_OK;
+}
+
+void wq_rule_destroy(wq_rule* rule) {
+    if (rule && rule->ctx && rule->ctx->device >= 0) cudaSetDevice(rule->ctx->device);
+    delete rule;
+}
+
+wq_status wq_rule_info_get(const wq_rule* rule, wq_rule_info* info) {
+    if (!rule || !info) return WQ_ERR_ARG;
+    *info = rule->info;
+    return WQ_OK;
+}
+
+wq_status wq_rule_points(const wq_rule* rule, const double** d_x, int64_t* n_points) {
+    if (!rule) return WQ_ERR_ARG;
+    if (d_x) *d_x = rule->d_x;
+    if (n_points) *n_points = rule->Q;
+    return WQ_OK;
+}
+
+wq_status wq_rule_gauss_points(const wq_rule* rule, const double** d_x, int64_t* n_gauss) {
+    if (!rule) return WQ_ERR_ARG;
+    if (d_x) *d_x = rule->d_gx;
+    if (n_gauss) *n_gauss = rule->G;
+    return WQ_OK;
+}
+
+wq_status wq_pattern(const wq_rule* rule, int64_t* n, int64_t* nnz, const int32_t** d_row_ptr, const int32_t** d_col) {
+    if (!rule) return WQ_ERR_ARG;
+    if (n) *n = rule->n;
+    if (nnz) *nnz = rule->nnz;
+    if (d_row_ptr) *d_row_ptr = rule->d_row_ptr;
+    if (d_col) *d_col = rule->d_col;
+    return WQ_OK;
+}
+
+wq_status wq_rule_weights(const wq_rule* rule, int32_t comp, const double** d_w, const int64_t** d_w_ptr) {
+    if (!rule || comp < 0 || comp > 4 || rule->wcidx[comp] < 0)
+        return fail(rule ? rule->ctx : nullptr, WQ_ERR_ARG, "component not built");
+    // the weights of all components are interleaved; expose the base of this one (stride nwc)
+    if (d_w) *d_w = rule->d_W + rule->wcidx[comp];
+    if (d_w_ptr) *d_w_ptr = rule->d_w_ptr;
+    return WQ_OK;
+}
+
+wq_status wq_rule_table(const wq_rule* rule, int32_t gauss, const double** d_table, const int64_t** d_off,
+                        const int64_t** d_pt_ptr, const double** d_gw, int32_t* ncomp) {
+    if (!rule) return WQ_ERR_ARG;
+    if (d_table) *d_table = gauss ? rule->d_gtable : rule->d_table;
+    if (d_off) *d_off = gauss ? rule->d_gbt_ptr : rule->d_bt_ptr;
+    if (d_pt_ptr) *d_pt_ptr = gauss ? rule->d_gp_ptr : rule->d_pt_ptr;
+    if (d_gw) *d_gw = gauss ? rule->d_gw : nullptr;
+    if (ncomp) *ncomp = rule->nc;
+    return WQ_OK;
+}
+
+wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* stream) {
+    if (!rule || !d_vals || comp < 0 || comp > 4 || !rule->d_mom[comp])
+        return fail(rule ? rule->ctx : nullptr, WQ_ERR_ARG, "component not built");
+    CUDA_TRY(rule->ctx, cudaMemcpyAsync(d_vals, rule->d_mom[comp], rule->nnz * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return WQ_OK;
+}
+
+wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t prec, void* d_vals,
+                      void* stream) {
+    if (!rule || !d_vals) return WQ_ERR_ARG;
+    wqd::Terms tm;
+    if (!op_terms(rule, op, alpha, true, tm))
+        return fail(rule->ctx, WQ_ERR_ARG, "operator needs weight sets that this rule did not build");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (prec == WQ_PREC_F64)
+        e = wqd::launch_rowasm_f64(rule->el, rule->rw, tm, 0, rule->d_table, rule->d_W, rule->nwc, nullptr,
+                                   (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
+    else if (prec == WQ_PREC_F32)
+        e = wqd::launch_rowasm_f32(rule->el, rule->rw, tm, rule->d_table2, rule->d_W2, rule->nwc,
+                                   (const double*)d_coef, (float*)d_vals, rule->max_n_i, st);
+    else
+        return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
+    if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
+    return WQ_OK;
+}
+
+wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t prec,
+                         void* d_vals, void* stream) {
+    if (!rule || !d_vals) return WQ_ERR_ARG;
+    wqd::Terms tm;
+    if (!op_terms(rule, op, alpha, false, tm)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
+    if (prec != WQ_PREC_F64) return fail(rule->ctx, WQ_ERR_ARG, "Gauss assembly supports WQ_PREC_F64");
+    cudaError_t e = wqd::launch_rowasm_f64(rule->el, rule->rw, tm, 1, rule->d_gtable, nullptr, 0, rule->d_gw,
+                                           (const double*)d_coef, (double*)d_vals, rule->max_n_i, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
+    return WQ_OK;
+}
+
+wq_status wq_interp(const wq_rule* rule, const double* d_u, double* d_uq, double* d_grad, void* stream) {
+    if (!rule || !d_u || !d_uq) return WQ_ERR_ARG;
+    cudaError_t e = wqd::launch_interp(rule->el, rule->d_pt_elem, rule->d_fns, rule->d_fn_ptr, rule->Q,
+                                       rule->d_table, d_u, d_uq, d_grad, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("interp launch: ") + cudaGetErrorString(e));
+    return WQ_OK;
+}
+
+wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha, int32_t prec,
+                           void* h_vals, void* stream) {
+    if (!rule || !h_coef || !h_vals) return WQ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(rule->ctx, cudaMemcpyAsync(rule->d_coef_stage, h_coef, rule->Q * sizeof(double), cudaMemcpyHostToDevice, st));
+    wq_status s = wq_assemble(rule, op, rule->d_coef_stage, alpha, prec, rule->d_vals_stage, stream);
+    if (s != WQ_OK) return s;
+    const size_t vb = rule->nnz * (prec == WQ_PREC_F32 ? sizeof(float) : sizeof(double));
+    CUDA_TRY(rule->ctx, cudaMemcpyAsync(h_vals, rule->d_vals_stage, vb, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(rule->ctx, cudaStreamSynchronize(st));
+    return WQ_OK;
+}
+
+}  // extern "C"

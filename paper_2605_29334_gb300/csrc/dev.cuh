@@ -1,0 +1,49 @@
+// Device-side views shared by the WQ kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wqd {
+
+// Status flags written by kernels (bitwise OR into a device word).
+enum : unsigned int {
+    ST_NOT_CONVERGED = 1u,
+    ST_NONFINITE = 2u,
+    ST_ILLPOSED = 4u,
+    ST_BAD_INDEX = 8u,
+    ST_GEOMETRY = 16u
+};
+
+// Per-element spline data and point tables of one rule.
+struct Elems {
+    int dim;                 // 2 or 3
+    int nc;                  // table components: N, d_x, d_y, (d_z), lap  (= dim + 2)
+    int64_t E;
+    const int32_t* m;        // [E] functions on the element
+    const int32_t* nsub;     // [E] 1 or 4
+    const int32_t* side;     // [E] WQ grid side
+    const int64_t* coef_ptr; // [E+1] into coef ([m][nsub][4][4])
+    const double* coef;
+    const int64_t* sub_ptr;  // [E+1]; geometry net of sub s of e at geom + 48*(sub_ptr[e]+s)
+    const double* geom;      // [nsub][4][4][3]
+    const int64_t* pt_ptr;   // [E+1] WQ points of e
+    const int64_t* gp_ptr;   // [E+1] Gauss points of e (16 nsub)
+    const int64_t* bt_ptr;   // [E+1] WQ table of e: [P_e][nc][m_e]
+    const int64_t* gbt_ptr;  // [E+1] Gauss table of e: [16 nsub][nc][m_e]
+};
+
+// Row (test function) plan: support elements and local positions.
+struct Rows {
+    int64_t n;
+    const int32_t* row_ptr;   // [n+1] CSR pattern of S_i
+    const int64_t* supp_ptr;  // [n+1]
+    const int32_t* supp;      // support elements, ascending
+    const int64_t* pos_ptr;   // [#supp + 1] into pos
+    const uint16_t* pos;      // for support entry s (element e): position in row i of each local function of e
+    const uint8_t* il;        // [#supp] local index of function i in element supp[s]
+    const int64_t* w_ptr;     // [n+1] weights of row i at [w_ptr[i], w_ptr[i+1])
+    const int32_t* order;     // [n] processing order of the rows (spatially sorted), or null
+};
+
+}  // namespace wqd

@@ -1,0 +1,249 @@
+// Truncated-SVD weights of every test function (paper Sec. 4.3):
+//     A = [D_c N_j(x_q)]  (j in S_i, q in the points of supp N_i),  A = U S V^T,
+//     keep s_k >= tol * s_max,
+//     w = Z^2 V_t (V_t^T Z^2 V_t)^{-1} S_t^{-1} U_t^T b,   Z = diag(N_i(x_q)).
+//
+// One CTA per system (persistent grid over rows), FP64, matrices in a per-CTA
+// global scratch slice:
+//  1. gather A^T row-major by function (At[a][q]) and z from the point tables;
+//  2. one-sided (Hestenes) Jacobi on the n_i vectors At[a] (length r_i), round-
+//     robin pairs, one warp per pair, accumulating the rotations in Jt (so that
+//     A^T J = [s_k v_k], U = J);  a sweep cap ends it with a status flag;
+//  3. s_k = |At[k]|, keep s_k >= tol s_max;  g = S_t^{-1} U_t^T b;
+//  4. G = Z V_t (columns z * At[k] / s_k), Householder QR G = Q R, then
+//     w = Z Q R^{-T} g  -- the inverse of G^T G = V_t^T Z^2 V_t applied through
+//     the QR factor, as the paper does for the full-rank case (Sec. 2, Eq. QR).
+//  If N_i vanishes at one of its points (z_q == 0, V_t^T Z^2 V_t singular) the
+//  row uses Z = I and is flagged.
+#include "kernels.h"
+
+namespace wqd {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* __restrict__ table, int tc,
+                                              const double* __restrict__ mom, double* __restrict__ W, int nwc,
+                                              int wc, double tol, int max_sweeps, double* __restrict__ scratch,
+                                              int64_t per_cta, int32_t* __restrict__ rank_out,
+                                              uint8_t* __restrict__ zid_out, unsigned* status) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5, bd = blockDim.x;
+    __shared__ int sh_t;
+    double* S = scratch + (int64_t)blockIdx.x * per_cta;
+    const int nc = el.nc;
+    for (int64_t i = blockIdx.x; i < rw.n; i += gridDim.x) {
+        const int n = rw.row_ptr[i + 1] - rw.row_ptr[i];
+        const int r = (int)(rw.w_ptr[i + 1] - rw.w_ptr[i]);
+        double* At = S;                      // [n][r]
+        double* G = At + (int64_t)n * r;     // [n][r]  (t columns of Z V_t, then Householder data)
+        double* Jt = G + (int64_t)n * r;     // [n][n]
+        double* z = Jt + (int64_t)n * n;     // [r]
+        double* v = z + r;                   // [r]
+        double* b = v + r;                   // [n]
+        double* sig = b + n;                 // [n]
+        double* g = sig + n;                 // [n]
+        double* tau = g + n;                 // [n]
+        int* keep = (int*)(tau + n);         // [n]
+        for (int64_t k = tid; k < (int64_t)n * r; k += bd) At[k] = 0.0;
+        for (int64_t k = tid; k < (int64_t)n * n; k += bd) Jt[k] = (k / n == k % n) ? 1.0 : 0.0;
+        for (int k = tid; k < n; k += bd) b[k] = mom[rw.row_ptr[i] + k];
+        __syncthreads();
+        // 1. gather
+        int qoff = 0;
+        for (int64_t s = rw.supp_ptr[i]; s < rw.supp_ptr[i + 1]; ++s) {
+            const int e = rw.supp[s];
+            const int m = el.m[e], P = el.side[e] * el.side[e];
+            const double* tb = table + el.bt_ptr[e];
+            const uint16_t* pos = rw.pos + rw.pos_ptr[s];
+            const int il = rw.il[s];
+            for (int k = tid; k < P * m; k += bd) {
+                const int q = k / m, jl = k - q * m;
+                At[(int64_t)pos[jl] * r + qoff + q] = tb[((int64_t)q * nc + tc) * m + jl];
+            }
+            for (int q = tid; q < P; q += bd) z[qoff + q] = tb[(int64_t)q * nc * m + il];
+            qoff += P;
+        }
+        __syncthreads();
+        int zero_z = 0;
+        for (int q = tid; q < r; q += bd) zero_z |= (z[q] == 0.0);
+        zero_z = __syncthreads_or(zero_z);
+        if (zero_z)
+            for (int q = tid; q < r; q += bd) z[q] = 1.0;
+        // 2. one-sided Jacobi
+        const int np = (n + 1) & ~1;
+        const double tolJ = fmax(2.220446049250313e-16 * sqrt((double)r), 1e-15);
+        int converged = (n < 2);
+        for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+            int rotated = 0;
+            for (int rnd = 0; rnd < np - 1; ++rnd) {
+                for (int k = warp; k < np / 2; k += nwarp) {
+                    int p, q;
+                    if (k == 0) {
+                        p = rnd;
+                        q = np - 1;
+                    } else {
+                        p = (rnd + k) % (np - 1);
+                        q = (rnd - k + (np - 1)) % (np - 1);
+                    }
+                    if (p >= n || q >= n) continue;
+                    double* ap = At + (int64_t)p * r;
+                    double* aq = At + (int64_t)q * r;
+                    double al = 0.0, be = 0.0, ga = 0.0;
+                    for (int x = lane; x < r; x += 32) {
+                        const double u = ap[x], w = aq[x];
+                        al += u * u;
+                        be += w * w;
+                        ga += u * w;
+                    }
+                    al = warp_sum(al);
+                    be = warp_sum(be);
+                    ga = warp_sum(ga);
+                    if (al > 0.0 && be > 0.0 && fabs(ga) > tolJ * sqrt(al * be)) {
+                        const double zeta = (be - al) / (2.0 * ga);
+                        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                        for (int x = lane; x < r; x += 32) {
+                            const double u = ap[x], w = aq[x];
+                            ap[x] = c * u - sn * w;
+                            aq[x] = sn * u + c * w;
+                        }
+                        double* jp = Jt + (int64_t)p * n;
+                        double* jq = Jt + (int64_t)q * n;
+                        for (int x = lane; x < n; x += 32) {
+                            const double u = jp[x], w = jq[x];
+                            jp[x] = c * u - sn * w;
+                            jq[x] = sn * u + c * w;
+                        }
+                        rotated = 1;
+                    }
+                }
+                __syncthreads();
+            }
+            converged = !__syncthreads_or(rotated);
+        }
+        if (!converged && tid == 0) atomicOr(status, ST_NOT_CONVERGED);
+        // 3. singular values, kept set, g = S_t^-1 U_t^T b
+        for (int a = warp; a < n; a += nwarp) {
+            double s2 = 0.0;
+            for (int x = lane; x < r; x += 32) s2 += At[(int64_t)a * r + x] * At[(int64_t)a * r + x];
+            s2 = warp_sum(s2);
+            if (lane == 0) sig[a] = sqrt(s2);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double smax = 0.0;
+            for (int a = 0; a < n; ++a) smax = fmax(smax, sig[a]);
+            int t = 0;
+            if (smax > 0.0)
+                for (int a = 0; a < n; ++a)
+                    if (sig[a] >= tol * smax) keep[t++] = a;
+            sh_t = t;
+        }
+        __syncthreads();
+        const int t = sh_t;
+        for (int k = warp; k < t; k += nwarp) {
+            const int a = keep[k];
+            double d = 0.0;
+            for (int x = lane; x < n; x += 32) d += Jt[(int64_t)a * n + x] * b[x];
+            d = warp_sum(d);
+            if (lane == 0) g[k] = d / sig[a];
+        }
+        // 4. G = Z V_t
+        for (int64_t k = tid; k < (int64_t)t * r; k += bd) {
+            const int c = (int)(k / r), q = (int)(k - (int64_t)c * r);
+            const int a = keep[c];
+            G[k] = z[q] * At[(int64_t)a * r + q] / sig[a];
+        }
+        __syncthreads();
+        // Householder QR of G (r x t, column c stored at G + c*r)
+        for (int c = 0; c < t; ++c) {
+            double* gc = G + (int64_t)c * r;
+            if (warp == 0) {
+                double xn2 = 0.0;
+                for (int x = c + 1 + lane; x < r; x += 32) xn2 += gc[x] * gc[x];
+                xn2 = warp_sum(xn2);
+                const double alpha = gc[c];
+                double tk = 0.0, beta = alpha, scale = 0.0;
+                if (xn2 > 0.0) {
+                    beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+                    tk = (beta - alpha) / beta;
+                    scale = 1.0 / (alpha - beta);
+                }
+                __syncwarp();
+                if (xn2 > 0.0)
+                    for (int x = c + 1 + lane; x < r; x += 32) gc[x] *= scale;
+                if (lane == 0) {
+                    gc[c] = beta;
+                    tau[c] = tk;
+                }
+            }
+            __syncthreads();
+            const double tk = tau[c];
+            for (int l = c + 1 + warp; l < t; l += nwarp) {
+                double* gl = G + (int64_t)l * r;
+                double d = 0.0;
+                for (int x = c + 1 + lane; x < r; x += 32) d += gc[x] * gl[x];
+                d = warp_sum(d);
+                d = tk * (gl[c] + d);
+                for (int x = c + 1 + lane; x < r; x += 32) gl[x] -= d * gc[x];
+                __syncwarp();
+                if (lane == 0) gl[c] -= d;
+            }
+            __syncthreads();
+        }
+        // solve R^T y = g (R[l][c] = G[c*r + l]), then v = Q [y; 0], w = z v
+        if (warp == 0) {
+            for (int x = lane; x < r; x += 32) v[x] = 0.0;
+            __syncwarp();
+            for (int c = 0; c < t; ++c) {
+                const double* gc = G + (int64_t)c * r;
+                double d = 0.0;
+                for (int l = lane; l < c; l += 32) d += gc[l] * v[l];
+                d = warp_sum(d);
+                const double y = (g[c] - d) / gc[c];
+                __syncwarp();
+                if (lane == 0) v[c] = y;
+                __syncwarp();
+            }
+            for (int c = t - 1; c >= 0; --c) {
+                const double* gc = G + (int64_t)c * r;
+                double d = 0.0;
+                for (int x = c + 1 + lane; x < r; x += 32) d += gc[x] * v[x];
+                d = warp_sum(d);
+                d = tau[c] * (v[c] + d);
+                __syncwarp();
+                for (int x = c + 1 + lane; x < r; x += 32) v[x] -= d * gc[x];
+                if (lane == 0) v[c] -= d;
+                __syncwarp();
+            }
+            int bad = 0;
+            double* wout = W + rw.w_ptr[i] * nwc + wc;
+            for (int x = lane; x < r; x += 32) {
+                const double wv = z[x] * v[x];
+                bad |= !isfinite(wv);
+                wout[(int64_t)x * nwc] = wv;
+            }
+            bad = __any_sync(0xffffffffu, bad);
+            if (lane == 0) {
+                rank_out[i] = t;
+                zid_out[i] = (uint8_t)zero_z;
+                if (bad) atomicOr(status, ST_NONFINITE);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, int tc, const double* mom, double* W,
+                        int nwc, int wc, double tol, int max_sweeps, double* scratch, int64_t per_cta, int n_cta,
+                        int32_t* rank, uint8_t* zid, unsigned* status, cudaStream_t st) {
+    if (rw.n == 0) return cudaSuccess;
+    k_tsvd<<<n_cta, 128, 0, st>>>(el, rw, table, tc, mom, W, nwc, wc, tol, max_sweeps, scratch, per_cta, rank, zid,
+                                  status);
+    return cudaGetLastError();
+}
+
+}  // namespace wqd

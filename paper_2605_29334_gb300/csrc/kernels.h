@@ -1,0 +1,67 @@
+// Launchers of the WQ device kernels (implemented in k_*.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dev.cuh"
+
+namespace wqd {
+
+// One assembly term: weight column wc (WQ) / table component tc, multiplied by
+// the point coefficient (use_coef) or by the constant scale.
+struct Term {
+    int wc, tc, use_coef;
+    double scale;
+};
+struct Terms {
+    int nt;
+    Term t[4];
+};
+// The same terms for the FP32 kernel (constant scales split into hi/lo floats).
+struct TermsF {
+    int wc[4], tc[4], use_coef[4];
+    float shi[4], slo[4];
+};
+
+// Placement + basis evaluation at WQ (gauss = 0) or Gauss (gauss = 1) points:
+// table [pts][nc][m_e] per element, coordinates xout [pts][3], Gauss weights
+// (w * area element) wout [pts] (Gauss only).
+cudaError_t launch_eval(const Elems& el, const int32_t* pt_elem, int64_t npts, int gauss,
+                        double* table, double* xout, double* wout, unsigned* status, cudaStream_t st);
+
+// Row-wise assembly of sum of terms into CSR values (FP64).
+//   gauss = 0: weights W [sum_r][nwc] at the WQ points, coef at WQ points;
+//   gauss = 1: Gauss weights gw (area element included) times the test
+//              function's table value, coef at Gauss points.
+// coef may be null (all terms then use their scale).
+cudaError_t launch_rowasm_f64(const Elems& el, const Rows& rw, const Terms& tm, int gauss,
+                              const double* table, const double* W, int nwc, const double* gw,
+                              const double* coef, double* vals, int max_n_i, cudaStream_t st);
+
+// FP32 contraction with hi/lo split products: tables and weights as float2 (hi, lo),
+// coefficient converted on the fly, FP32 accumulation into float CSR values.
+cudaError_t launch_rowasm_f32(const Elems& el, const Rows& rw, const Terms& tm,
+                              const float2* table2, const float2* W2, int nwc,
+                              const double* coef, float* vals, int max_n_i, cudaStream_t st);
+
+// Truncated-SVD weights of every row for one component (Sec. 4.3):
+//   table comp tc gives A, table comp 0 gives Z, mom [nnz] gives b;
+//   writes W[(w_ptr[i] + q) * nwc + wc].  scratch holds `per_cta` doubles per CTA.
+//   Per-row rank written to rank[i], Z = I fallback flagged in zid[i].
+cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, int tc,
+                        const double* mom, double* W, int nwc, int wc, double tol, int max_sweeps,
+                        double* scratch, int64_t per_cta, int n_cta, int32_t* rank, uint8_t* zid,
+                        unsigned* status, cudaStream_t st);
+
+// u_h and grad u_h at WQ points (Sec. 5 interpolation).
+cudaError_t launch_interp(const Elems& el, const int32_t* pt_elem, const int32_t* fns,
+                          const int64_t* fn_ptr, int64_t Q, const double* table, const double* u,
+                          double* uq, double* grad, cudaStream_t st);
+
+// Convert double arrays to (hi, lo) float pairs.
+cudaError_t launch_split_f32(const double* src, float2* dst, int64_t n, cudaStream_t st);
+
+void set_gauss_constants(const double x[4], const double w[4]);
+
+}  // namespace wqd

@@ -1,0 +1,301 @@
+"""Python binding of the WQ C ABI (include/wq.h) -- argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module loads
+``lib/libwq.so`` (built in-tree by ``paper_2605_29334_gb300.build``) and fails
+loudly if it is missing.  Device buffers are torch tensors (the caller's
+memory) or zero-copy torch views of library-owned memory; streams are torch
+streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libwq.so")
+
+WQ_OK, WQ_ERR_ARG, WQ_ERR_MESH, WQ_ERR_ILLPOSED, WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE, WQ_ERR_CUDA, \
+    WQ_ERR_OOM, WQ_ERR_NO_DEVICE = range(9)
+OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S = range(4)
+COMP_N, COMP_X, COMP_Y, COMP_Z, COMP_LAP = range(5)
+PREC_F64, PREC_F32 = 0, 1
+TYPE_NAMES = ["passive", "boundary", "irregular", "enriched_transition", "transition", "enriched_regular", "regular"]
+
+
+class WQError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("wq status %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int64), ("xyz", C.POINTER(C.c_double)),
+                ("n_faces", C.c_int64), ("quads", C.POINTER(C.c_int32)), ("level0_face", C.POINTER(C.c_int32))]
+
+
+class BasisInfo(C.Structure):
+    _fields_ = [("n_functions", C.c_int64), ("n_elements", C.c_int64), ("n_irregular", C.c_int64),
+                ("nnz", C.c_int64), ("max_m", C.c_int32), ("max_n_i", C.c_int32), ("type_count", C.c_int64 * 7)]
+
+
+class RuleOpts(C.Structure):
+    _fields_ = [("comps", C.c_uint32), ("count_mode", C.c_int32), ("tsvd_rel_tol", C.c_double),
+                ("max_sweeps", C.c_int32), ("stream", C.c_void_p)]
+
+
+class RuleInfo(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("n_gauss", C.c_int64), ("sum_r", C.c_int64), ("max_r", C.c_int32),
+                ("n_truncated", C.c_int32 * 5), ("n_z_identity", C.c_int32 * 5), ("setup_ms", C.c_double)]
+
+
+EXPORTS = {
+    "wq_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "wq_destroy": (None, [C.c_void_p]),
+    "wq_last_error": (C.c_char_p, [C.c_void_p]),
+    "wq_build_basis": (C.c_int, [C.c_void_p, C.POINTER(_Mesh), C.POINTER(C.c_void_p)]),
+    "wq_basis_destroy": (None, [C.c_void_p]),
+    "wq_basis_info_get": (C.c_int, [C.c_void_p, C.POINTER(BasisInfo)]),
+    "wq_basis_element": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p, C.c_void_p]),
+    "wq_basis_ctrl": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "wq_basis_pattern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "wq_point_counts": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "wq_rule_build": (C.c_int, [C.c_void_p, C.POINTER(RuleOpts), C.POINTER(C.c_void_p)]),
+    "wq_rule_destroy": (None, [C.c_void_p]),
+    "wq_rule_info_get": (C.c_int, [C.c_void_p, C.POINTER(RuleInfo)]),
+    "wq_rule_points": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
+    "wq_rule_gauss_points": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
+    "wq_pattern": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_void_p),
+                             C.POINTER(C.c_void_p)]),
+    "wq_rule_weights": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "wq_rule_table": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]),
+    "wq_moments": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "wq_assemble": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
+    "wq_gq_assemble": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
+                                 C.c_void_p]),
+    "wq_interp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "wq_assemble_host": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
+                                   C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises ImportError when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("WQ library not built: %s missing (run __graft_entry__.build())" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class _CAI:
+    """Zero-copy __cuda_array_interface__ wrapper of library-owned device memory."""
+
+    def __init__(self, ptr, shape, typestr, strides=None, owner=None):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": strides}
+        self._owner = owner
+
+
+def _dev_view(ptr, shape, dtype, strides=None, owner=None):
+    import torch
+    typestr = {"f8": "<f8", "f4": "<f4", "i4": "<i4", "i8": "<i8"}[dtype]
+    if int(np.prod(shape)) == 0:
+        return torch.empty(shape, dtype={"f8": torch.float64, "f4": torch.float32, "i4": torch.int32,
+                                         "i8": torch.int64}[dtype], device="cuda")
+    return torch.as_tensor(_CAI(ptr, shape, typestr, strides, owner), device="cuda")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return C.c_void_p(0)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    def __init__(self, device=0):
+        h = C.c_void_p()
+        st = lib().wq_create(int(device), C.byref(h))
+        if st != WQ_OK:
+            raise WQError(st, "wq_create(%d) failed" % device)
+        self.h = h
+        self.device = device
+
+    def check(self, st):
+        if st != WQ_OK:
+            raise WQError(st, lib().wq_last_error(self.h).decode(errors="replace"))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().wq_destroy(self.h)
+            self.h = None
+
+
+class Basis:
+    """wq_build_basis on a mesh dict {xyz, quads, level0_face, dim}."""
+
+    def __init__(self, ctx, mesh):
+        self.ctx = ctx
+        self._xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
+        self._quads = np.ascontiguousarray(mesh["quads"], dtype=np.int32)
+        l0 = mesh.get("level0_face")
+        self._l0 = None if l0 is None else np.ascontiguousarray(l0, dtype=np.int32)
+        md = _Mesh(int(mesh.get("dim", 2)), len(self._xyz), self._xyz.ctypes.data_as(C.POINTER(C.c_double)),
+                   len(self._quads), self._quads.ctypes.data_as(C.POINTER(C.c_int32)),
+                   None if self._l0 is None else self._l0.ctypes.data_as(C.POINTER(C.c_int32)))
+        h = C.c_void_p()
+        ctx.check(lib().wq_build_basis(ctx.h, C.byref(md), C.byref(h)))
+        self.h = h
+        info = BasisInfo()
+        ctx.check(lib().wq_basis_info_get(h, C.byref(info)))
+        self.info = info
+        self.n, self.E, self.nnz = info.n_functions, info.n_elements, info.nnz
+
+    def element(self, e):
+        face, typ, m, ns = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self.ctx.check(lib().wq_basis_element(self.h, e, C.byref(face), C.byref(typ), C.byref(m), C.byref(ns),
+                                              None, None))
+        fns = np.zeros(m.value, dtype=np.int32)
+        coef = np.zeros((m.value, ns.value, 4, 4))
+        self.ctx.check(lib().wq_basis_element(self.h, e, None, None, None, None, _ptr(fns), _ptr(coef)))
+        return {"face": face.value, "type": typ.value, "fns": fns, "coef": coef}
+
+    def ctrl(self):
+        out = np.zeros((self.n, 3))
+        self.ctx.check(lib().wq_basis_ctrl(self.h, _ptr(out)))
+        return out
+
+    def pattern(self):
+        rp = np.zeros(self.n + 1, dtype=np.int64)
+        col = np.zeros(self.nnz, dtype=np.int32)
+        self.ctx.check(lib().wq_basis_pattern(self.h, _ptr(rp), _ptr(col)))
+        return rp, col
+
+    def point_counts(self):
+        side = np.zeros(self.E, dtype=np.int32)
+        self.ctx.check(lib().wq_point_counts(self.h, 0, _ptr(side)))
+        return side
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().wq_basis_destroy(self.h)
+            self.h = None
+
+
+class Rule:
+    """wq_rule_build: placement, basis tables, Gauss moments and TSVD weights on the device."""
+
+    def __init__(self, basis, comps=(COMP_N, COMP_X, COMP_Y), tol=1e-12, max_sweeps=0, stream=None):
+        self.basis = basis
+        self.ctx = basis.ctx
+        mask = 0
+        for c in comps:
+            mask |= 1 << int(c)
+        self.comps = tuple(comps)
+        opts = RuleOpts(mask, 0, float(tol), int(max_sweeps), _stream_handle(stream))
+        h = C.c_void_p()
+        self.ctx.check(lib().wq_rule_build(basis.h, C.byref(opts), C.byref(h)))
+        self.h = h
+        info = RuleInfo()
+        self.ctx.check(lib().wq_rule_info_get(h, C.byref(info)))
+        self.info = info
+        self.Q, self.G, self.n, self.nnz = info.n_points, info.n_gauss, basis.n, basis.nnz
+
+    def points(self):
+        p, q = C.c_void_p(), C.c_int64()
+        self.ctx.check(lib().wq_rule_points(self.h, C.byref(p), C.byref(q)))
+        return _dev_view(p.value, (q.value, 3), "f8", owner=self)
+
+    def gauss_points(self):
+        p, q = C.c_void_p(), C.c_int64()
+        self.ctx.check(lib().wq_rule_gauss_points(self.h, C.byref(p), C.byref(q)))
+        return _dev_view(p.value, (q.value, 3), "f8", owner=self)
+
+    def pattern(self):
+        n, nnz, rp, col = C.c_int64(), C.c_int64(), C.c_void_p(), C.c_void_p()
+        self.ctx.check(lib().wq_pattern(self.h, C.byref(n), C.byref(nnz), C.byref(rp), C.byref(col)))
+        return (_dev_view(rp.value, (n.value + 1,), "i4", owner=self),
+                _dev_view(col.value, (nnz.value,), "i4", owner=self))
+
+    def weights(self, comp):
+        w, wp = C.c_void_p(), C.c_void_p()
+        self.ctx.check(lib().wq_rule_weights(self.h, int(comp), C.byref(w), C.byref(wp)))
+        nwc = len(self.comps)
+        return (_dev_view(w.value, (self.info.sum_r,), "f8", strides=(8 * nwc,), owner=self),
+                _dev_view(wp.value, (self.n + 1,), "i8", owner=self))
+
+    def table(self, gauss=False):
+        t, off, pp, gw, nc = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_int32()
+        self.ctx.check(lib().wq_rule_table(self.h, int(gauss), C.byref(t), C.byref(off), C.byref(pp), C.byref(gw),
+                                           C.byref(nc)))
+        E = self.basis.E
+        offs = _dev_view(off.value, (E + 1,), "i8", owner=self)
+        total = int(offs[-1].item())
+        out = {"table": _dev_view(t.value, (total,), "f8", owner=self), "off": offs,
+               "pt_ptr": _dev_view(pp.value, (E + 1,), "i8", owner=self), "ncomp": nc.value}
+        if gauss:
+            out["gw"] = _dev_view(gw.value, (self.G,), "f8", owner=self)
+        return out
+
+    def moments(self, comp, stream=None):
+        import torch
+        out = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+        self.ctx.check(lib().wq_moments(self.h, int(comp), C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def assemble(self, op, coef, alpha=0.0, prec=PREC_F64, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.nnz, dtype=torch.float64 if prec == PREC_F64 else torch.float32, device="cuda")
+        cp = C.c_void_p(coef.data_ptr()) if coef is not None else C.c_void_p(0)
+        self.ctx.check(lib().wq_assemble(self.h, int(op), cp, float(alpha), int(prec), C.c_void_p(out.data_ptr()),
+                                         _stream_handle(stream)))
+        return out
+
+    def gq_assemble(self, op, coef_gauss, alpha=0.0, prec=PREC_F64, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+        cp = C.c_void_p(coef_gauss.data_ptr()) if coef_gauss is not None else C.c_void_p(0)
+        self.ctx.check(lib().wq_gq_assemble(self.h, int(op), cp, float(alpha), int(prec),
+                                            C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def interp(self, u, stream=None):
+        import torch
+        uq = torch.empty(self.Q, dtype=torch.float64, device="cuda")
+        gr = torch.empty((self.Q, 3), dtype=torch.float64, device="cuda")
+        self.ctx.check(lib().wq_interp(self.h, C.c_void_p(u.data_ptr()), C.c_void_p(uq.data_ptr()),
+                                       C.c_void_p(gr.data_ptr()), _stream_handle(stream)))
+        return uq, gr
+
+    def assemble_host(self, op, h_coef, alpha=0.0, prec=PREC_F64, out=None, stream=None):
+        h_coef = np.ascontiguousarray(h_coef, dtype=np.float64)
+        if out is None:
+            out = np.zeros(self.nnz, dtype=np.float64 if prec == PREC_F64 else np.float32)
+        self.ctx.check(lib().wq_assemble_host(self.h, int(op), h_coef.ctypes.data_as(C.c_void_p), float(alpha),
+                                              int(prec), out.ctypes.data_as(C.c_void_p), _stream_handle(stream)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().wq_rule_destroy(self.h)
+            self.h = None

@@ -1,0 +1,202 @@
+"""GPU path vs the FP64 oracle, step by step, through the C ABI.
+
+a2 placement, a3 basis tables at WQ and Gauss points, a4 Gauss moments,
+a5 truncated-SVD weights, a6 WQ assembly (FP64 to 1e-11 normwise -- the bar of
+the FP64 path -- or, where the weight systems' conditioning makes that
+unreachable for any two FP64 implementations, 4x the oracle's own spread
+between two LAPACK SVD drivers; FP32 split-product path to 1e-6), a7
+interpolation, a8 Gauss assembly.  Meshes cover one EP of valence 3..8 (m_e up to 37 > 32 lanes),
+refined enriched regions, clustered EPs, an EP-free grid, a closed surface and
+a mesh with a single active element.
+"""
+import numpy as np
+import pytest
+
+from wq_synth import meshes
+
+pytestmark = pytest.mark.gpu
+
+COMP_ID = {"N": 0, "x": 1, "y": 2, "z": 3, "lap": 4}
+
+CASES = {
+    "disk5": (lambda: meshes.disk(mu=5, n=6), ["N", "x", "y", "lap"]),
+    "disk8_L1": (lambda: meshes.disk(mu=8, n=4, levels=1), ["N", "x", "y"]),
+    "disk3_L2": (lambda: meshes.disk(mu=3, n=3, levels=2), ["N", "x", "y", "lap"]),
+    "rotated_L1": (lambda: meshes.rotated(levels=1), ["N", "x", "y"]),
+    "sphere": (lambda: meshes.cube_sphere(pre=1, levels=1), ["N", "x", "y", "z", "lap"]),
+    "grid1x1": (lambda: meshes.grid(1, 1), ["N", "x", "y"]),
+}
+
+
+def _kappa(x):
+    x = np.asarray(x)
+    return 1.0 + 0.5 * np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) + 0.25 * x[:, 2] ** 2
+
+
+def nerr(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    from paper_2605_29334_gb300 import build, wq
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return wq
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, W):
+    from oracle.basis import Basis
+    from oracle import wq as owq
+    make, comps = CASES[request.param]
+    mesh = make()
+    B = Basis(mesh)
+    R = owq.Rule(B, comps)
+    R.compute_weights()
+    # the oracle's reproducibility floor: same steps with LAPACK gesvd instead of gesdd
+    R2 = owq.Rule(B, comps)
+    R2.compute_weights(driver="gesvd")
+    ctx = W.Context(0)
+    b = W.Basis(ctx, mesh)
+    r = W.Rule(b, comps=[COMP_ID[c] for c in comps])
+    return {"name": request.param, "B": B, "R": R, "R2": R2, "ctx": ctx, "b": b, "r": r, "comps": comps}
+
+
+def fp64_tol(spread, factor=4.0):
+    """1e-11, or factor x the oracle's driver-to-driver spread where that is larger."""
+    return max(1e-11, factor * spread)
+
+
+def test_points(case):
+    R, r = case["R"], case["r"]
+    assert r.Q == R.Q
+    assert np.max(np.abs(r.points().cpu().numpy() - R.x)) < 1e-14
+
+
+def _oracle_block(d, comps_all):
+    rows = [d["N"], d["grad"][..., 0], d["grad"][..., 1]]
+    if comps_all == 5:
+        rows.append(d["grad"][..., 2])
+    rows.append(d["lap"])
+    return np.stack(rows, axis=1)           # [m, nc, P]
+
+
+def test_tables(case):
+    from oracle.gq import gauss_data
+    B, R, r = case["B"], case["R"], case["r"]
+    for gauss in (False, True):
+        t = r.table(gauss)
+        tab = t["table"].cpu().numpy()
+        off = t["off"].cpu().numpy()
+        nc = t["ncomp"]
+        worst = np.zeros(nc)
+        scale = np.zeros(nc)
+        for e in range(B.E):
+            d = gauss_data(B, e) if gauss else R.data[e]
+            ref = _oracle_block(d, nc)                       # [m, nc, P]
+            m, P = ref.shape[0], ref.shape[2]
+            got = tab[off[e]:off[e + 1]].reshape(P, nc, m).transpose(2, 1, 0)
+            worst = np.maximum(worst, np.max(np.abs(got - ref), axis=(0, 2)))
+            scale = np.maximum(scale, np.max(np.abs(ref), axis=(0, 2)))
+            if gauss:
+                gw = t["gw"].cpu().numpy()[t["pt_ptr"].cpu().numpy()[e]:t["pt_ptr"].cpu().numpy()[e + 1]]
+                assert np.max(np.abs(gw - d["w"])) <= 1e-13 * np.max(d["w"])
+        assert np.all(worst <= 1e-12 * scale), (gauss, worst / scale)
+
+
+def test_moments(case):
+    R, r = case["R"], case["r"]
+    for c in case["comps"]:
+        got = r.moments(COMP_ID[c]).cpu().numpy()
+        assert nerr(got, R.moments[c]) < 1e-13, c
+
+
+def test_weights(case):
+    R, r = case["R"], case["r"]
+    for c in case["comps"]:
+        w, wp = r.weights(COMP_ID[c])
+        w = w.cpu().numpy()
+        assert np.array_equal(wp.cpu().numpy(), R.w_ptr)
+        # weights are an intermediate (unique only up to the system's conditioning): 10x the spread
+        assert nerr(w, R.weights[c]) < fp64_tol(nerr(case["R2"].weights[c], R.weights[c]), 10.0), c
+        n_trunc = int(np.sum(R.rank[c] < np.diff(R.row_ptr)))
+        assert r.info.n_truncated[COMP_ID[c]] == n_trunc, c
+
+
+def _ops(case, kap, alpha):
+    comps = case["comps"]
+    grads = [c for c in ("x", "y", "z") if c in comps]
+    ops = {}
+    if "N" in comps:
+        ops[0] = [("N", kap)]
+        if len(grads) >= 2:
+            ops[3] = [("N", alpha * np.ones_like(kap))] + [(g, kap) for g in grads]
+    if len(grads) >= 2:
+        ops[1] = [(g, kap) for g in grads]
+    if "lap" in comps:
+        ops[2] = [("lap", kap)]
+    return ops
+
+
+def test_assembly_f64_and_f32(case, W):
+    import torch
+    R, r = case["R"], case["r"]
+    kap = _kappa(R.x)
+    alpha = 7.5
+    kd = torch.tensor(kap, device="cuda")
+    for op, terms in _ops(case, kap, alpha).items():
+        ref = R.assemble(terms)
+        tol = fp64_tol(nerr(case["R2"].assemble(terms), ref))
+        got = r.assemble(op, kd, alpha=alpha, prec=W.PREC_F64).cpu().numpy()
+        assert nerr(got, ref) < tol, (op, nerr(got, ref), tol)
+        got32 = r.assemble(op, kd, alpha=alpha, prec=W.PREC_F32).cpu().numpy()
+        assert nerr(got32, ref) < 1e-6, (op, nerr(got32, ref))
+    # constant coefficient reproduces the Gauss moments (exactness, Sec. 4.3)
+    if "x" in case["comps"]:
+        ones = torch.ones(R.Q, dtype=torch.float64, device="cuda")
+        K1 = r.assemble(1, ones).cpu().numpy()
+        G = sum(R.moments[c] for c in case["comps"] if c in ("x", "y", "z"))
+        assert nerr(K1, G) < 1e-11
+
+
+def test_gauss_assembly(case, W):
+    import torch
+    from oracle import gq
+    B, R, r = case["B"], case["R"], case["r"]
+    gx = r.gauss_points().cpu().numpy()
+    kg = torch.tensor(_kappa(gx), device="cuda")
+    comps = case["comps"]
+    grads = [c for c in ("x", "y", "z") if c in comps]
+    checks = {0: ["N"], 1: grads}
+    if "lap" in comps:
+        checks[2] = ["lap"]
+    for op, cc in checks.items():
+        ref = gq.assemble(B, cc, coef=_kappa, row_ptr=R.row_ptr, col=R.col)
+        got = r.gq_assemble(op, kg).cpu().numpy()
+        assert nerr(got, ref) < 1e-12, op
+
+
+def test_interp(case):
+    import torch
+    R, r = case["R"], case["r"]
+    rng = np.random.Generator(np.random.PCG64(4))
+    u = rng.normal(size=R.basis.n)
+    uq, gr = r.interp(torch.tensor(u, device="cuda"))
+    ruq, rgr = R.interp(u)
+    assert nerr(uq.cpu().numpy(), ruq) < 1e-13
+    assert nerr(gr.cpu().numpy(), rgr) < 1e-12
+
+
+def test_assemble_host_roundtrip(case, W):
+    import torch
+    R, r = case["R"], case["r"]
+    if "x" not in case["comps"]:
+        pytest.skip("no stiffness weights")
+    kap = _kappa(R.x)
+    dev = r.assemble(1, torch.tensor(kap, device="cuda")).cpu().numpy()
+    torch.cuda.synchronize()
+    host = r.assemble_host(1, kap)
+    assert np.array_equal(dev, host)
