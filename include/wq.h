@@ -211,6 +211,23 @@ wq_status wq_interp(const wq_rule* rule, const double* d_u, double* d_uq, double
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
                            int32_t prec, void* h_vals, void* stream);
 
+/* Truncated-SVD weights of component comp of an existing rule, recomputed into
+ * caller memory d_w [sum_r] (row i at [w_ptr[i], w_ptr[i+1]), the layout of
+ * wq_rule_weights but contiguous), WITHOUT allocating: the solve's workspace is
+ * a fixed 32 MiB array compiled into the library (every device that loads the
+ * library holds it until exit).  The paper has no counterpart; this entry point
+ * serves callers that cannot allocate device memory while they run (a host
+ * program whose own pool allocator owns the free device memory, or a
+ * time-critical loop where cudaMalloc's implicit synchronisation is not
+ * acceptable).  The first call on each device looks up the array's device
+ * address (with that device current) and caches it: make that first call before
+ * any stream capture.  Every call uses the same array, which keeps the last
+ * call's contents; calls that overlap on the GPU race.  The call synchronises
+ * on stream to report the solve's status.  Errors: WQ_ERR_ARG (component not
+ * built; a system needing more than 32 MiB of workspace), WQ_ERR_CUDA,
+ * WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE. */
+wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, double* d_w, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,64 +9,8 @@
 #include <vector>
 
 #include "kernels.h"
+#include "rule.h"
 #include "wq_internal.h"
-
-struct wq_ctx {
-    int device = -1;
-    std::string err;
-};
-
-struct wq_basis {
-    wq_ctx* ctx = nullptr;
-    wqi::BasisHost B;
-};
-
-namespace {
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-};
-
-}  // namespace
-
-struct wq_rule {
-    wq_ctx* ctx = nullptr;
-    const wq_basis* basis = nullptr;
-    int dim = 2, nc = 4;
-    uint32_t comps = 0;
-    int nwc = 0;
-    int wcidx[5] = {-1, -1, -1, -1, -1};
-    int64_t n = 0, E = 0, Q = 0, G = 0, nnz = 0, sum_r = 0, nsupp = 0;
-    int max_n_i = 0, max_r = 0;
-    std::vector<DevBuf> bufs;
-    // device arrays
-    int32_t *d_m = nullptr, *d_nsub = nullptr, *d_side = nullptr, *d_pt_elem = nullptr, *d_gp_elem = nullptr;
-    int64_t *d_coef_ptr = nullptr, *d_sub_ptr = nullptr, *d_pt_ptr = nullptr, *d_gp_ptr = nullptr;
-    int64_t *d_bt_ptr = nullptr, *d_gbt_ptr = nullptr, *d_fn_ptr = nullptr;
-    double *d_coef = nullptr, *d_geom = nullptr, *d_table = nullptr, *d_gtable = nullptr;
-    double *d_x = nullptr, *d_gx = nullptr, *d_gw = nullptr;
-    int32_t *d_row_ptr = nullptr, *d_col = nullptr, *d_supp = nullptr, *d_fns = nullptr;
-    int64_t *d_supp_ptr = nullptr, *d_pos_ptr = nullptr, *d_w_ptr = nullptr;
-    int32_t* d_order = nullptr;
-    uint16_t* d_pos = nullptr;
-    uint8_t* d_il = nullptr;
-    double* d_W = nullptr;                 // [sum_r][nwc]
-    double* d_mom[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    float2 *d_table2 = nullptr, *d_W2 = nullptr;
-    unsigned* d_status = nullptr;
-    // staging for wq_assemble_host
-    double* d_coef_stage = nullptr;
-    double* d_vals_stage = nullptr;
-    wqd::Elems el{};
-    wqd::Rows rw{};
-    wq_rule_info info{};
-
-    ~wq_rule() {
-        for (auto& b : bufs)
-            if (b.p) cudaFree(b.p);
-    }
-};
 
 namespace {
 
@@ -294,6 +238,8 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     R->E = B.E;
     R->nnz = B.row_ptr[B.n];
     R->max_n_i = B.max_n_i;
+    R->tol = tol;
+    R->max_sweeps = sweeps;
     wq_status sst = WQ_OK;
     auto bail = [&](wq_status s) {
         delete R;

@@ -14,7 +14,7 @@
 //     w = Z Q R^{-T} g  -- the inverse of G^T G = V_t^T Z^2 V_t applied through
 //     the QR factor, as the paper does for the full-rank case (Sec. 2, Eq. QR).
 //  If N_i vanishes at one of its points (z_q == 0, V_t^T Z^2 V_t singular) the
-//  row uses Z = I and is flagged.
+//  row uses Z = I and is flagged.  rank_out / zid_out may be null.
 #include "kernels.h"
 
 namespace wqd {
@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
             }
             bad = __any_sync(0xffffffffu, bad);
             if (lane == 0) {
-                rank_out[i] = t;
-                zid_out[i] = (uint8_t)zero_z;
+                if (rank_out) rank_out[i] = t;
+                if (zid_out) zid_out[i] = (uint8_t)zero_z;
                 if (bad) atomicOr(status, ST_NONFINITE);
             }
         }

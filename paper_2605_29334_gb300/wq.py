@@ -79,6 +79,7 @@ EXPORTS = {
     "wq_interp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_assemble_host": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
                                    C.c_void_p]),
+    "wq_rule_weights_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -293,6 +294,13 @@ class Rule:
             out = np.zeros(self.nnz, dtype=np.float64 if prec == PREC_F64 else np.float32)
         self.ctx.check(lib().wq_assemble_host(self.h, int(op), h_coef.ctypes.data_as(C.c_void_p), float(alpha),
                                               int(prec), out.ctypes.data_as(C.c_void_p), _stream_handle(stream)))
+        return out
+
+    def weights_noalloc(self, comp, out, stream=None):
+        """Recompute the weights of comp into the caller's device tensor out [sum_r]
+        using the library's fixed scratch array (no device allocation)."""
+        self.ctx.check(lib().wq_rule_weights_noalloc(self.h, int(comp), C.c_void_p(out.data_ptr()),
+                                                     _stream_handle(stream)))
         return out
 
     def __del__(self):
