@@ -119,6 +119,20 @@ def time_steps(fn, steps, warmup, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def aggregate(nnz, t_total, world, device):
+    """Whole-job totals over ranks: nonzeros summed, timed region max over ranks
+    (each rank assembles its own independent instance; no data-path collective)."""
+    if world <= 1:
+        return float(nnz), float(t_total)
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([float(nnz)], dtype=torch.float64, device=device)
+    dist.all_reduce(v)
+    tt = torch.tensor([float(t_total)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(v.item()), float(tt.item())
+
+
 def bench_ours(args, rank, world):
     import torch
     from paper_2605_29334_gb300 import wq
@@ -181,15 +195,7 @@ def bench_ours(args, rank, world):
         rule.assemble_host(wq.OP_STIFF, hc, prec=prec, out=hv)
     e2e_s = (time.perf_counter() - te) / n_e2e
     stats = {"nnz": nnz, "t": t_total, "t64": float(np.mean(ms64)) / 1e3, "tg": float(np.mean(msg)) / 1e3}
-    if world > 1:
-        import torch.distributed as dist
-        v = torch.tensor([float(nnz)], device="cuda")
-        dist.all_reduce(v)
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_nnz, t_max = float(v.item()), float(tt.item())
-    else:
-        tot_nnz, t_max = float(nnz), t_total
+    tot_nnz, t_max = aggregate(nnz, t_total, world, "cuda")
     if rank != 0:
         return None
     value = tot_nnz * args.steps / t_max

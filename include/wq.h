@@ -192,7 +192,9 @@ wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* st
  *   d_coef  [Q] coefficient c(x_q) at the WQ points (device)
  *   alpha   scalar of WQ_OP_HEAT_S (ignored otherwise)
  *   prec    wq_prec; d_vals [nnz] double (F64) or float (F32), caller-owned.
- * No allocation, no host synchronisation; asynchronous on stream.
+ * No allocation, no host synchronisation; asynchronous on stream.  WQ_PREC_F32
+ * splits the coefficient into a rule-owned buffer first (two kernel launches),
+ * so F32 assemblies on one rule must not overlap on the GPU.
  * Errors: WQ_ERR_ARG (op not built into this rule, bad precision). */
 wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha,
                       int32_t prec, void* d_vals, void* stream);

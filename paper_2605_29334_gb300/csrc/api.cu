@@ -263,6 +263,7 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
         gbt_ptr[e + 1] = gbt_ptr[e] + 16LL * nsub[e] * nc * m[e];
     }
     R->Q = pt_ptr[E];
+    for (int64_t e = 0; e < E; ++e) R->max_P = std::max<int>(R->max_P, side[e] * side[e]);
     R->G = gp_ptr[E];
     std::vector<int32_t> pt_elem(R->Q), gp_elem(R->G);
     for (int64_t e = 0; e < E; ++e) {
@@ -322,6 +323,20 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
         for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
     }
+    // packed per-(row, support element) descriptors for the assembly kernels
+    if (bt_ptr[E] > INT32_MAX || gbt_ptr[E] > INT32_MAX || pos_ptr[R->nsupp] > INT32_MAX || R->G > INT32_MAX)
+        return bail(fail(ctx, WQ_ERR_ARG, "mesh too large for 32-bit table offsets"));
+    std::vector<int4> desc_wq(R->nsupp), desc_gq(R->nsupp);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
+            const int32_t e = B.supp[s];
+            if (m[e] > 255 || side[e] * side[e] > 255)
+                return bail(fail(ctx, WQ_ERR_ARG, "element with more than 255 functions or points"));
+            desc_wq[s] = make_int4((int)bt_ptr[e], (int)pt_ptr[e], m[e] | (side[e] * side[e]) << 8 | il[s] << 16,
+                                   (int)pos_ptr[s]);
+            desc_gq[s] = make_int4((int)gbt_ptr[e], (int)gp_ptr[e], m[e] | (16 * nsub[e]) << 8 | il[s] << 16,
+                                   (int)pos_ptr[s]);
+        }
     std::vector<int32_t> row_ptr32(n + 1);
     for (int64_t i = 0; i <= n; ++i) row_ptr32[i] = (int32_t)B.row_ptr[i];
     if (B.row_ptr[n] > INT32_MAX) return bail(fail(ctx, WQ_ERR_ARG, "nnz exceeds 32-bit row pointers"));
@@ -337,7 +352,8 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
         !upload(R, R->d_supp_ptr, B.supp_ptr, sst) || !upload(R, R->d_supp, B.supp, sst) ||
         !upload(R, R->d_pos_ptr, pos_ptr, sst) || !upload(R, R->d_pos, pos, sst) || !upload(R, R->d_il, il, sst) ||
         !upload(R, R->d_w_ptr, w_ptr, sst) || !upload(R, R->d_fn_ptr, B.fn_ptr, sst) ||
-        !upload(R, R->d_order, order, sst) ||
+        !upload(R, R->d_order, order, sst) || !upload(R, R->d_desc_wq, desc_wq, sst) ||
+        !upload(R, R->d_desc_gq, desc_gq, sst) ||
         !upload(R, R->d_fns, B.fns, sst))
         return bail(sst);
     if (!dalloc(R, R->d_table, (size_t)bt_ptr[E], sst) || !dalloc(R, R->d_gtable, (size_t)gbt_ptr[E], sst) ||
@@ -345,7 +361,7 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
         !dalloc(R, R->d_gw, (size_t)R->G, sst) || !dalloc(R, R->d_W, (size_t)R->sum_r * R->nwc, sst) ||
         !dalloc(R, R->d_status, 1, sst) || !dalloc(R, R->d_table2, (size_t)bt_ptr[E], sst) ||
         !dalloc(R, R->d_W2, (size_t)R->sum_r * R->nwc, sst) || !dalloc(R, R->d_coef_stage, (size_t)R->Q, sst) ||
-        !dalloc(R, R->d_vals_stage, (size_t)R->nnz, sst))
+        !dalloc(R, R->d_vals_stage, (size_t)R->nnz, sst) || !dalloc(R, R->d_coef2, (size_t)R->Q, sst))
         return bail(sst);
     for (int c = 0; c < 5; ++c)
         if (R->wcidx[c] >= 0 && !dalloc(R, R->d_mom[c], (size_t)R->nnz, sst)) return bail(sst);
@@ -357,6 +373,7 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     const int64_t per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    R->n_sm = std::max(n_sm, 1);
     int n_cta = (int)std::min<int64_t>(n, (int64_t)std::max(n_sm, 1) * 8);
     double* d_scratch = nullptr;
     if (!dalloc(R, d_scratch, (size_t)per_cta * n_cta, sst)) return bail(sst);
@@ -421,8 +438,8 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
         wqd::Terms tm;
         tm.nt = 1;
         tm.t[0] = {0, table_comp(R, c), 0, 1.0};
-        ce = wqd::launch_rowasm_f64(el, rw, tm, 1, R->d_gtable, nullptr, 0, R->d_gw, nullptr, R->d_mom[c],
-                                    R->max_n_i, st);
+        ce = wqd::launch_rowasm_f64(rw, R->d_desc_gq, tm, nc, 1, R->d_gtable, nullptr, 0, R->d_gw, nullptr,
+                                    R->d_mom[c], R->max_n_i, st);
     }
     // a5: truncated-SVD weights per component
     std::vector<int32_t> rank(n);
@@ -540,11 +557,14 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (prec == WQ_PREC_F64)
-        e = wqd::launch_rowasm_f64(rule->el, rule->rw, tm, 0, rule->d_table, rule->d_W, rule->nwc, nullptr,
-                                   (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
+        e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_wq, tm, rule->nc, 0, rule->d_table, rule->d_W, rule->nwc,
+                                   nullptr, (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
+    else if (prec == WQ_PREC_F32 && rule->max_P > 64)
+        return fail(rule->ctx, WQ_ERR_ARG, "FP32 assembly supports at most 64 WQ points per element");
     else if (prec == WQ_PREC_F32)
-        e = wqd::launch_rowasm_f32(rule->el, rule->rw, tm, rule->d_table2, rule->d_W2, rule->nwc,
-                                   (const double*)d_coef, (float*)d_vals, rule->max_n_i, st);
+        e = wqd::launch_rowasm_f32(rule->rw, rule->d_desc_wq, tm, rule->nc, rule->d_table2, rule->d_W2, rule->nwc,
+                                   (const double*)d_coef, rule->d_coef2, rule->Q, (float*)d_vals, rule->max_n_i,
+                                   rule->n_sm, st);
     else
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
@@ -557,8 +577,9 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
     wqd::Terms tm;
     if (!op_terms(rule, op, alpha, false, tm)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
     if (prec != WQ_PREC_F64) return fail(rule->ctx, WQ_ERR_ARG, "Gauss assembly supports WQ_PREC_F64");
-    cudaError_t e = wqd::launch_rowasm_f64(rule->el, rule->rw, tm, 1, rule->d_gtable, nullptr, 0, rule->d_gw,
-                                           (const double*)d_coef, (double*)d_vals, rule->max_n_i, (cudaStream_t)stream);
+    cudaError_t e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_gq, tm, rule->nc, 1, rule->d_gtable, nullptr, 0,
+                                           rule->d_gw, (const double*)d_coef, (double*)d_vals, rule->max_n_i,
+                                           (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
     return WQ_OK;
 }

@@ -30,20 +30,23 @@ struct TermsF {
 cudaError_t launch_eval(const Elems& el, const int32_t* pt_elem, int64_t npts, int gauss,
                         double* table, double* xout, double* wout, unsigned* status, cudaStream_t st);
 
-// Row-wise assembly of sum of terms into CSR values (FP64).
+// Row-wise assembly of a sum of terms into CSR values (FP64).
+//   desc [#supp] per (row, support element): {table offset, first point,
+//   m | P << 8 | il << 16, position offset};
 //   gauss = 0: weights W [sum_r][nwc] at the WQ points, coef at WQ points;
 //   gauss = 1: Gauss weights gw (area element included) times the test
 //              function's table value, coef at Gauss points.
 // coef may be null (all terms then use their scale).
-cudaError_t launch_rowasm_f64(const Elems& el, const Rows& rw, const Terms& tm, int gauss,
-                              const double* table, const double* W, int nwc, const double* gw,
-                              const double* coef, double* vals, int max_n_i, cudaStream_t st);
+cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm, int nc, int gauss,
+                              const double* table, const double* W, int nwc, const double* gw, const double* coef,
+                              double* vals, int max_n_i, cudaStream_t st);
 
-// FP32 contraction with hi/lo split products: tables and weights as float2 (hi, lo),
-// coefficient converted on the fly, FP32 accumulation into float CSR values.
-cudaError_t launch_rowasm_f32(const Elems& el, const Rows& rw, const Terms& tm,
-                              const float2* table2, const float2* W2, int nwc,
-                              const double* coef, float* vals, int max_n_i, cudaStream_t st);
+// FP32 contraction with hi/lo split products and TwoSum accumulation: tables and
+// weights as float2 (hi, lo); the coefficient is split into coef2_buf [n_points]
+// by a small pre-kernel (two launches); float CSR values.
+cudaError_t launch_rowasm_f32(const Rows& rw, const int4* desc, const Terms& tm, int nc, const float2* table2,
+                              const float2* W2, int nwc, const double* coef, float2* coef2_buf, int64_t n_points,
+                              float* vals, int max_n_i, int n_sm, cudaStream_t st);
 
 // Truncated-SVD weights of every row for one component (Sec. 4.3):
 //   table comp tc gives A, table comp 0 gives Z, mom [nnz] gives b;

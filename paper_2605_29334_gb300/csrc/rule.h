@@ -47,6 +47,11 @@ struct wq_rule {
     int32_t *d_row_ptr = nullptr, *d_col = nullptr, *d_supp = nullptr, *d_fns = nullptr;
     int64_t *d_supp_ptr = nullptr, *d_pos_ptr = nullptr, *d_w_ptr = nullptr;
     int32_t* d_order = nullptr;
+    int4 *d_desc_wq = nullptr, *d_desc_gq = nullptr;
+
+    float2* d_coef2 = nullptr;
+    int n_sm = 1;
+    int max_P = 0;          // most WQ points on one element (the FP32 kernel stages <= 64 per window)
     uint16_t* d_pos = nullptr;
     uint8_t* d_il = nullptr;
     double* d_W = nullptr;                 // [sum_r][nwc]
