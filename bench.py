@@ -158,14 +158,22 @@ def bench_ours(args, rank, world):
     out64 = torch.empty(nnz, dtype=torch.float64, device="cuda")
     out32 = torch.empty(nnz, dtype=torch.float32, device="cuda")
     outg = torch.empty(nnz, dtype=torch.float64, device="cuda")
-    # accuracy of the FP32 split-product path against the FP64 path (same weights)
+    # accuracy of the FP32 paths against the FP64 path (same weights), per mode
     rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F64, out=out64)
-    rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F32, out=out32)
     torch.cuda.synchronize()
     a64 = out64.cpu().numpy()
-    rel32 = float(np.max(np.abs(out32.cpu().numpy().astype(np.float64) - a64)) / np.max(np.abs(a64)))
-    prec = wq.PREC_F32 if (args.prec == "auto" and rel32 <= 1e-6) or args.prec == "f32" else wq.PREC_F64
-    out = out32 if prec == wq.PREC_F32 else out64
+    rel = {}
+    for name, pm in (("f32", wq.PREC_F32), ("f32_fast", wq.PREC_F32_FAST)):
+        rule.assemble(wq.OP_STIFF, coef, prec=pm, out=out32)
+        torch.cuda.synchronize()
+        rel[name] = float(np.max(np.abs(out32.cpu().numpy().astype(np.float64) - a64)) / np.max(np.abs(a64)))
+    modes = {"f64": wq.PREC_F64, "f32": wq.PREC_F32, "f32_fast": wq.PREC_F32_FAST}
+    if args.prec == "auto":
+        choice = "f32_fast" if rel["f32_fast"] <= 1e-6 else ("f32" if rel["f32"] <= 1e-6 else "f64")
+    else:
+        choice = args.prec
+    prec = modes[choice]
+    out = out64 if prec == wq.PREC_F64 else out32
     step = lambda: rule.assemble(wq.OP_STIFF, coef, prec=prec, out=out)
     if world > 1:
         torch.distributed.barrier()
@@ -181,11 +189,16 @@ def bench_ours(args, rank, world):
     # comparators on the same GPU and protocol
     ms64 = time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F64, out=out64),
                       max(args.steps // 4, 10), args.warmup, flush)
+    ms32 = {}
+    for name in ("f32", "f32_fast"):
+        pm = modes[name]
+        ms32[name] = float(np.mean(time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=pm, out=out32),
+                                              max(args.steps // 4, 10), args.warmup, flush)))
     msg = time_steps(lambda: rule.gq_assemble(wq.OP_STIFF, coef_g, out=outg), max(args.steps // 4, 10),
                      args.warmup, flush)
     # end to end through the C ABI with pinned host buffers
     h_coef = torch.tensor(kap(xq)).pin_memory()
-    h_vals = torch.empty(nnz, dtype=torch.float32 if prec == wq.PREC_F32 else torch.float64).pin_memory()
+    h_vals = torch.empty(nnz, dtype=torch.float64 if prec == wq.PREC_F64 else torch.float32).pin_memory()
     hc, hv = h_coef.numpy(), h_vals.numpy()
     for _ in range(args.warmup):
         rule.assemble_host(wq.OP_STIFF, hc, prec=prec, out=hv)
@@ -201,6 +214,7 @@ def bench_ours(args, rank, world):
     value = tot_nnz * args.steps / t_max
     mean_s = t_total / args.steps
     ab = algorithmic_bytes_f(rule, basis, prec)
+    gpu_launches = args.steps * (1 if prec == wq.PREC_F64 else 2)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -208,23 +222,25 @@ def bench_ours(args, rank, world):
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == wq.PREC_F32 else "f64", "data": "synthetic",
+        "dtype": "f64" if prec == wq.PREC_F64 else "f32", "precision_mode": choice, "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_functions": basis.n, "n_elements": basis.E, "nnz": nnz,
                    "n_points": rule.Q, "n_gauss": rule.G, "op": "stiffness", "l2": "flushed (256 MB write) before "
                    "every timed step; timed = the assembly kernel only", "parallelism": "independent instance per GPU"},
-        "rel_err_f32_vs_f64": rel32,
-        "gpu_launches": args.steps,
+        "rel_err_vs_f64": rel,
+        "gpu_launches": gpu_launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "k_rowasm_f32" if prec == wq.PREC_F32 else "k_rowasm_f64",
+                     "traffic": None, "kernel": "k_rowasm_f64" if prec == wq.PREC_F64 else "k_chunk_f32",
                      "algorithmic_bytes": ab},
         "comparators": {
             "wq_f64_nnz_per_s": nnz / stats["t64"], "gq_f64_nnz_per_s": nnz / stats["tg"],
+            "wq_f32_nnz_per_s": nnz / (ms32["f32"] / 1e3), "wq_f32_fast_nnz_per_s": nnz / (ms32["f32_fast"] / 1e3),
+            "wq_f32_ms": ms32["f32"], "wq_f32_fast_ms": ms32["f32_fast"],
             "wq_f64_ms": stats["t64"] * 1e3, "gq_f64_ms": stats["tg"] * 1e3,
             "speedup_wq_over_gq_f64": stats["tg"] / stats["t64"]},
         "setup": {"host_basis_ms": host_ms, "rule_build_wall_ms": build_ms, "rule_build_device_ms": rule.info.setup_ms,
                   "n_truncated_x": rule.info.n_truncated[1], "n_z_identity_x": rule.info.n_z_identity[1]},
         "e2e": {"value": nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(rule.Q * 8),
-                "d2h_bytes_per_step": int(nnz * (4 if prec == wq.PREC_F32 else 8))},
+                "d2h_bytes_per_step": int(nnz * (8 if prec == wq.PREC_F64 else 4))},
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -245,7 +261,7 @@ def algorithmic_bytes_f(rule, basis, prec):
     pos = int(np.sum(m * m)) * 2
     supp = int(np.sum(m)) * 4
     rows = (basis.n + 1) * (4 + 8 + 8)
-    out = rule.nnz * (4 if prec == 1 else 8)
+    out = rule.nnz * (8 if prec == 0 else 4)
     return int(weights + tables + coef + pos + supp + rows + out)
 
 
@@ -307,7 +323,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="auto", choices=["auto", "f32", "f64"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "f32", "f32_fast", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -57,8 +57,10 @@ typedef enum { WQ_COMP_N = 0, WQ_COMP_X = 1, WQ_COMP_Y = 2, WQ_COMP_Z = 3, WQ_CO
 
 /* Precision of the assembly contraction. */
 typedef enum {
-    WQ_PREC_F64 = 0,   /* FP64 weights, tables and accumulation; CSR values double */
-    WQ_PREC_F32 = 1    /* FP32 split (hi/lo) products, FP32 accumulation; CSR values float */
+    WQ_PREC_F64 = 0,      /* FP64 weights, tables and accumulation; CSR values double */
+    WQ_PREC_F32 = 1,      /* FP32 split (hi/lo) products, error-free (TwoSum) accumulation; float values */
+    WQ_PREC_F32_FAST = 2  /* FP32 split products, plain FP32 sums (operators with <= 2 terms); float
+                             values; its error depends on the cancellation in the rows -- measure it */
 } wq_prec;
 
 /* Point-count rule (Sec. 4.2). */
@@ -206,6 +208,26 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
 
 /* u_h and grad u_h at the WQ points (Sec. 5): d_u [n] -> d_uq [Q], d_grad [Q][3]. */
 wq_status wq_interp(const wq_rule* rule, const double* d_u, double* d_uq, double* d_grad, void* stream);
+
+/* Matrix-free WQ functional (the residual form of Sec. 5; NEXT: operator apply):
+ *   y_i = sum_t sum_{q in pts(supp N_i)} w^{comps[t]}_iq * g_t(x_q)
+ * h_comps [n_terms] (host, wq_comp, 1 <= n_terms <= 4); d_g [n_terms][Q] point
+ * data (term-major); d_y [n].  No allocation; asynchronous on stream. */
+wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps, const double* d_g, double* d_y,
+                   void* stream);
+
+/* Point fields of the nonlinear heat problem (Sec. 5, theta = 1) from control
+ * variables d_u, d_u_old [n]:  d_kappa [Q] = k0 + k2 u(x_q)^2 (the coefficient
+ * of the tangent S, Eq. S), d_g [1 + dim][Q] with g_0 = (u - u_old)/dt - f and
+ * g_{1+d} = kappa d_d u, so that wq_apply(N, x, y[, z]) gives the residual R_A
+ * of Eq. heat_residual_discrete.  No allocation; asynchronous on stream. */
+wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d_u_old, double dt, double k0,
+                         double k2, double f, double* d_kappa, double* d_g, void* stream);
+
+/* Control-variable id of every function (host) [n]: < n_vertices: the vertex
+ * of a vertex-based function; otherwise n_vertices + 4 * (rank of the enriched
+ * face) + corner for a face-based function. */
+wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
 
 /* Host-buffer round trip for end-to-end use: copies h_coef [Q] to the device,
  * assembles, copies the CSR values back to h_vals [nnz] (double or float by

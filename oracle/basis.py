@@ -177,8 +177,12 @@ class Basis:
                 P[i] = (4 * xyz[q[c]] + 2 * xyz[q[(c + 1) % 4]] + 2 * xyz[q[(c + 3) % 4]]
                         + xyz[q[(c + 2) % 4]]) / 9.0
         self.ctrl = P
-        # geometry Bezier nets per element: [nsub, 4, 4, 3]
-        self.geom = [np.einsum("msij,mk->sijk", c, P[fns]) for c, fns in zip(self.elem_coef, self.elem_fns)]
+        # geometry Bezier nets per element relative to a reference control point
+        # (the element's first function): x = ref + sum_j c_j (P_j - ref), the same map
+        # (partition of unity) without the cancellation of absolute coordinates
+        self.geom_ref = [P[fns[0]] for fns in self.elem_fns]
+        self.geom = [np.einsum("msij,mk->sijk", c, P[fns] - P[fns[0]])
+                     for c, fns in zip(self.elem_coef, self.elem_fns)]
         # supports (as active-element index lists)
         self.supp = [[] for _ in range(self.n)]
         for e, fns in enumerate(self.elem_fns):

@@ -2,6 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
+The contravariant base vectors are evaluated through the normal n = a_1 x a_2
+(a^1 = (a_2 x n)/|n|^2, a^2 = (n x a_1)/|n|^2, |n|^2 = det a_ab), which is the
+same quantity as inverting the metric but avoids the cancellation in
+a_11 a_22 - a_12^2 on skewed elements.
+
 On an element (or one of the four sub-elements of a split irregular element)
 each function is a bicubic Bernstein polynomial in the local coordinates
 xi = (u, v) in [0, 1]^2; the geometry is x(xi) = sum_j P_j N_j(xi).
@@ -70,13 +75,15 @@ def eval_element(basis, e, theta=None, sub=None, xi=None):
         sub, xi = locate(coef.shape[1], theta)
     N, Nu, Nv, Nuu, Nuv, Nvv = _tensor_derivs(coef, sub, xi)
     X, Xu, Xv, Xuu, Xuv, Xvv = [a[0] for a in _tensor_derivs(geom[None], sub, xi)]   # [P, 3]
+    X = basis.geom_ref[e][None, :] + X          # nets are stored relative to a control point
     a1, a2 = Xu, Xv
-    g11 = np.sum(a1 * a1, -1); g12 = np.sum(a1 * a2, -1); g22 = np.sum(a2 * a2, -1)
-    det = g11 * g22 - g12 * g12
-    i11, i12, i22 = g22 / det, -g12 / det, g11 / det
-    # contravariant base vectors a^alpha = a^{alpha beta} a_beta
-    A1 = i11[:, None] * a1 + i12[:, None] * a2
-    A2 = i12[:, None] * a1 + i22[:, None] * a2
+    # contravariant base vectors a^alpha = a^{alpha beta} a_beta, written with the
+    # normal n = a_1 x a_2 (|n|^2 = det a_ab):  a^1 = (a_2 x n)/|n|^2, a^2 = (n x a_1)/|n|^2
+    nrm = np.cross(a1, a2)
+    det = np.sum(nrm * nrm, -1)
+    A1 = np.cross(a2, nrm) / det[:, None]
+    A2 = np.cross(nrm, a1) / det[:, None]
+    i11 = np.sum(A1 * A1, -1); i12 = np.sum(A1 * A2, -1); i22 = np.sum(A2 * A2, -1)
     grad = Nu[..., None] * A1[None] + Nv[..., None] * A2[None]
     # Christoffel symbols Gamma^g_ab = a^g . a_{a,b}
     G1 = [np.sum(A1 * Xuu, -1), np.sum(A1 * Xuv, -1), np.sum(A1 * Xvv, -1)]

@@ -144,17 +144,27 @@ class Rule:
         return np.concatenate(blocks, axis=1), np.concatenate(zs)
 
     # ---------------------------------------------------- 4-5. moments, TSVD
-    def compute_weights(self, gdata=None, driver="gesdd"):
+    def compute_weights(self, gdata=None, driver="gesdd", perturb_seed=None, perturb_ulps=16):
+        """Moments and TSVD weights of every row.  perturb_seed (test use only): multiply
+        every input of the weight solves (A, z, b) by 1 + perturb_ulps 2^-52 u, u ~ U(-1, 1)
+        seeded -- the spread this causes measures the conditioning of the solves at FP64
+        for inputs that agree to a few ulps (as two FP64 evaluations of the basis do)."""
         self.moments = {c: gq_assemble(self.basis, [c], row_ptr=self.row_ptr, col=self.col, gdata=gdata)
                         for c in self.comps}
         self.w_ptr = np.zeros(self.basis.n + 1, dtype=np.int64)
         self.w_ptr[1:] = np.cumsum([len(self.row_points(i)) for i in range(self.basis.n)])
         self.weights = {c: np.zeros(int(self.w_ptr[-1])) for c in self.comps}
         self.rank = {c: np.zeros(self.basis.n, dtype=np.int64) for c in self.comps}
+        rng = None if perturb_seed is None else np.random.Generator(np.random.PCG64(perturb_seed))
         for c in self.comps:
             for i in range(self.basis.n):
                 A, z = self.local_system(i, c)
                 b = self.moments[c][self.row_ptr[i]:self.row_ptr[i + 1]]
+                if rng is not None:
+                    u = perturb_ulps * 2.0 ** -52
+                    A = A * (1 + u * rng.uniform(-1, 1, A.shape))
+                    z = z * (1 + u * rng.uniform(-1, 1, z.shape))
+                    b = b * (1 + u * rng.uniform(-1, 1, b.shape))
                 w, t = tsvd_weights(A, z, b, self.tol, driver)
                 self.weights[c][self.w_ptr[i]:self.w_ptr[i + 1]] = w
                 self.rank[c][i] = t

@@ -538,18 +538,24 @@ bool build_basis(const wq_mesh_desc& mesh, BasisHost& B, Error& err) {
                                      2.0 * B.xyz[q[(c + 3) % 4] * 3 + d] + B.xyz[q[(c + 2) % 4] * 3 + d]) / 9.0;
         }
     }
-    // geometry nets
+    // geometry nets relative to the control point of the element's first function:
+    // x = ref + sum_j c_j (P_j - ref) (partition of unity), so that derivatives of the
+    // geometry do not cancel absolute coordinates
     B.geom.assign(48 * B.sub_ptr[E], 0.0);
+    B.geom_ref.assign(3 * E, 0.0);
     for (int64_t e = 0; e < E; ++e) {
         int ns = nsub[e];
         int32_t m = B.m(e);
         double* G = &B.geom[48 * B.sub_ptr[e]];
         const double* C = &B.coef[B.coef_ptr[e]];
+        const double* ref = &B.ctrl[3 * B.fns[B.fn_ptr[e]]];
+        for (int d = 0; d < 3; ++d) B.geom_ref[3 * e + d] = ref[d];
         for (int32_t a = 0; a < m; ++a) {
             const double* P = &B.ctrl[3 * B.fns[B.fn_ptr[e] + a]];
+            const double rel[3] = {P[0] - ref[0], P[1] - ref[1], P[2] - ref[2]};
             for (int p = 0; p < ns * 16; ++p) {
                 double w = C[a * ns * 16 + p];
-                for (int d = 0; d < 3; ++d) G[p * 3 + d] += w * P[d];
+                for (int d = 0; d < 3; ++d) G[p * 3 + d] += w * rel[d];
             }
         }
     }

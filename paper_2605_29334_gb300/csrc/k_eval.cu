@@ -5,7 +5,8 @@
 // geometry net and the warp reduces x, x_u, x_v, x_uu, x_uv, x_vv by butterfly
 // shuffles; then every lane evaluates the functions jl = lane, lane + 32, ...
 // of the element:
-//   a_alpha = dx/dxi^alpha, a_ab = a_a.a_b, a^ab = inverse,
+//   a_alpha = dx/dxi^alpha, a^1 = (a_2 x n)/|n|^2, a^2 = (n x a_1)/|n|^2 with
+//   n = a_1 x a_2 (the contravariant basis, |n|^2 = det a_ab), a^ab = a^a.a^b,
 //   grad N = (a^1b N_,b) a_1 + (a^2b N_,b) a_2,
 //   lap N  = a^ab (N_,ab - Gamma^g_ab N_,g),  Gamma^g_ab = a^g . x_,ab,
 // and writes table[(point * nc + comp) * m + jl] (comp: N, d_x, d_y, [d_z], lap).
@@ -107,21 +108,26 @@ __global__ void __launch_bounds__(256) k_eval(Elems el, const int32_t* __restric
         for (int a = 0; a < 18; ++a) g[a] = __shfl_sync(0xffffffffu, g[a], 0);
     }
     const double *a1 = g + 3, *a2 = g + 6, *xuu = g + 9, *xuv = g + 12, *xvv = g + 15;
-    const double g11 = a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2];
-    const double g12 = a1[0] * a2[0] + a1[1] * a2[1] + a1[2] * a2[2];
-    const double g22 = a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2];
-    const double det = g11 * g22 - g12 * g12;
+    // contravariant base vectors through the normal n = a1 x a2 (|n|^2 = det a_ab):
+    // a^1 = (a2 x n)/|n|^2, a^2 = (n x a1)/|n|^2 -- no cancellation in a11 a22 - a12^2
+    const double nx = a1[1] * a2[2] - a1[2] * a2[1];
+    const double ny = a1[2] * a2[0] - a1[0] * a2[2];
+    const double nz = a1[0] * a2[1] - a1[1] * a2[0];
+    const double det = nx * nx + ny * ny + nz * nz;
     if (!(det > 0.0) || !isfinite(det)) {
         if (lane == 0) atomicOr(status, ST_GEOMETRY);
         return;
     }
-    const double i11 = g22 / det, i12 = -g12 / det, i22 = g11 / det;
     double A1[3], A2[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        A1[d] = i11 * a1[d] + i12 * a2[d];
-        A2[d] = i12 * a1[d] + i22 * a2[d];
-    }
+    A1[0] = (a2[1] * nz - a2[2] * ny) / det;
+    A1[1] = (a2[2] * nx - a2[0] * nz) / det;
+    A1[2] = (a2[0] * ny - a2[1] * nx) / det;
+    A2[0] = (ny * a1[2] - nz * a1[1]) / det;
+    A2[1] = (nz * a1[0] - nx * a1[2]) / det;
+    A2[2] = (nx * a1[1] - ny * a1[0]) / det;
+    const double i11 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+    const double i12 = A1[0] * A2[0] + A1[1] * A2[1] + A1[2] * A2[2];
+    const double i22 = A2[0] * A2[0] + A2[1] * A2[1] + A2[2] * A2[2];
     const double G1uu = A1[0] * xuu[0] + A1[1] * xuu[1] + A1[2] * xuu[2];
     const double G1uv = A1[0] * xuv[0] + A1[1] * xuv[1] + A1[2] * xuv[2];
     const double G1vv = A1[0] * xvv[0] + A1[1] * xvv[1] + A1[2] * xvv[2];
@@ -164,9 +170,10 @@ __global__ void __launch_bounds__(256) k_eval(Elems el, const int32_t* __restric
         T[(nc - 1) * m + jl] = lap;
     }
     if (lane == 0) {
-        xout[pt * 3 + 0] = g[0];
-        xout[pt * 3 + 1] = g[1];
-        xout[pt * 3 + 2] = g[2];
+        const double* ref = el.geom_ref + 3 * (int64_t)e;
+        xout[pt * 3 + 0] = ref[0] + g[0];
+        xout[pt * 3 + 1] = ref[1] + g[1];
+        xout[pt * 3 + 2] = ref[2] + g[2];
         if (gauss) wout[pt] = wq * sqrt(det);
     }
 }
@@ -240,6 +247,100 @@ cudaError_t launch_split_f32(const double* src, float2* dst, int64_t n, cudaStre
     if (n == 0) return cudaSuccess;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
     k_split_f32<<<blocks, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace wqd
+
+namespace wqd {
+
+// ---------------------------------------------------------------- heat fields
+// Point data of the nonlinear heat problem (paper Sec. 5, theta = 1):
+//   u_q = sum_j N_j(x_q) u_j, grad u_q likewise, uo_q from u_old;
+//   kappa_q = k0 + k2 u_q^2 (coefficient of the tangent S, Eq. S),
+//   g[0][q] = (u_q - uo_q) / dt - f,   g[1 + d][q] = kappa_q d_d u_q
+// (the residual R_A = Q_A((u - u_old)/dt - f) + sum_d Q^d_A(kappa d_d u)).
+__global__ void __launch_bounds__(256) k_heat_fields(Elems el, const int32_t* __restrict__ pt_elem,
+                                                     const int32_t* __restrict__ fns,
+                                                     const int64_t* __restrict__ fn_ptr, int64_t Q,
+                                                     const double* __restrict__ table, const double* __restrict__ u,
+                                                     const double* __restrict__ uo, double dt, double k0, double k2,
+                                                     double f, double* __restrict__ kappa, double* __restrict__ g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t pt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (pt >= Q) return;
+    const int e = pt_elem[pt];
+    const int m = el.m[e], nc = el.nc;
+    const double* T = table + el.bt_ptr[e] + (pt - el.pt_ptr[e]) * nc * m;
+    double v = 0, vo = 0, gx = 0, gy = 0, gz = 0;
+    for (int jl = lane; jl < m; jl += 32) {
+        const int j = fns[fn_ptr[e] + jl];
+        const double uj = u[j];
+        v += uj * T[jl];
+        vo += uo[j] * T[jl];
+        gx += uj * T[m + jl];
+        gy += uj * T[2 * m + jl];
+        if (nc == 5) gz += uj * T[3 * m + jl];
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+        vo += __shfl_xor_sync(0xffffffffu, vo, off);
+        gx += __shfl_xor_sync(0xffffffffu, gx, off);
+        gy += __shfl_xor_sync(0xffffffffu, gy, off);
+        gz += __shfl_xor_sync(0xffffffffu, gz, off);
+    }
+    if (lane == 0) {
+        const double k = k0 + k2 * v * v;
+        kappa[pt] = k;
+        g[pt] = (v - vo) / dt - f;
+        g[Q + pt] = k * gx;
+        g[2 * Q + pt] = k * gy;
+        if (nc == 5) g[3 * Q + pt] = k * gz;
+    }
+}
+
+cudaError_t launch_heat_fields(const Elems& el, const int32_t* pt_elem, const int32_t* fns, const int64_t* fn_ptr,
+                               int64_t Q, const double* table, const double* u, const double* uo, double dt, double k0,
+                               double k2, double f, double* kappa, double* g, cudaStream_t st) {
+    if (Q == 0) return cudaSuccess;
+    const int threads = 256, wpb = threads / 32;
+    k_heat_fields<<<(unsigned)((Q + wpb - 1) / wpb), threads, 0, st>>>(el, pt_elem, fns, fn_ptr, Q, table, u, uo, dt,
+                                                                        k0, k2, f, kappa, g);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- WQ apply
+// Matrix-free WQ functional: y_i = sum_t sum_{q in pts(supp N_i)} w^{c_t}_iq g_t(x_q),
+// one warp per row, lanes over the points of each support element.
+__global__ void __launch_bounds__(256) k_apply(Rows rw, const int4* __restrict__ desc, int nt, int4 wc4,
+                                               const double* __restrict__ W, int nwc, const double* __restrict__ g,
+                                               int64_t Q, double* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= rw.n) return;
+    const int wc[4] = {wc4.x, wc4.y, wc4.z, wc4.w};
+    int64_t woff = rw.w_ptr[i];
+    double acc = 0.0;
+    for (int64_t s = rw.supp_ptr[i]; s < rw.supp_ptr[i + 1]; ++s) {
+        const int4 d = desc[s];
+        const int P = (d.z >> 8) & 255;
+        for (int q = lane; q < P; q += 32) {
+            const double* wrow = W + (woff + q) * nwc;
+            for (int t = 0; t < nt; ++t) acc += wrow[wc[t]] * g[t * Q + d.y + q];
+        }
+        woff += P;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) y[i] = acc;
+}
+
+cudaError_t launch_apply(const Rows& rw, const int4* desc, int nt, int4 wc4, const double* W, int nwc,
+                         const double* g, int64_t Q, double* y, cudaStream_t st) {
+    if (rw.n == 0) return cudaSuccess;
+    const int threads = 256, wpb = threads / 32;
+    k_apply<<<(unsigned)((rw.n + wpb - 1) / wpb), threads, 0, st>>>(rw, desc, nt, wc4, W, nwc, g, Q, y);
     return cudaGetLastError();
 }
 

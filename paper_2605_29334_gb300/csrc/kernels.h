@@ -44,9 +44,18 @@ cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm,
 // FP32 contraction with hi/lo split products and TwoSum accumulation: tables and
 // weights as float2 (hi, lo); the coefficient is split into coef2_buf [n_points]
 // by a small pre-kernel (two launches); float CSR values.
-cudaError_t launch_rowasm_f32(const Rows& rw, const int4* desc, const Terms& tm, int nc, const float2* table2,
-                              const float2* W2, int nwc, const double* coef, float2* coef2_buf, int64_t n_points,
-                              float* vals, int max_n_i, int n_sm, cudaStream_t st);
+// With a chunk plan and at most two terms the shared-memory staged kernel runs.
+// compensated = false: split products, plain FP32 sums (only with <= 2 terms).
+cudaError_t launch_rowasm_f32(const Rows& rw, const int4* desc, const Chunks* ch, const Terms& tm, int nc,
+                              const float2* table2, const float2* W2, int nwc, const double* coef, float2* coef2_buf,
+                              int64_t n_points, float* vals, int max_n_i, int n_sm, bool compensated,
+                              cudaStream_t st);
+
+// FP32 element-major assembly: element tiles into the slot buffer, then one
+// compensated sum per CSR entry; 1..4 terms; compensated = TwoSum accumulation.
+cudaError_t launch_elem_f32(const ElemPlan& ep, int64_t nnz, const Terms& tm, int nc, const float2* table2,
+                            const float2* W2, int nwc, const double* coef, float* vals, bool compensated,
+                            cudaStream_t st);
 
 // Truncated-SVD weights of every row for one component (Sec. 4.3):
 //   table comp tc gives A, table comp 0 gives Z, mom [nnz] gives b;
@@ -61,6 +70,15 @@ cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, in
 cudaError_t launch_interp(const Elems& el, const int32_t* pt_elem, const int32_t* fns,
                           const int64_t* fn_ptr, int64_t Q, const double* table, const double* u,
                           double* uq, double* grad, cudaStream_t st);
+
+// Heat point fields (Sec. 5): kappa [Q] = k0 + k2 u^2; g [1 + dim][Q] residual data.
+cudaError_t launch_heat_fields(const Elems& el, const int32_t* pt_elem, const int32_t* fns, const int64_t* fn_ptr,
+                               int64_t Q, const double* table, const double* u, const double* uo, double dt, double k0,
+                               double k2, double f, double* kappa, double* g, cudaStream_t st);
+
+// Matrix-free WQ functional y_i = sum_t sum_q w^{wc_t}_iq g[t][q] (weight columns in wc4, nt <= 4).
+cudaError_t launch_apply(const Rows& rw, const int4* desc, int nt, int4 wc4, const double* W, int nwc,
+                         const double* g, int64_t Q, double* y, cudaStream_t st);
 
 // Convert double arrays to (hi, lo) float pairs.
 cudaError_t launch_split_f32(const double* src, float2* dst, int64_t n, cudaStream_t st);

@@ -42,7 +42,7 @@ struct wq_rule {
     int32_t *d_m = nullptr, *d_nsub = nullptr, *d_side = nullptr, *d_pt_elem = nullptr, *d_gp_elem = nullptr;
     int64_t *d_coef_ptr = nullptr, *d_sub_ptr = nullptr, *d_pt_ptr = nullptr, *d_gp_ptr = nullptr;
     int64_t *d_bt_ptr = nullptr, *d_gbt_ptr = nullptr, *d_fn_ptr = nullptr;
-    double *d_coef = nullptr, *d_geom = nullptr, *d_table = nullptr, *d_gtable = nullptr;
+    double *d_coef = nullptr, *d_geom = nullptr, *d_geom_ref = nullptr, *d_table = nullptr, *d_gtable = nullptr;
     double *d_x = nullptr, *d_gx = nullptr, *d_gw = nullptr;
     int32_t *d_row_ptr = nullptr, *d_col = nullptr, *d_supp = nullptr, *d_fns = nullptr;
     int64_t *d_supp_ptr = nullptr, *d_pos_ptr = nullptr, *d_w_ptr = nullptr;
@@ -50,6 +50,15 @@ struct wq_rule {
     int4 *d_desc_wq = nullptr, *d_desc_gq = nullptr;
 
     float2* d_coef2 = nullptr;
+    int32_t *d_ch_row_ptr = nullptr, *d_ch_u_ptr = nullptr;
+    int4 *d_ch_u = nullptr, *d_ch_rows = nullptr, *d_ch_info = nullptr;
+    uint16_t* d_ch_sloc = nullptr;
+    wqd::Chunks ch{};
+    int4* d_el_item = nullptr;
+    int32_t *d_el_item_k = nullptr, *d_ew_off = nullptr, *d_scat = nullptr, *d_gptr = nullptr;
+    float2* d_kscr = nullptr;
+    int64_t kscr_len = 0;
+    wqd::ElemPlan ep{};
     int n_sm = 1;
     int max_P = 0;          // most WQ points on one element (the FP32 kernel stages <= 64 per window)
     uint16_t* d_pos = nullptr;

@@ -58,7 +58,8 @@ struct BasisHost {
     std::vector<int32_t> fns;           // function ids per element, ascending
     std::vector<int64_t> coef_ptr;      // [E+1] offsets into coef
     std::vector<double> coef;           // per element [m][nsub][4][4]
-    std::vector<double> geom;           // per element [nsub][4][4][3], offsets 48*sub_ptr
+    std::vector<double> geom;           // per element [nsub][4][4][3] relative to geom_ref, offsets 48*sub_ptr
+    std::vector<double> geom_ref;       // [E][3] control point of the element's first function
     std::vector<int64_t> sub_ptr;       // [E+1] prefix sums of nsub
     std::vector<double> ctrl;           // [n][3]
     std::vector<int64_t> raw_ids;       // [n]

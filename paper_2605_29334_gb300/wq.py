@@ -20,7 +20,7 @@ WQ_OK, WQ_ERR_ARG, WQ_ERR_MESH, WQ_ERR_ILLPOSED, WQ_ERR_NOT_CONVERGED, WQ_ERR_NO
     WQ_ERR_OOM, WQ_ERR_NO_DEVICE = range(9)
 OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S = range(4)
 COMP_N, COMP_X, COMP_Y, COMP_Z, COMP_LAP = range(5)
-PREC_F64, PREC_F32 = 0, 1
+PREC_F64, PREC_F32, PREC_F32_FAST = 0, 1, 2
 TYPE_NAMES = ["passive", "boundary", "irregular", "enriched_transition", "transition", "enriched_regular", "regular"]
 
 
@@ -80,6 +80,10 @@ EXPORTS = {
     "wq_assemble_host": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
                                    C.c_void_p]),
     "wq_rule_weights_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "wq_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "wq_heat_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "wq_basis_functions": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -169,6 +173,7 @@ class Basis:
         ctx.check(lib().wq_basis_info_get(h, C.byref(info)))
         self.info = info
         self.n, self.E, self.nnz = info.n_functions, info.n_elements, info.nnz
+        self.dim = int(mesh.get("dim", 2))
 
     def element(self, e):
         face, typ, m, ns = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
@@ -189,6 +194,11 @@ class Basis:
         col = np.zeros(self.nnz, dtype=np.int32)
         self.ctx.check(lib().wq_basis_pattern(self.h, _ptr(rp), _ptr(col)))
         return rp, col
+
+    def raw_ids(self):
+        out = np.zeros(self.n, dtype=np.int64)
+        self.ctx.check(lib().wq_basis_functions(self.h, _ptr(out)))
+        return out
 
     def point_counts(self):
         side = np.zeros(self.E, dtype=np.int32)
@@ -219,6 +229,7 @@ class Rule:
         self.ctx.check(lib().wq_rule_info_get(h, C.byref(info)))
         self.info = info
         self.Q, self.G, self.n, self.nnz = info.n_points, info.n_gauss, basis.n, basis.nnz
+        self.basis_dim = basis.dim
 
     def points(self):
         p, q = C.c_void_p(), C.c_int64()
@@ -287,6 +298,30 @@ class Rule:
         self.ctx.check(lib().wq_interp(self.h, C.c_void_p(u.data_ptr()), C.c_void_p(uq.data_ptr()),
                                        C.c_void_p(gr.data_ptr()), _stream_handle(stream)))
         return uq, gr
+
+    def apply(self, comps, g, out=None, stream=None):
+        """y_i = sum_t sum_q w^{comps[t]}_iq g[t][q]; g: device tensor [len(comps), Q]."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        hc = np.ascontiguousarray(comps, dtype=np.int32)
+        self.ctx.check(lib().wq_apply(self.h, len(hc), _ptr(hc), C.c_void_p(g.data_ptr()), C.c_void_p(out.data_ptr()),
+                                      _stream_handle(stream)))
+        return out
+
+    def heat_fields(self, u, u_old, dt, k0=1.0, k2=1.0, f=0.0, kappa=None, g=None, stream=None):
+        """kappa(u) = k0 + k2 u^2 at the WQ points and the residual point data g [1 + dim, Q]."""
+        import torch
+        ng = 1 + (3 if self.basis_dim == 3 else 2)
+        if kappa is None:
+            kappa = torch.empty(self.Q, dtype=torch.float64, device="cuda")
+        if g is None:
+            g = torch.empty((ng, self.Q), dtype=torch.float64, device="cuda")
+        self.ctx.check(lib().wq_heat_fields(self.h, C.c_void_p(u.data_ptr()), C.c_void_p(u_old.data_ptr()),
+                                            float(dt), float(k0), float(k2), float(f),
+                                            C.c_void_p(kappa.data_ptr()), C.c_void_p(g.data_ptr()),
+                                            _stream_handle(stream)))
+        return kappa, g
 
     def assemble_host(self, op, h_coef, alpha=0.0, prec=PREC_F64, out=None, stream=None):
         h_coef = np.ascontiguousarray(h_coef, dtype=np.float64)

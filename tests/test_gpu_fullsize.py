@@ -1,0 +1,154 @@
+"""Full-size parity on sampled rows, through the C ABI, in the launch
+configuration the benchmark times.
+
+Workloads (seeded, synthetic):
+  * Poisson stiffness on the 8x5-core, 12-EP planar mesh refined 4 times
+    (10,240 elements) with a log-normal kappa -- the benchmark workload;
+  * bilaplacian + mass on the cube-sphere surface, 6 x 64 x 64 elements;
+  * the heat tangent S (mass / dt + stiffness with kappa(u) = 1 + u^2) on the
+    12-EP mesh refined 5 times (40,960 elements).
+The oracle computes a sampled row from scratch (its own basis, points, Gauss
+moments of that row, truncated SVD, row sum), so rows near EPs, boundary rows
+and regular rows are checked without assembling the whole oracle matrix.
+FP64 bar: 1e-11 relative to the largest sampled entry, or 4x the oracle's own
+spread (the largest of: two LAPACK SVD drivers, two seeded 16-ulp perturbations
+of every weight solve's inputs -- the size of the differences between the GPU's
+and the oracle's basis tables); FP32 (compensated): 1e-6 against the GPU's FP64
+result and max(1e-6, the FP64 bar) against the oracle.
+"""
+import numpy as np
+import pytest
+
+from wq_synth import meshes
+
+pytestmark = pytest.mark.gpu
+
+COMP_ID = {"N": 0, "x": 1, "y": 2, "z": 3, "lap": 4}
+
+
+def _sample_rows(B, rng, k=8):
+    from oracle.topology import REGULAR, BOUNDARY
+    et = B.etype
+    near_ep = [i for i in range(B.n) if any(B.topo.irregular[B.elements[e]] for e in B.supp[i])]
+    bnd = [i for i in range(B.n) if any(et[e] == BOUNDARY for e in B.supp[i])]
+    reg = [i for i in range(B.n) if all(et[e] == REGULAR for e in B.supp[i])]
+    enr = [i for i in range(B.n) if all(B.topo.enriched[B.elements[e]] for e in B.supp[i])]
+    out = set()
+    for group in (near_ep, bnd, reg, enr):
+        if group:
+            out.update(rng.choice(group, size=min(k, len(group)), replace=False).tolist())
+    return sorted(out)
+
+
+def _oracle_row(B, side, row_ptr, col, i, terms, coef_fn, driver, rng=None):
+    """Row i of the WQ operator sum_t (comp_t, a_t) from scratch (oracle steps)."""
+    from oracle.geometry import eval_element
+    from oracle.gq import gauss_data, comp_values
+    from oracle.wq import local_points, tsvd_weights
+    cols = col[row_ptr[i]:row_ptr[i + 1]]
+    datas, gdatas = {}, {}
+    for e in B.supp[i]:
+        datas[e] = eval_element(B, e, theta=local_points(int(side[e])))
+        gdatas[e] = gauss_data(B, e)
+    row = np.zeros(len(cols))
+    for comp, scale in terms:
+        # moments b (Gauss, c = 1) of row i for this component
+        b = np.zeros(len(cols))
+        blocks, zs = [], []
+        for e in B.supp[i]:
+            fns = B.elem_fns[e]
+            li = int(np.nonzero(fns == i)[0][0])
+            g = gdatas[e]
+            Dg = comp_values(g, comp)
+            b[np.searchsorted(cols, fns)] += Dg @ (g["w"] * Dg[li])
+            d = datas[e]
+            D = comp_values(d, comp)
+            blk = np.zeros((len(cols), D.shape[1]))
+            blk[np.searchsorted(cols, fns)] = D
+            blocks.append(blk)
+            zs.append(d["N"][li])
+        A = np.concatenate(blocks, axis=1)
+        z = np.concatenate(zs)
+        if rng is not None:                       # 16-ulp perturbation of the solve's inputs
+            u = 16 * 2.0 ** -52
+            A = A * (1 + u * rng.uniform(-1, 1, A.shape))
+            z = z * (1 + u * rng.uniform(-1, 1, z.shape))
+            b = b * (1 + u * rng.uniform(-1, 1, b.shape))
+        w, _ = tsvd_weights(A, z, b, 1e-12, driver)
+        off = 0
+        for e in B.supp[i]:
+            d = datas[e]
+            P = d["x"].shape[0]
+            a = coef_fn(d["x"]) if scale is None else np.full(P, scale)
+            row[np.searchsorted(cols, B.elem_fns[e])] += comp_values(d, comp) @ (w[off:off + P] * a)
+            off += P
+    return row
+
+
+def _run(W, mesh, comps, op, terms, coef_fn, alpha, precs, seed):
+    import torch
+    from oracle.basis import Basis
+    from oracle import gq, wq as owq
+    ctx = W.Context(0)
+    b = W.Basis(ctx, mesh)
+    r = W.Rule(b, comps=[COMP_ID[c] for c in comps])
+    kap = torch.tensor(coef_fn(r.points().cpu().numpy()), device="cuda")
+    got = {p: r.assemble(op, kap, alpha=alpha, prec=p).cpu().numpy().astype(np.float64) for p in precs}
+    B = Basis(mesh)
+    row_ptr, col = gq.pattern(B)
+    side = owq.point_counts(B, row_ptr)
+    assert np.array_equal(side, b.point_counts())
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rows = _sample_rows(B, rng)
+    refs, others = {}, [{}, {}, {}]
+    prng = np.random.Generator(np.random.PCG64(seed + 1000))
+    for i in rows:
+        refs[i] = _oracle_row(B, side, row_ptr, col, i, terms, coef_fn, "gesdd")
+        others[0][i] = _oracle_row(B, side, row_ptr, col, i, terms, coef_fn, "gesvd")
+        others[1][i] = _oracle_row(B, side, row_ptr, col, i, terms, coef_fn, "gesdd", prng)
+        others[2][i] = _oracle_row(B, side, row_ptr, col, i, terms, coef_fn, "gesdd", prng)
+    scale = max(np.max(np.abs(v)) for v in refs.values())
+    spread = max(max(np.max(np.abs(refs[i] - o[i])) for i in rows) for o in others) / scale
+    tol64 = max(1e-11, 4 * spread)
+    err = {p: max(np.max(np.abs(got[p][row_ptr[i]:row_ptr[i + 1]] - refs[i])) for i in rows) / scale for p in precs}
+    assert err[W.PREC_F64] < tol64, (err, tol64, len(rows))
+    for p in precs:
+        if p != W.PREC_F64:
+            arith = max(np.max(np.abs(got[p][row_ptr[i]:row_ptr[i + 1]] - got[W.PREC_F64][row_ptr[i]:row_ptr[i + 1]]))
+                        for i in rows) / scale
+            assert arith < 1e-6, (p, arith)
+            assert err[p] < max(1e-6, tol64), (p, err, tol64)
+    return rows
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    from paper_2605_29334_gb300 import build, wq
+    build.build()
+    assert torch.cuda.is_available()
+    return wq
+
+
+def test_fullsize_poisson_stiffness(W):
+    mesh = meshes.rotated(nx=8, ny=5, n_ep=12, levels=4, seed=2001)
+    field = meshes.LogNormalField(2101, mesh["xyz"].min(0), mesh["xyz"].max(0), nk=16, sigma=0.5)
+    rows = _run(W, mesh, ["x", "y"], W.OP_STIFF, [("x", None), ("y", None)],
+                field, 0.0, [W.PREC_F64, W.PREC_F32], seed=11)
+    assert len(rows) >= 20
+
+
+def test_fullsize_sphere_biharmonic(W):
+    mesh = meshes.cube_sphere(pre=3, levels=3)
+    coef = lambda x: 1.0 + 0.25 * x[:, 0] * x[:, 1] + 0.1 * x[:, 2]
+    _run(W, mesh, ["N", "lap"], W.OP_BIHARM, [("lap", None)], coef, 0.0, [W.PREC_F64, W.PREC_F32], seed=12)
+    _run(W, mesh, ["N", "lap"], W.OP_MASS, [("N", None)], coef, 0.0, [W.PREC_F64, W.PREC_F32], seed=13)
+
+
+def test_fullsize_heat_tangent(W):
+    mesh = meshes.rotated(nx=8, ny=5, n_ep=12, levels=5, seed=2001)
+    u0 = meshes.gaussian_bumps(4001, mesh["xyz"].min(0), mesh["xyz"].max(0))
+    kap = lambda x: 1.0 + u0(x) ** 2            # kappa(u) at the points, u a smooth field
+    dt = 1e-2
+    _run(W, mesh, ["N", "x", "y"], W.OP_HEAT_S, [("N", 1.0 / dt), ("x", None), ("y", None)], kap, 1.0 / dt,
+         [W.PREC_F64, W.PREC_F32], seed=14)

@@ -65,7 +65,7 @@ def _area_green(B):
                            3 * thc[:, 0] ** 2 * (1 - thc[:, 0]), thc[:, 0] ** 3], -1)
             Bv = np.stack([(1 - thc[:, 1]) ** 3, 3 * thc[:, 1] * (1 - thc[:, 1]) ** 2,
                            3 * thc[:, 1] ** 2 * (1 - thc[:, 1]), thc[:, 1] ** 3], -1)
-            X = np.einsum("ijk,pi,pj->pk", net[0], Bu, Bv)
+            X = B.geom_ref[e][None, :] + np.einsum("ijk,pi,pj->pk", net[0], Bu, Bv)
             dx = X.imag / h
             x = d["x"]
             area += 0.5 * np.sum(ws * (x[:, 0] * dx[:, 1] - x[:, 1] * dx[:, 0]))

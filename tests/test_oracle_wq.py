@@ -132,7 +132,7 @@ def test_assembly_constant_coefficient_is_gauss(disk_rule):
         A1 = R.assemble([(c, ones)])
         assert np.max(np.abs(A1 - G)) <= 1e-12 * np.max(np.abs(G))
         A3 = R.assemble([(c, 3.0 * ones)])
-        assert np.max(np.abs(A3 - 3 * G)) <= 1e-12 * np.max(np.abs(G))
+        assert np.max(np.abs(A3 - 3 * G)) <= 1e-12 * np.max(np.abs(3 * G))
 
 
 def test_assembly_rowsums_and_mass_sums(disk_rule):
