@@ -263,7 +263,6 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
         gbt_ptr[e + 1] = gbt_ptr[e] + 16LL * nsub[e] * nc * m[e];
     }
     R->Q = pt_ptr[E];
-    for (int64_t e = 0; e < E; ++e) R->max_P = std::max<int>(R->max_P, side[e] * side[e]);
     R->G = gp_ptr[E];
     std::vector<int32_t> pt_elem(R->Q), gp_elem(R->G);
     for (int64_t e = 0; e < E; ++e) {
@@ -337,104 +336,44 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
             desc_gq[s] = make_int4((int)gbt_ptr[e], (int)gp_ptr[e], m[e] | (16 * nsub[e]) << 8 | il[s] << 16,
                                    (int)pos_ptr[s]);
         }
-    // staged-FP32 chunk plan (sized for two weight/table components)
-    std::vector<int32_t> ch_row_ptr(1, 0), ch_u_ptr(1, 0);
-    std::vector<int4> ch_u, ch_rows(n), ch_info;
-    std::vector<uint16_t> ch_sloc(R->nsupp);
-    int ch_data_max = 0;
-    {
-        const int64_t BUDGET = 80 * 1024;
-        std::vector<int32_t> uslot(E, -1);
-        std::vector<int32_t> cur_u;
-        int64_t k = 0;
-        auto bytes_of = [](int64_t tab2, int64_t sv2, int64_t nsup, int64_t npos, int64_t nu) {
-            // regions: union info, tables, s-values (float2), local indices, positions (uint16)
-            return (int64_t)(nu * 16 + ((tab2 + sv2) * 8) + ((nsup + npos) * 2 + 15) / 16 * 16) + 16;
-        };
-        while (k < n) {
-            int64_t tab2 = 0, sv2 = 0, nsup = 0, npos = 0;
-            cur_u.clear();
-            const int64_t kstart = k;
-            while (k < n) {
-                const int32_t i = order[k];
-                int64_t add_tab = 0, add_u = 0, add_sv = 0, add_sup = 0, add_pos = 0;
-                for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
-                    const int32_t e = B.supp[s];
-                    const int64_t P = (int64_t)side[e] * side[e];
-                    if (uslot[e] < 0) {   // a support lists each element once
-                        add_tab += P * m[e] * 2;
-                        add_u += 1;
-                    }
-                    add_sv += P * 2;
-                    add_sup += 1;
-                    add_pos += m[e];
-                }
-                const int64_t nb = bytes_of(tab2 + add_tab, sv2 + add_sv, nsup + add_sup, npos + add_pos,
-                                            (int64_t)cur_u.size() + add_u);
-                if (k > kstart && (nb > BUDGET || k - kstart >= 64)) break;
-                // admit row
-                ch_rows[k] = make_int4(i, (int)sv2, (int)npos, (int)nsup);
-                for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
-                    const int32_t e = B.supp[s];
-                    if (uslot[e] < 0) {
-                        uslot[e] = (int32_t)cur_u.size();
-                        cur_u.push_back(e);
-                    }
-                    ch_sloc[s] = (uint16_t)uslot[e];
-                }
-                tab2 += add_tab;
-                sv2 += add_sv;
-                nsup += add_sup;
-                npos += add_pos;
-                ++k;
-            }
-            int64_t uoff = 0;
-            for (int32_t e : cur_u) {
-                const int64_t P = (int64_t)side[e] * side[e];
-                ch_u.push_back(make_int4((int)bt_ptr[e], m[e] | (int)P << 8, (int)uoff, 0));
-                uoff += P * m[e] * 2;
-                uslot[e] = -1;
-            }
-            ch_info.push_back(make_int4((int)tab2, (int)sv2, (int)nsup, (int)npos));
-            ch_row_ptr.push_back((int32_t)k);
-            ch_u_ptr.push_back((int32_t)ch_u.size());
-            ch_data_max = std::max<int>(ch_data_max, (int)bytes_of(tab2, sv2, nsup, npos, (int64_t)cur_u.size()));
-        }
-        ch_data_max = (ch_data_max + 15) / 16 * 16;
+    // element-major FP32 plan: 16 x 16 tiles of the element blocks (elements with
+    // more chunks of points first), the element-major row of every weight row, and
+    // the slot of every block entry, grouped by CSR entry in support order
+    std::vector<int64_t> kptr(E + 1, 0), wbase(E + 1, 0);
+    for (int64_t e = 0; e < E; ++e) {
+        kptr[e + 1] = kptr[e] + (int64_t)m[e] * m[e];
+        wbase[e + 1] = wbase[e] + (int64_t)m[e] * side[e] * side[e];
     }
-    // element-major FP32 plan: 16 x 16 tiles of the element blocks (larger elements
-    // first), the weight row of each (function, element) pair, and the slot of every
-    // block entry, grouped by CSR entry in the order of the elements in supp N_i
-    std::vector<int64_t> kptr(E + 1, 0);
-    for (int64_t e = 0; e < E; ++e) kptr[e + 1] = kptr[e] + (int64_t)m[e] * m[e];
-    if (kptr[E] > INT32_MAX || w_ptr[n] > INT32_MAX)
+    if (kptr[E] > INT32_MAX || wbase[E] > INT32_MAX)
         return bail(fail(ctx, WQ_ERR_ARG, "mesh too large for 32-bit element block offsets"));
-    std::vector<int4> el_item;
-    std::vector<int32_t> el_item_k;
-    {
+    std::vector<int4> it_wq, it_gq;
+    std::vector<int32_t> kb_wq, kb_gq;
+    auto make_items = [&](bool gauss, std::vector<int4>& item, std::vector<int32_t>& kb) {
+        auto npts = [&](int64_t e) { return gauss ? 16 * nsub[e] : side[e] * side[e]; };
+        auto chunks = [&](int64_t e) { return (npts(e) + 7) / 8; };
         std::vector<int32_t> by_work(E);
         for (int64_t e = 0; e < E; ++e) by_work[e] = (int32_t)e;
-        auto work = [&](int32_t e) { return (int64_t)((m[e] + 15) / 16) * ((int64_t)side[e] * side[e] + 7) / 8; };
         std::stable_sort(by_work.begin(), by_work.end(), [&](int32_t x, int32_t y) {
-            return (side[x] * side[x] + 7) / 8 > (side[y] * side[y] + 7) / 8 ||
-                   ((side[x] * side[x] + 7) / 8 == (side[y] * side[y] + 7) / 8 && work(x) > work(y));
+            return chunks(x) * ((m[x] + 15) / 16) > chunks(y) * ((m[y] + 15) / 16);
         });
         for (int32_t e : by_work)
             for (int a0 = 0; a0 < m[e]; a0 += 16)
                 for (int b0 = 0; b0 < m[e]; b0 += 16) {
-                    el_item.push_back(make_int4((int)bt_ptr[e], (int)pt_ptr[e],
-                                                m[e] | (side[e] * side[e]) << 8 | (a0 / 16) << 16 | (b0 / 16) << 20,
-                                                (int)B.fn_ptr[e]));
-                    el_item_k.push_back((int32_t)kptr[e]);
+                    item.push_back(make_int4(gauss ? (int)gbt_ptr[e] : (int)bt_ptr[e],
+                                             gauss ? (int)gp_ptr[e] : (int)pt_ptr[e],
+                                             m[e] | npts(e) << 8 | (a0 / 16) << 16 | (b0 / 16) << 20,
+                                             (int)wbase[e]));
+                    kb.push_back((int32_t)kptr[e]);
                 }
-    }
-    std::vector<int32_t> ew_off(B.fn_ptr[E]), scat(kptr[E]), gptr(R->nnz + 1, 0);
+    };
+    make_items(false, it_wq, kb_wq);
+    make_items(true, it_gq, kb_gq);
+    std::vector<int32_t> wrow_dst(w_ptr[n]), scat(kptr[E]), gptr(R->nnz + 1, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t r = w_ptr[i];
         for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
             const int32_t e = B.supp[s];
-            ew_off[B.fn_ptr[e] + il[s]] = (int32_t)r;
-            r += (int64_t)side[e] * side[e];
+            for (int q = 0; q < side[e] * side[e]; ++q) wrow_dst[r++] = (int32_t)(wbase[e] + (int64_t)q * m[e] + il[s]);
             for (int b = 0; b < m[e]; ++b) ++gptr[B.row_ptr[i] + pos[pos_ptr[s] + b] + 1];
         }
     }
@@ -466,20 +405,19 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
         !upload(R, R->d_pos_ptr, pos_ptr, sst) || !upload(R, R->d_pos, pos, sst) || !upload(R, R->d_il, il, sst) ||
         !upload(R, R->d_w_ptr, w_ptr, sst) || !upload(R, R->d_fn_ptr, B.fn_ptr, sst) ||
         !upload(R, R->d_order, order, sst) || !upload(R, R->d_desc_wq, desc_wq, sst) ||
-        !upload(R, R->d_desc_gq, desc_gq, sst) || !upload(R, R->d_ch_row_ptr, ch_row_ptr, sst) ||
-        !upload(R, R->d_ch_u_ptr, ch_u_ptr, sst) || !upload(R, R->d_ch_u, ch_u, sst) ||
-        !upload(R, R->d_ch_rows, ch_rows, sst) || !upload(R, R->d_ch_info, ch_info, sst) ||
-        !upload(R, R->d_ch_sloc, ch_sloc, sst) ||
-        !upload(R, R->d_fns, B.fns, sst) || !upload(R, R->d_el_item, el_item, sst) ||
-        !upload(R, R->d_el_item_k, el_item_k, sst) || !upload(R, R->d_ew_off, ew_off, sst) ||
-        !upload(R, R->d_scat, scat, sst) || !upload(R, R->d_gptr, gptr, sst))
+        !upload(R, R->d_desc_gq, desc_gq, sst) || !upload(R, R->d_fns, B.fns, sst) ||
+        !upload(R, R->d_it_wq, it_wq, sst) || !upload(R, R->d_kb_wq, kb_wq, sst) ||
+        !upload(R, R->d_it_gq, it_gq, sst) || !upload(R, R->d_kb_gq, kb_gq, sst) ||
+        !upload(R, R->d_wrow_dst, wrow_dst, sst) || !upload(R, R->d_scat, scat, sst) ||
+        !upload(R, R->d_gptr, gptr, sst))
         return bail(sst);
     if (!dalloc(R, R->d_table, (size_t)bt_ptr[E], sst) || !dalloc(R, R->d_gtable, (size_t)gbt_ptr[E], sst) ||
         !dalloc(R, R->d_x, (size_t)R->Q * 3, sst) || !dalloc(R, R->d_gx, (size_t)R->G * 3, sst) ||
         !dalloc(R, R->d_gw, (size_t)R->G, sst) || !dalloc(R, R->d_W, (size_t)R->sum_r * R->nwc, sst) ||
         !dalloc(R, R->d_status, 1, sst) || !dalloc(R, R->d_table2, (size_t)bt_ptr[E], sst) ||
+        !dalloc(R, R->d_gtable2, (size_t)gbt_ptr[E], sst) ||
         !dalloc(R, R->d_W2, (size_t)R->sum_r * R->nwc, sst) || !dalloc(R, R->d_coef_stage, (size_t)R->Q, sst) ||
-        !dalloc(R, R->d_vals_stage, (size_t)R->nnz, sst) || !dalloc(R, R->d_coef2, (size_t)R->Q, sst) ||
+        !dalloc(R, R->d_vals_stage, (size_t)R->nnz, sst) ||
         !dalloc(R, R->d_kscr, (size_t)std::max<int64_t>(R->kscr_len, 1), sst))
         return bail(sst);
     for (int c = 0; c < 5; ++c)
@@ -523,21 +461,9 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     rw.il = R->d_il;
     rw.w_ptr = R->d_w_ptr;
     rw.order = R->d_order;
-    R->ep.n_items = (int64_t)el_item.size();
-    R->ep.item = R->d_el_item;
-    R->ep.item_k = R->d_el_item_k;
-    R->ep.ew_off = R->d_ew_off;
-    R->ep.scat = R->d_scat;
-    R->ep.gptr = R->d_gptr;
-    R->ep.kscr = R->d_kscr;
-    R->ch.n_chunks = (int64_t)ch_info.size();
-    R->ch.row_ptr = R->d_ch_row_ptr;
-    R->ch.u_ptr = R->d_ch_u_ptr;
-    R->ch.u = R->d_ch_u;
-    R->ch.rows = R->d_ch_rows;
-    R->ch.sloc = R->d_ch_sloc;
-    R->ch.info = R->d_ch_info;
-    R->ch.data_bytes = ch_data_max;
+    R->it_wq = {(int64_t)it_wq.size(), R->d_it_wq, R->d_kb_wq};
+    R->it_gq = {(int64_t)it_gq.size(), R->d_it_gq, R->d_kb_gq};
+    R->ep = {R->d_scat, R->d_gptr, R->d_kscr};
 
     // Gauss-Legendre 4-point rule on [0, 1] (closed form)
     {
@@ -598,7 +524,8 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     }
     // FP32 split copies for the mixed-precision assembly
     if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_table, R->d_table2, bt_ptr[E], st);
-    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_W, R->d_W2, R->sum_r * R->nwc, st);
+    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gtable, R->d_gtable2, gbt_ptr[E], st);
+    if (ce == cudaSuccess) ce = wqd::launch_split_rows(R->d_W, R->d_wrow_dst, R->d_W2, R->sum_r, R->nwc, R->n_sm, st);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev1, st);
     unsigned hstat = 0;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstat, R->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -695,17 +622,8 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
         e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_wq, tm, rule->nc, 0, rule->d_table, rule->d_W, rule->nwc,
                                    nullptr, (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
     else if (prec == WQ_PREC_F32 || prec == WQ_PREC_F32_FAST)
-        e = wqd::launch_elem_f32(rule->ep, rule->nnz, tm, rule->nc, rule->d_table2, rule->d_W2, rule->nwc,
-                                 (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32, st);
-    else if ((prec == 3 || prec == 4) && rule->max_P > 64)
-        return fail(rule->ctx, WQ_ERR_ARG, "FP32 assembly supports at most 64 WQ points per element");
-    else if (prec == 4 && tm.nt > 2)
-        return fail(rule->ctx, WQ_ERR_ARG, "WQ_PREC_F32_FAST supports operators with at most two terms");
-    else if (prec == 3 || prec == 4)
-        e = wqd::launch_rowasm_f32(rule->rw, rule->d_desc_wq, &rule->ch, tm, rule->nc, rule->d_table2, rule->d_W2,
-                                   rule->nwc,
-                                   (const double*)d_coef, rule->d_coef2, rule->Q, (float*)d_vals, rule->max_n_i,
-                                   rule->n_sm, prec == 3, st);
+        e = wqd::launch_elem_f32(rule->it_wq, rule->ep, rule->nnz, tm, rule->nc, 0, rule->d_table2, rule->d_W2,
+                                 rule->nwc, nullptr, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32, st);
     else
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
@@ -717,10 +635,16 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
     if (!rule || !d_vals) return WQ_ERR_ARG;
     wqd::Terms tm;
     if (!op_terms(rule, op, alpha, false, tm)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
-    if (prec != WQ_PREC_F64) return fail(rule->ctx, WQ_ERR_ARG, "Gauss assembly supports WQ_PREC_F64");
-    cudaError_t e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_gq, tm, rule->nc, 1, rule->d_gtable, nullptr, 0,
-                                           rule->d_gw, (const double*)d_coef, (double*)d_vals, rule->max_n_i,
-                                           (cudaStream_t)stream);
+    cudaError_t e;
+    if (prec == WQ_PREC_F64)
+        e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_gq, tm, rule->nc, 1, rule->d_gtable, nullptr, 0, rule->d_gw,
+                                   (const double*)d_coef, (double*)d_vals, rule->max_n_i, (cudaStream_t)stream);
+    else if (prec == WQ_PREC_F32 || prec == WQ_PREC_F32_FAST)
+        e = wqd::launch_elem_f32(rule->it_gq, rule->ep, rule->nnz, tm, rule->nc, 1, rule->d_gtable2, nullptr, 0,
+                                 rule->d_gw, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32,
+                                 (cudaStream_t)stream);
+    else
+        return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
     return WQ_OK;
 }

@@ -47,34 +47,18 @@ struct Rows {
     const int32_t* order;     // [n] processing order of the rows (spatially sorted), or null
 };
 
-// Row chunks of the staged FP32 assembly (Morton-consecutive rows whose data fit
-// one CTA's shared memory).  Per chunk: its union elements
-//   u = {table offset, m | P << 8, offset of the element's staged table (float2 units), 0},
-// per row (Morton position k): {row, s-value offset, position offset, local-index offset},
-// per support entry: the union-local index of its element, and the chunk's sizes
-//   info = {staged table float2s, s-value float2s, support entries, positions}.
-struct Chunks {
-    int64_t n_chunks;
-    const int32_t* row_ptr;   // [n_chunks + 1] ranges of Morton positions
-    const int32_t* u_ptr;     // [n_chunks + 1] into u
-    const int4* u;
-    const int4* rows;         // [n]
-    const uint16_t* sloc;     // [#supp]
-    const int4* info;         // [n_chunks]
-    int data_bytes;           // largest staged data region (bytes, 16-aligned)
-};
-
-// Element-major FP32 assembly plan.  Work items are 16 x 16 tiles of element
-// blocks: item[k] = {table offset, first point, m | P << 8 | (a0/16) << 16 |
-// (b0/16) << 20, offset of the element's functions in ew_off}; item_k[k] = start
-// of the element's m x m entries in scat; ew_off[fn_ptr[e] + a] = first weight row
-// of (function a of e, e); scat[.] = kscr slot of a block entry; gptr[n] .. gptr[n+1]
-// = the slots of CSR entry n.
-struct ElemPlan {
-    int64_t n_items;
+// Element-major FP32 assembly.  Work items are 16 x 16 tiles of element blocks:
+// item[k] = {table offset, first point, m | P << 8 | (a0/16) << 16 | (b0/16) << 20,
+// first row of the element in the element-major weights}, kb[k] = start of the
+// element's m x m entries in scat.  scat[.] = kscr slot of a block entry;
+// gptr[n] .. gptr[n+1] = the slots of CSR entry n (shared by the WQ and Gauss items,
+// whose blocks have the same shape).
+struct ElemItems {
+    int64_t n;
     const int4* item;
-    const int32_t* item_k;
-    const int32_t* ew_off;
+    const int32_t* kb;
+};
+struct ElemPlan {
     const int32_t* scat;
     const int32_t* gptr;
     float2* kscr;

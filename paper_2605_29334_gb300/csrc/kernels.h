@@ -18,10 +18,10 @@ struct Terms {
     int nt;
     Term t[4];
 };
-// The same terms for the FP32 kernel (constant scales split into hi/lo floats).
+// The same terms for the FP32 kernels.
 struct TermsF {
     int wc[4], tc[4], use_coef[4];
-    float shi[4], slo[4];
+    double scale[4];
 };
 
 // Placement + basis evaluation at WQ (gauss = 0) or Gauss (gauss = 1) points:
@@ -41,21 +41,17 @@ cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm,
                               const double* table, const double* W, int nwc, const double* gw, const double* coef,
                               double* vals, int max_n_i, cudaStream_t st);
 
-// FP32 contraction with hi/lo split products and TwoSum accumulation: tables and
-// weights as float2 (hi, lo); the coefficient is split into coef2_buf [n_points]
-// by a small pre-kernel (two launches); float CSR values.
-// With a chunk plan and at most two terms the shared-memory staged kernel runs.
-// compensated = false: split products, plain FP32 sums (only with <= 2 terms).
-cudaError_t launch_rowasm_f32(const Rows& rw, const int4* desc, const Chunks* ch, const Terms& tm, int nc,
-                              const float2* table2, const float2* W2, int nwc, const double* coef, float2* coef2_buf,
-                              int64_t n_points, float* vals, int max_n_i, int n_sm, bool compensated,
-                              cudaStream_t st);
+// FP32 element-major assembly (split products; compensated = TwoSum sums):
+// element tiles into the slot buffer, then one sum per CSR entry.  WQ items
+// (gauss = 0) read the test side from the element-major weights W2e; Gauss items
+// (gauss = 1) from the table, times the Gauss weights gw.  1..4 terms; float CSR values.
+cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz, const Terms& tm, int nc,
+                            int gauss, const float2* table2, const float2* W2e, int nwc, const double* gw,
+                            const double* coef, float* vals, bool compensated, cudaStream_t st);
 
-// FP32 element-major assembly: element tiles into the slot buffer, then one
-// compensated sum per CSR entry; 1..4 terms; compensated = TwoSum accumulation.
-cudaError_t launch_elem_f32(const ElemPlan& ep, int64_t nnz, const Terms& tm, int nc, const float2* table2,
-                            const float2* W2, int nwc, const double* coef, float* vals, bool compensated,
-                            cudaStream_t st);
+// Element-major split copy of the weights (W2e[dst[r]] = split(W[r]), nwc columns).
+cudaError_t launch_split_rows(const double* W, const int32_t* dst, float2* W2e, int64_t rows, int nwc, int n_sm,
+                              cudaStream_t st);
 
 // Truncated-SVD weights of every row for one component (Sec. 4.3):
 //   table comp tc gives A, table comp 0 gives Z, mom [nnz] gives b;

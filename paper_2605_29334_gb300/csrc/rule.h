@@ -49,23 +49,20 @@ struct wq_rule {
     int32_t* d_order = nullptr;
     int4 *d_desc_wq = nullptr, *d_desc_gq = nullptr;
 
-    float2* d_coef2 = nullptr;
-    int32_t *d_ch_row_ptr = nullptr, *d_ch_u_ptr = nullptr;
-    int4 *d_ch_u = nullptr, *d_ch_rows = nullptr, *d_ch_info = nullptr;
-    uint16_t* d_ch_sloc = nullptr;
-    wqd::Chunks ch{};
-    int4* d_el_item = nullptr;
-    int32_t *d_el_item_k = nullptr, *d_ew_off = nullptr, *d_scat = nullptr, *d_gptr = nullptr;
+    // element-major FP32 assembly
+    int4 *d_it_wq = nullptr, *d_it_gq = nullptr;
+    int32_t *d_kb_wq = nullptr, *d_kb_gq = nullptr, *d_wrow_dst = nullptr, *d_scat = nullptr, *d_gptr = nullptr;
     float2* d_kscr = nullptr;
     int64_t kscr_len = 0;
+    wqd::ElemItems it_wq{}, it_gq{};
     wqd::ElemPlan ep{};
     int n_sm = 1;
-    int max_P = 0;          // most WQ points on one element (the FP32 kernel stages <= 64 per window)
     uint16_t* d_pos = nullptr;
     uint8_t* d_il = nullptr;
     double* d_W = nullptr;                 // [sum_r][nwc]
     double* d_mom[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    float2 *d_table2 = nullptr, *d_W2 = nullptr;
+    float2 *d_table2 = nullptr, *d_gtable2 = nullptr;
+    float2* d_W2 = nullptr;                // element-major split weights [wbase_e + q m_e + a][nwc]
     unsigned* d_status = nullptr;
     // staging for wq_assemble_host
     double* d_coef_stage = nullptr;

@@ -285,7 +285,7 @@ class Rule:
     def gq_assemble(self, op, coef_gauss, alpha=0.0, prec=PREC_F64, out=None, stream=None):
         import torch
         if out is None:
-            out = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+            out = torch.empty(self.nnz, dtype=torch.float64 if prec == PREC_F64 else torch.float32, device="cuda")
         cp = C.c_void_p(coef_gauss.data_ptr()) if coef_gauss is not None else C.c_void_p(0)
         self.ctx.check(lib().wq_gq_assemble(self.h, int(op), cp, float(alpha), int(prec),
                                             C.c_void_p(out.data_ptr()), _stream_handle(stream)))

@@ -162,10 +162,10 @@ def test_assembly_f64_and_f32(case, W):
         got32 = r.assemble(op, kd, alpha=alpha, prec=W.PREC_F32).cpu().numpy()
         assert nerr(got32, got) < 1e-6, (op, nerr(got32, got))
         assert nerr(got32, ref) < max(1e-6, tol), (op, nerr(got32, ref))
-        if len(terms) <= 2:
-            # plain FP32 sums: error grows with the cancellation in the rows (stated, not 1e-6)
-            gotf = r.assemble(op, kd, alpha=alpha, prec=W.PREC_F32_FAST).cpu().numpy()
-            assert nerr(gotf, got) < 2e-5, (op, nerr(gotf, got))
+        assert np.array_equal(got32, r.assemble(op, kd, alpha=alpha, prec=W.PREC_F32).cpu().numpy())
+        # plain FP32 sums: error grows with the cancellation in the rows (stated, not 1e-6)
+        gotf = r.assemble(op, kd, alpha=alpha, prec=W.PREC_F32_FAST).cpu().numpy()
+        assert nerr(gotf, got) < 2e-5, (op, nerr(gotf, got))
     # constant coefficient reproduces the Gauss moments (exactness, Sec. 4.3)
     if "x" in case["comps"]:
         ones = torch.ones(R.Q, dtype=torch.float64, device="cuda")
@@ -189,6 +189,11 @@ def test_gauss_assembly(case, W):
         ref = gq.assemble(B, cc, coef=_kappa, row_ptr=R.row_ptr, col=R.col)
         got = r.gq_assemble(op, kg).cpu().numpy()
         assert nerr(got, ref) < 1e-12, op
+        # element-major FP32 (split products, TwoSum): Gauss systems are well conditioned
+        got32 = r.gq_assemble(op, kg, prec=W.PREC_F32).cpu().numpy().astype(np.float64)
+        assert nerr(got32, ref) < 1e-6, op
+        again = r.gq_assemble(op, kg, prec=W.PREC_F32).cpu().numpy().astype(np.float64)
+        assert np.array_equal(got32, again)
 
 
 def test_interp(case):
