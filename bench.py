@@ -181,21 +181,33 @@ def bench_ours(args, rank, world):
     clk = ClockSampler(dev)
     clk.start()
     ms = time_steps(step, args.steps, args.warmup, flush)
+    # per-kernel durations: the same K steps again, with the library recording CUDA
+    # events around each of its kernels (kept out of the headline region: the extra
+    # event records cost a few microseconds per step)
+    rule.set_timing(args.steps)
+    ms_inst = time_steps(step, args.steps, 0, flush)
+    kt = rule.kernel_times(args.steps)
+    rule.set_timing(0)
     clocks = clk.stop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     t_total = float(np.sum(ms)) / 1e3
     # comparators on the same GPU and protocol
-    ms64 = time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F64, out=out64),
-                      max(args.steps // 4, 10), args.warmup, flush)
-    ms32 = {}
-    for name in ("f32", "f32_fast"):
-        pm = modes[name]
-        ms32[name] = float(np.mean(time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=pm, out=out32),
-                                              max(args.steps // 4, 10), args.warmup, flush)))
-    msg = time_steps(lambda: rule.gq_assemble(wq.OP_STIFF, coef_g, out=outg), max(args.steps // 4, 10),
-                     args.warmup, flush)
+    nc = max(args.steps // 4, 10)
+    comp_ms = {
+        "wq_f64": time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F64, out=out64), nc,
+                             args.warmup, flush),
+        "wq_f32": time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F32, out=out32), nc,
+                             args.warmup, flush),
+        "wq_f32_fast": time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F32_FAST, out=out32), nc,
+                                  args.warmup, flush),
+        "gq_f64": time_steps(lambda: rule.gq_assemble(wq.OP_STIFF, coef_g, prec=wq.PREC_F64, out=outg), nc,
+                             args.warmup, flush),
+        "gq_f32": time_steps(lambda: rule.gq_assemble(wq.OP_STIFF, coef_g, prec=wq.PREC_F32, out=out32), nc,
+                             args.warmup, flush),
+    }
+    comp_ms = {k: float(np.mean(v)) for k, v in comp_ms.items()}
     # end to end through the C ABI with pinned host buffers
     h_coef = torch.tensor(kap(xq)).pin_memory()
     h_vals = torch.empty(nnz, dtype=torch.float64 if prec == wq.PREC_F64 else torch.float32).pin_memory()
@@ -207,36 +219,53 @@ def bench_ours(args, rank, world):
     for _ in range(n_e2e):
         rule.assemble_host(wq.OP_STIFF, hc, prec=prec, out=hv)
     e2e_s = (time.perf_counter() - te) / n_e2e
-    stats = {"nnz": nnz, "t": t_total, "t64": float(np.mean(ms64)) / 1e3, "tg": float(np.mean(msg)) / 1e3}
     tot_nnz, t_max = aggregate(nnz, t_total, world, "cuda")
     if rank != 0:
         return None
     value = tot_nnz * args.steps / t_max
     mean_s = t_total / args.steps
-    ab = algorithmic_bytes_f(rule, basis, prec)
-    gpu_launches = args.steps * (1 if prec == wq.PREC_F64 else 2)
+    work = assembly_work(rule, basis, n_terms=2)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = ab / mean_s / 1e9
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    t_k1 = float(np.mean(kt[:, 0])) / 1e3 if len(kt) else float("nan")
+    t_k2 = float(np.mean(kt[:, 1])) / 1e3 if len(kt) else float("nan")
+    step_bytes = work["hbm_bytes_f64"] if prec == wq.PREC_F64 else work["hbm_bytes_f32"]
+    if prec == wq.PREC_F64:
+        kname = "k_rowasm_f64"
+        achieved = step_bytes / t_k1 / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": kname, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        # the element-block kernel is bound by FP32 instruction issue: 12 FP32 instructions per
+        # split product with TwoSum (3 without); peak = 152 SMs x 128 FP32 lanes x max SM clock
+        per = 12 if prec == wq.PREC_F32 else 3
+        kname = "k_elem_f32<2,%d,0>" % (1 if prec == wq.PREC_F32 else 0)
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        achieved = per * work["products"] / t_k1 / 1e12
+        traffic = ELEM_TRAFFIC.get(kname) if _kernel_source_sha1() == ELEM_TRAFFIC.get("source_sha1") else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 lane-instructions/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (MEASURED_PEAKS.json sm_max_mhz)" % sm_mhz,
+                "kernel_ms": t_k1 * 1e3, "gather_ms": t_k2 * 1e3,
+                "instrumented_step_ms": float(np.mean(ms_inst)),
+                "kernel_share_of_step": t_k1 / (float(np.mean(ms_inst)) / 1e3),
+                "step_hbm_frac": step_bytes / mean_s / 1e9 / hbm, "step_algorithmic_bytes": step_bytes}
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == wq.PREC_F64 else "f32", "precision_mode": choice, "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_functions": basis.n, "n_elements": basis.E, "nnz": nnz,
                    "n_points": rule.Q, "n_gauss": rule.G, "op": "stiffness", "l2": "flushed (256 MB write) before "
-                   "every timed step; timed = the assembly kernel only", "parallelism": "independent instance per GPU"},
+                   "every timed step; timed = the assembly call only", "parallelism": "independent instance per GPU"},
         "rel_err_vs_f64": rel,
-        "gpu_launches": gpu_launches,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "k_rowasm_f64" if prec == wq.PREC_F64 else "k_chunk_f32",
-                     "algorithmic_bytes": ab},
-        "comparators": {
-            "wq_f64_nnz_per_s": nnz / stats["t64"], "gq_f64_nnz_per_s": nnz / stats["tg"],
-            "wq_f32_nnz_per_s": nnz / (ms32["f32"] / 1e3), "wq_f32_fast_nnz_per_s": nnz / (ms32["f32_fast"] / 1e3),
-            "wq_f32_ms": ms32["f32"], "wq_f32_fast_ms": ms32["f32_fast"],
-            "wq_f64_ms": stats["t64"] * 1e3, "gq_f64_ms": stats["tg"] * 1e3,
-            "speedup_wq_over_gq_f64": stats["tg"] / stats["t64"]},
+        "gpu_launches": args.steps * (1 if prec == wq.PREC_F64 else 2),
+        "roofline": roof,
+        "comparators": dict({k + "_ms": v for k, v in comp_ms.items()},
+                            **{k + "_nnz_per_s": nnz / (v / 1e3) for k, v in comp_ms.items()},
+                            speedup_wq_over_gq_f64=comp_ms["gq_f64"] / comp_ms["wq_f64"],
+                            speedup_wq_over_gq_f32=comp_ms["gq_f32"] / comp_ms["wq_f32"]),
         "setup": {"host_basis_ms": host_ms, "rule_build_wall_ms": build_ms, "rule_build_device_ms": rule.info.setup_ms,
                   "n_truncated_x": rule.info.n_truncated[1], "n_z_identity_x": rule.info.n_z_identity[1]},
         "e2e": {"value": nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(rule.Q * 8),
@@ -248,21 +277,37 @@ def bench_ours(args, rank, world):
     return res
 
 
-def algorithmic_bytes_f(rule, basis, prec):
-    """Algorithmic bytes of one stiffness assembly launch (2 weight/table components)."""
+# DRAM bytes (read + write) of one launch of the element-block kernel on this workload,
+# from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md), valid for the kernel
+# source it was taken on.
+ELEM_TRAFFIC = {"source_sha1": "d1a9be980e3633021aa0296aa8ba544841c07ea2", "k_elem_f32<2,1,0>": 60484352}
+
+
+def _kernel_source_sha1():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2605_29334_gb300", "csrc", "k_assemble.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def assembly_work(rule, basis, n_terms):
+    """Algorithmic work of one stiffness assembly (n_terms weight/table components):
+    products = sum_e m_e^2 P_e n_terms (one per test x trial x point x term);
+    HBM bytes = what must be read and written once: weights and the used table
+    components (FP64 values, or FP32 (hi, lo) pairs), the coefficient at the points,
+    the index data the kernels read, and the CSR values."""
     E = basis.E
     side = basis.point_counts().astype(np.int64)
     m = np.array([basis.element(e)["fns"].size for e in range(E)], dtype=np.int64)
     P = side * side
-    vb = 8  # FP64 value, or an FP32 (hi, lo) pair
-    weights = rule.info.sum_r * 2 * vb
-    tables = int(np.sum(P * m)) * 2 * vb
+    products = int(np.sum(m * m * P)) * n_terms
+    weights = rule.info.sum_r * n_terms * 8
+    tables = int(np.sum(P * m)) * n_terms * 8
     coef = rule.Q * 8
-    pos = int(np.sum(m * m)) * 2
-    supp = int(np.sum(m)) * 4
-    rows = (basis.n + 1) * (4 + 8 + 8)
-    out = rule.nnz * (8 if prec == 0 else 4)
-    return int(weights + tables + coef + pos + supp + rows + out)
+    n = basis.n
+    f64 = weights + tables + coef + int(np.sum(m * m)) * 2 + int(np.sum(m)) * 16 + (n + 1) * 20 + rule.nnz * 8
+    n_tiles = int(np.sum(((m + 15) // 16) ** 2))
+    f32 = weights + tables + coef + int(np.sum(m * m)) * 4 + (rule.nnz + 1) * 4 + n_tiles * 20 + rule.nnz * 4
+    return {"products": products, "hbm_bytes_f64": int(f64), "hbm_bytes_f32": int(f32)}
 
 
 def cpu_baseline(args, seconds=12.0):

@@ -235,6 +235,23 @@ wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
                            int32_t prec, void* h_vals, void* stream);
 
+/* Kernel timing of the assembly calls.  Instrumentation with no counterpart in
+ * the paper (it serves the benchmark's per-kernel roofline): capacity > 0 makes
+ * the next `capacity` calls of wq_assemble / wq_gq_assemble on this rule record
+ * CUDA events on their stream before the first, between the two and after the
+ * second kernel they launch (FP32 paths: element blocks, then the per-entry sums;
+ * FP64 paths: the single row kernel, reported as the first with a zero second).
+ * Calls beyond the capacity are not recorded; capacity 0 turns recording off and
+ * frees the events.  Not for calls inside a stream capture.  Errors: WQ_ERR_ARG,
+ * WQ_ERR_CUDA (event creation). */
+wq_status wq_rule_set_timing(wq_rule* rule, int32_t capacity);
+
+/* Durations of the recorded calls in call order: h_ms[2k] and h_ms[2k + 1] are
+ * the first and second kernel of call k (milliseconds); *n_calls = number of
+ * recorded calls (at most max_calls are written).  Waits for the recorded events,
+ * then clears the record (the capacity stays).  Errors: WQ_ERR_ARG, WQ_ERR_CUDA. */
+wq_status wq_rule_kernel_times(wq_rule* rule, int32_t max_calls, float* h_ms, int32_t* n_calls);
+
 /* Truncated-SVD weights of component comp of an existing rule, recomputed into
  * caller memory d_w [sum_r] (row i at [w_ptr[i], w_ptr[i+1]), the layout of
  * wq_rule_weights but contiguous), WITHOUT allocating: the solve's workspace is

@@ -618,14 +618,18 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
         return fail(rule->ctx, WQ_ERR_ARG, "operator needs weight sets that this rule did not build");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
-    if (prec == WQ_PREC_F64)
+    if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST)
+        return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
+    cudaEvent_t* evs = rule->next_timing_events();
+    if (prec == WQ_PREC_F64) {
+        if (evs) cudaEventRecord(evs[0], st);
         e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_wq, tm, rule->nc, 0, rule->d_table, rule->d_W, rule->nwc,
                                    nullptr, (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
-    else if (prec == WQ_PREC_F32 || prec == WQ_PREC_F32_FAST)
+        if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
+    } else
         e = wqd::launch_elem_f32(rule->it_wq, rule->ep, rule->nnz, tm, rule->nc, 0, rule->d_table2, rule->d_W2,
-                                 rule->nwc, nullptr, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32, st);
-    else
-        return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
+                                 rule->nwc, nullptr, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32, st,
+                                 evs);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
     return WQ_OK;
 }
@@ -636,15 +640,18 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
     wqd::Terms tm;
     if (!op_terms(rule, op, alpha, false, tm)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
     cudaError_t e;
-    if (prec == WQ_PREC_F64)
-        e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_gq, tm, rule->nc, 1, rule->d_gtable, nullptr, 0, rule->d_gw,
-                                   (const double*)d_coef, (double*)d_vals, rule->max_n_i, (cudaStream_t)stream);
-    else if (prec == WQ_PREC_F32 || prec == WQ_PREC_F32_FAST)
-        e = wqd::launch_elem_f32(rule->it_gq, rule->ep, rule->nnz, tm, rule->nc, 1, rule->d_gtable2, nullptr, 0,
-                                 rule->d_gw, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32,
-                                 (cudaStream_t)stream);
-    else
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
+    cudaEvent_t* evs = rule->next_timing_events();
+    if (prec == WQ_PREC_F64) {
+        if (evs) cudaEventRecord(evs[0], st);
+        e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_gq, tm, rule->nc, 1, rule->d_gtable, nullptr, 0, rule->d_gw,
+                                   (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
+        if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
+    } else
+        e = wqd::launch_elem_f32(rule->it_gq, rule->ep, rule->nnz, tm, rule->nc, 1, rule->d_gtable2, nullptr, 0,
+                                 rule->d_gw, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32, st, evs);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
     return WQ_OK;
 }
@@ -679,6 +686,41 @@ wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d
                                             rule->d_table, d_u, d_u_old, dt, k0, k2, f, d_kappa, d_g,
                                             (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("heat fields launch: ") + cudaGetErrorString(e));
+    return WQ_OK;
+}
+
+wq_status wq_rule_set_timing(wq_rule* rule, int32_t capacity) {
+    if (!rule || capacity < 0) return WQ_ERR_ARG;
+    CUDA_TRY(rule->ctx, cudaSetDevice(rule->ctx->device));
+    for (auto ev : rule->tev) cudaEventDestroy(ev);
+    rule->tev.clear();
+    rule->tcap = 0;
+    rule->tcount = 0;
+    rule->tev.resize((size_t)capacity * 3, nullptr);
+    for (auto& ev : rule->tev) {
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            ev = nullptr;
+            for (auto e2 : rule->tev)
+                if (e2) cudaEventDestroy(e2);
+            rule->tev.clear();
+            return fail(rule->ctx, WQ_ERR_CUDA, "event creation failed");
+        }
+    }
+    rule->tcap = capacity;
+    return WQ_OK;
+}
+
+wq_status wq_rule_kernel_times(wq_rule* rule, int32_t max_calls, float* h_ms, int32_t* n_calls) {
+    if (!rule || max_calls < 0 || (max_calls > 0 && !h_ms)) return WQ_ERR_ARG;
+    const int n = std::min(rule->tcount, max_calls);
+    for (int k = 0; k < n; ++k) {
+        cudaEvent_t* ev = rule->tev.data() + 3 * k;
+        CUDA_TRY(rule->ctx, cudaEventSynchronize(ev[2]));
+        CUDA_TRY(rule->ctx, cudaEventElapsedTime(&h_ms[2 * k], ev[0], ev[1]));
+        CUDA_TRY(rule->ctx, cudaEventElapsedTime(&h_ms[2 * k + 1], ev[1], ev[2]));
+    }
+    if (n_calls) *n_calls = n;
+    rule->tcount = 0;
     return WQ_OK;
 }
 

@@ -344,8 +344,13 @@ __global__ void __launch_bounds__(256) k_gather_f32(int64_t nnz, const int32_t* 
 
 cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz, const Terms& tm, int nc,
                             int gauss, const float2* table2, const float2* W2e, int nwc, const double* gw,
-                            const double* coef, float* vals, bool compensated, cudaStream_t st) {
-    if (nnz == 0) return cudaSuccess;
+                            const double* coef, float* vals, bool compensated, cudaStream_t st,
+                            cudaEvent_t* evs) {
+    if (evs) cudaEventRecord(evs[0], st);
+    if (nnz == 0) {
+        if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
+        return cudaSuccess;
+    }
     TermsF tf{};
     for (int t = 0; t < tm.nt; ++t) {
         tf.wc[t] = tm.t[t].wc;
@@ -376,11 +381,13 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz
 #undef WQ_EL_CASE
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (evs) cudaEventRecord(evs[1], st);
     const unsigned gb = (unsigned)((nnz + 255) / 256);
     if (compensated)
         k_gather_f32<true><<<gb, 256, 0, st>>>(nnz, ep.gptr, ep.kscr, vals);
     else
         k_gather_f32<false><<<gb, 256, 0, st>>>(nnz, ep.gptr, ep.kscr, vals);
+    if (evs) cudaEventRecord(evs[2], st);
     return cudaGetLastError();
 }
 

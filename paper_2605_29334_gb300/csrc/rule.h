@@ -67,11 +67,20 @@ struct wq_rule {
     // staging for wq_assemble_host
     double* d_coef_stage = nullptr;
     double* d_vals_stage = nullptr;
+    // kernel timing (wq_rule_set_timing): 3 events per recorded call
+    mutable std::vector<cudaEvent_t> tev;
+    mutable int tcount = 0;
+    int tcap = 0;
+    cudaEvent_t* next_timing_events() const {
+        if (tcount >= tcap) return nullptr;
+        return tev.data() + 3 * (tcount++);
+    }
     wqd::Elems el{};
     wqd::Rows rw{};
     wq_rule_info info{};
 
     ~wq_rule() {
+        for (auto ev : tev) cudaEventDestroy(ev);
         for (auto& b : bufs)
             if (b.p) cudaFree(b.p);
     }

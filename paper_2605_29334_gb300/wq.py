@@ -84,6 +84,8 @@ EXPORTS = {
     "wq_heat_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_basis_functions": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "wq_rule_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "wq_rule_kernel_times": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
 }
 
 _lib = None
@@ -337,6 +339,18 @@ class Rule:
         self.ctx.check(lib().wq_rule_weights_noalloc(self.h, int(comp), C.c_void_p(out.data_ptr()),
                                                      _stream_handle(stream)))
         return out
+
+    def set_timing(self, capacity):
+        """Record per-kernel CUDA events for the next `capacity` assembly calls (0: off)."""
+        self.ctx.check(lib().wq_rule_set_timing(self.h, int(capacity)))
+
+    def kernel_times(self, max_calls=1 << 20):
+        """[calls, 2] durations (ms) of the two kernels of each recorded assembly call."""
+        max_calls = max(0, min(int(max_calls), 1 << 24))
+        buf = np.zeros(2 * max(max_calls, 1), dtype=np.float32)
+        n = C.c_int32(0)
+        self.ctx.check(lib().wq_rule_kernel_times(self.h, max_calls, _ptr(buf), C.byref(n)))
+        return buf[:2 * n.value].reshape(n.value, 2)
 
     def __del__(self):
         if getattr(self, "h", None):
