@@ -151,11 +151,21 @@ cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm,
 
 // ------------------------------------------------------------------ FP32
 // Split products: weights, table values and coefficients are (hi, lo) float
-// pairs with hi = fl32(v), lo = fl32(v - hi); s * T ~ s_hi T_hi + (s_hi T_lo +
-// s_lo T_hi), the large parts summed with Knuth's TwoSum (error-free) and every
-// rounding error collected in a correction sum.  The weighted terms of one entry
-// cancel heavily, so plain FP32 sums lose digits (~1.5e-6 normwise on the
-// 10,240-element Poisson workload, against ~3e-8 with TwoSum).
+// pairs with hi = fl32(v), lo = fl32(v - hi), and s * T ~ s_hi T_hi + (s_hi T_lo +
+// s_lo T_hi).  The weighted terms of one entry cancel heavily, so plain FP32 sums
+// of the s_hi T_hi lose digits (~1.5e-6 normwise on the 10,240-element Poisson
+// workload, F32_FAST).  The compensated mode accumulates them without error
+// growth by extraction against a power-of-two constant (the splitting idea of
+// Rump, Ogita and Oishi, "Accurate floating-point summation", SIAM J. Sci.
+// Comput. 31, 2008): with C = 2^k >= 4 B, B a bound on every partial sum of the
+// entry, the accumulator acc = C + partial sum stays in [3C/4, 5C/4], so
+//     acc' = fma(s_hi, T_hi, acc),  d = acc - acc'  (exact, Sterbenz),
+//     e = fma(s_hi, T_hi, d)        (the rounding error of acc', to 2^-24 of itself)
+// and the errors e, together with the cross terms, go to a correction sum lo.  The
+// entry is (acc - C) + lo: 6 FP32 instructions per product, and errors of order
+// N^2 2^-48 C for N products, far below the final FP32 rounding.  B is taken per
+// tile and chunk as (products in the chunk) x max|s_hi| x max|T_hi|; on the next
+// chunk the accumulator is moved to a new constant with TwoSum.
 //
 // Element-major form.  Phase 1 computes the dense block of every element's
 // test x trial pairs
@@ -165,16 +175,15 @@ cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm,
 // (a, b over the m_e functions of e, q over its points).  One warp computes one
 // 16 x 16 tile of one block: a regular element (m_e = 16) is one tile; larger
 // elements are several and are listed first, so their longer point loops start
-// in the first wave.  Per chunk of points, everything the tile needs -- trial
-// table columns, test-side rows (weights or table values), coefficients, Gauss
-// weights, and (once) the destination slots -- is copied to shared memory with
-// cp.async in one batch; the products s are then formed in place and every lane
-// accumulates one column b over 8 rows (two half-warps), reading its table value
-// once per (point, term) and the row values as broadcasts.  Each entry goes to
-// its slot in kscr, where the contributions to one CSR entry are contiguous and
-// in the order of the elements in supp N_i.
-// Phase 2, one thread per CSR entry, sums its slots (compensated).  No atomics:
-// the result is bitwise reproducible.
+// in the first wave.  Per chunk of points, the tile's trial table columns,
+// test-side rows (weights or table values), coefficients and Gauss weights are
+// copied to shared memory with cp.async in one batch; the products s are then
+// formed in place and every lane accumulates one column b over 8 rows (two
+// half-warps), reading its table value once per (point, term) and the row values
+// as broadcasts.  Each entry goes to its slot in kscr, where the contributions to
+// one CSR entry are contiguous and in the order of the elements in supp N_i.
+// Phase 2, one thread per CSR entry, sums its slots with TwoSum.  No atomics: the
+// result is bitwise reproducible.
 constexpr int EL_NWARP = 4;     // warps per block
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
@@ -187,56 +196,77 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Smallest power of two >= 4 x (a non-negative finite float x).
+__device__ __forceinline__ float pow2_above_4x(float x) {
+    const unsigned bits = __float_as_uint(x * 4.0f);
+    return __uint_as_float(((bits >> 23) + 1u) << 23);
+}
+
 template <int NT, bool COMP, bool GAUSS>
-__global__ void __launch_bounds__(EL_NWARP * 32)
+__global__ void __launch_bounds__(EL_NWARP * 32, 6)
     k_elem_f32(ElemItems it, ElemPlan ep, TermsF tm, int nc, const float2* __restrict__ table2,
                const float2* __restrict__ W2e, int nwc, const double* __restrict__ gw,
                const double* __restrict__ coef) {
-    constexpr int QC = NT <= 2 ? 16 : 8;            // most points per staged chunk
+    constexpr int QC = NT <= 2 ? 12 : 8;            // most points per staged chunk
     __shared__ __align__(16) float2 sT[EL_NWARP][QC * NT * 16];   // trial side [point][term][column]
     __shared__ __align__(16) float2 sS[EL_NWARP][QC * NT * 16];   // test side, then the products s
-    __shared__ __align__(16) int32_t sSlot[EL_NWARP][256];
     __shared__ __align__(16) double sD[EL_NWARP][2 * QC];         // coefficients, Gauss weights
     __shared__ __align__(16) float2 sC[EL_NWARP][QC * NT];        // split multipliers per (point, term)
+    __shared__ __align__(16) int32_t sSlot[EL_NWARP][256];        // destination slots of the tile
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * EL_NWARP + wib;
     if (k >= it.n) return;
     const int4 d = it.item[k];
     const int kb = it.kb[k];
     const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
-    const float2* tb = table2 + d.x;
     float2* T_ = sT[wib];
     float2* S_ = sS[wib];
-    int32_t* SL = sSlot[wib];
     double* D_ = sD[wib];
     float2* C_ = sC[wib];
-    const int bl = lane & 15, rbase = 8 * (lane >> 4);
+    const int bl = lane & 15, half = lane >> 4, rbase = 8 * half;
     const int b = b0 + bl;
-    for (int x = lane; x < 256; x += 32) {
-        const int r = x >> 4, c = x & 15;
-        if (a0 + r < m && b0 + c < m) cp_async4(SL + x, ep.scat + kb + (a0 + r) * m + b0 + c);
-    }
-    float hi[8], lo[8];
+    const bool bok = b < m, aok = a0 + bl < m;      // this lane's column; the row it stages
+    int32_t* SL = sSlot[wib];
+    // destination slots of the tile's entries, copied with the first chunk
 #pragma unroll
-    for (int r = 0; r < 8; ++r) hi[r] = lo[r] = 0.0f;
+    for (int r = 0; r < 8; ++r) {
+        const int a = a0 + rbase + r;
+        if (bok && a < m) cp_async4(SL + (rbase + r) * 16 + bl, ep.scat + kb + a * m + b);
+    }
+    float acc[8], lo[8];
+    float cst = 0.0f;                               // the extraction constant C
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = lo[r] = 0.0f;
     const int nch = (P + QC - 1) / QC;
     const int qc = (P + nch - 1) / nch;            // balanced chunks of at most QC points
+    // staging offsets (32-bit: tables and weights are below 2^31 entries): lane (half, bl)
+    // copies points q0 + half + 2 j, column / row bl
+    const float2* tb = table2 + d.x;
+    const int ncm = nc * m;
+    const int tcol = half * ncm + b0 + bl, trow = half * ncm + a0 + bl;
+    const float2* wb = W2e + (int64_t)d.w * nwc;
+    const int wrow = (half * m + a0 + bl) * nwc, mnwc = m * nwc;
     for (int q0 = 0; q0 < P; q0 += qc) {
         const int nq = min(qc, P - q0);
+        const int nj = (nq + 1 - half) >> 1;       // this half-warp's points in the chunk
         __syncwarp();
+        for (int j = 0; j < nj; ++j) {
+            const int qq = half + 2 * j;
+            const int qo = (q0 + 2 * j) * ncm;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int tc = tm.tc[t], wc = tm.wc[t];
-            for (int x = lane; x < nq * 16; x += 32) {
-                const int qq = x >> 4, c = x & 15;
-                const int64_t q = q0 + qq;
-                const float2* trow = tb + (q * nc + tc) * m;
-                if (b0 + c < m) cp_async8(T_ + (qq * NT + t) * 16 + c, trow + b0 + c);
-                if (a0 + c < m) {
+            for (int t = 0; t < NT; ++t) {
+                if (bok) cp_async8(T_ + (qq * NT + t) * 16 + bl, tb + (tcol + qo + tm.tc[t] * m));
+                if (aok) {
                     if (GAUSS)
-                        cp_async8(S_ + (qq * NT + t) * 16 + c, trow + a0 + c);
+                        cp_async8(S_ + (qq * NT + t) * 16 + bl, tb + (trow + qo + tm.tc[t] * m));
                     else
-                        cp_async8(S_ + (qq * NT + t) * 16 + c, W2e + ((int64_t)d.w + q * m + a0 + c) * nwc + wc);
+                        cp_async8(S_ + (qq * NT + t) * 16 + bl, wb + (wrow + (q0 + 2 * j) * mnwc + tm.wc[t]));
                 }
             }
         }
@@ -248,58 +278,99 @@ __global__ void __launch_bounds__(EL_NWARP * 32)
         __syncwarp();
         if (lane < nq) {
             const double cq = coef ? D_[lane] : 1.0;
-            const double g = GAUSS ? D_[QC + lane] : 1.0;
+            if (GAUSS) {
+                const double g = D_[QC + lane];
 #pragma unroll
-            for (int t = 0; t < NT; ++t) {
-                const double v = g * (tm.use_coef[t] ? cq : tm.scale[t]);
-                const float vh = (float)v;
-                C_[lane * NT + t] = make_float2(vh, (float)(v - (double)vh));
+                for (int t = 0; t < NT; ++t) {
+                    const double v = g * (tm.use_coef[t] ? cq : tm.scale[t]);
+                    const float vh = (float)v;
+                    C_[lane * NT + t] = make_float2(vh, (float)(v - (double)vh));
+                }
+            } else {
+                const float ch = (float)cq;
+                const float2 cs = make_float2(ch, (float)(cq - (double)ch));   // split once per point
+#pragma unroll
+                for (int t = 0; t < NT; ++t)
+                    C_[lane * NT + t] = tm.use_coef[t] ? cs : make_float2(tm.shi[t], tm.slo[t]);
             }
         }
         __syncwarp();
-        for (int x = lane; x < nq * 16; x += 32) {
-            const int qq = x >> 4, ar = x & 15;
+        // products s in place (rows beyond m are zeroed), with the largest |s_hi| and
+        // |T_hi| of the chunk for the accumulation bound
+        float smax = 0.0f, tmax = 0.0f;
+        for (int j = 0; j < nj; ++j) {
+            const int qq = half + 2 * j;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
-                float2* sp = S_ + (qq * NT + t) * 16 + ar;
+                float2* sp = S_ + (qq * NT + t) * 16 + bl;
                 float2 v = make_float2(0.0f, 0.0f);
-                if (a0 + ar < m) {
+                if (aok) {
                     const float2 w = *sp, c = C_[qq * NT + t];
                     float ph, pe;
                     two_prod(w.x, c.x, ph, pe);
                     v = make_float2(ph, pe + fmaf(w.x, c.y, w.y * c.x));
                 }
                 *sp = v;
+                if (COMP) {
+                    smax = fmaxf(smax, fabsf(v.x));
+                    if (bok) tmax = fmaxf(tmax, fabsf(T_[(qq * NT + t) * 16 + bl].x));
+                }
+            }
+        }
+        if (COMP) {
+            // constant for this chunk: C >= 4 (|value so far| + N max|s| max|T|)
+            smax = warp_max(smax);
+            tmax = warp_max(tmax);
+            if (q0 == 0) {
+                cst = pow2_above_4x((float)(nq * NT) * smax * tmax * 1.0001f);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) acc[r] = cst;
+            } else {
+                float vmax = 0.0f;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) vmax = fmaxf(vmax, fabsf(acc[r] - cst));
+                vmax = warp_max(vmax);
+                const float cn = pow2_above_4x(vmax + (float)(nq * NT) * smax * tmax * 1.0001f);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    float s2, e2;
+                    two_sum(cn, acc[r] - cst, s2, e2);
+                    acc[r] = s2;
+                    lo[r] += e2;
+                }
+                cst = cn;
             }
         }
         __syncwarp();
-        if (b < m) {
+        if (bok) {
+#pragma unroll 2
             for (int qq = 0; qq < nq; ++qq) {
+                float2 T[NT];
+                const float4* srow[NT];
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    const float2 T = T_[(qq * NT + t) * 16 + bl];
-                    const float4* srow = reinterpret_cast<const float4*>(S_ + (qq * NT + t) * 16 + rbase);
+                    T[t] = T_[(qq * NT + t) * 16 + bl];
+                    srow[t] = reinterpret_cast<const float4*>(S_ + (qq * NT + t) * 16 + rbase);
+                }
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
 #pragma unroll
                     for (int r2 = 0; r2 < 4; ++r2) {
-                        const float4 sv = srow[r2];
+                        const float4 sv = srow[t][r2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const float sx = h ? sv.z : sv.x, sy = h ? sv.w : sv.y;
                             const int r = 2 * r2 + h;
                             if (COMP) {
-                                float ph, pe, s2, e2;
-                                two_prod(sx, T.x, ph, pe);
-                                two_sum(hi[r], ph, s2, e2);
-                                hi[r] = s2;
-                                lo[r] += e2;
-                                lo[r] += pe;
-                                lo[r] = fmaf(sx, T.y, lo[r]);
-                                lo[r] = fmaf(sy, T.x, lo[r]);
+                                const float an = fmaf(sx, T[t].x, acc[r]);
+                                const float e = fmaf(sx, T[t].x, acc[r] - an);
+                                acc[r] = an;
+                                lo[r] += e;
                             } else {
-                                hi[r] = fmaf(sx, T.x, hi[r]);
-                                lo[r] = fmaf(sx, T.y, lo[r]);
-                                lo[r] = fmaf(sy, T.x, lo[r]);
+                                acc[r] = fmaf(sx, T[t].x, acc[r]);
                             }
+                            lo[r] = fmaf(sx, T[t].y, lo[r]);
+                            lo[r] = fmaf(sy, T[t].x, lo[r]);
                         }
                     }
                 }
@@ -308,38 +379,48 @@ __global__ void __launch_bounds__(EL_NWARP * 32)
     }
     cp_async_wait_all();
     __syncwarp();
-    if (b < m) {
+    if (bok) {
 #pragma unroll
         for (int r = 0; r < 8; ++r)
-            if (a0 + rbase + r < m) ep.kscr[SL[(rbase + r) * 16 + bl]] = make_float2(hi[r], lo[r]);
+            if (a0 + rbase + r < m) ep.kscr[SL[(rbase + r) * 16 + bl]] = make_float2(acc[r] - cst, lo[r]);
     }
 }
 
+// Phase 2: one thread per two consecutive CSR entries.  Their slots are contiguous;
+// they are fetched 8 at a time, all loads in flight together, and each is added
+// with TwoSum to the entry it belongs to (in slot order, i.e. support order).
 template <bool COMP>
 __global__ void __launch_bounds__(256) k_gather_f32(int64_t nnz, const int32_t* __restrict__ gptr,
                                                     const float2* __restrict__ kscr, float* __restrict__ vals) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // launched as a programmatic dependent of the element kernel: wait for its results
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    const int64_t n = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (n >= nnz) return;
-    const int c0 = gptr[n], c1 = gptr[n + 1];
-    float hi = 0.0f, lo = 0.0f;
-    for (int cb = c0; cb < c1; cb += 8) {
+    const int c0 = gptr[n], c1 = gptr[n + 1], c2 = gptr[min(n + 2, nnz)];
+    float hi0 = 0.0f, lo0 = 0.0f, hi1 = 0.0f, lo1 = 0.0f;
+    for (int cb = c0; cb < c2; cb += 8) {
         float2 v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = cb + j < c1 ? kscr[cb + j] : make_float2(0.0f, 0.0f);
+        for (int j = 0; j < 8; ++j) v[j] = cb + j < c2 ? kscr[cb + j] : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
+            const bool first = cb + j < c1;
+            float h = first ? hi0 : hi1, l = first ? lo0 : lo1;
             if (COMP) {
                 float s3, e3;
-                two_sum(hi, v[j].x, s3, e3);
-                hi = s3;
-                lo += v[j].y + e3;
+                two_sum(h, v[j].x, s3, e3);
+                h = s3;
+                l += v[j].y + e3;
             } else {
-                hi += v[j].x;
-                lo += v[j].y;
+                h += v[j].x;
+                l += v[j].y;
             }
+            if (first) hi0 = h, lo0 = l;
+            else hi1 = h, lo1 = l;
         }
     }
-    vals[n] = hi + lo;
+    vals[n] = hi0 + lo0;
+    if (n + 1 < nnz) vals[n + 1] = hi1 + lo1;
 }
 
 cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz, const Terms& tm, int nc,
@@ -357,6 +438,8 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz
         tf.tc[t] = tm.t[t].tc;
         tf.use_coef[t] = tm.t[t].use_coef;
         tf.scale[t] = tm.t[t].scale;
+        tf.shi[t] = (float)tm.t[t].scale;
+        tf.slo[t] = (float)(tm.t[t].scale - (double)tf.shi[t]);
     }
     const unsigned eb = (unsigned)((it.n + EL_NWARP - 1) / EL_NWARP);
 #define WQ_EL_CASE(N, C)                                                                                      \
@@ -382,11 +465,23 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (evs) cudaEventRecord(evs[1], st);
-    const unsigned gb = (unsigned)((nnz + 255) / 256);
+    // programmatic dependent launch: the sums' grid is set up while the element
+    // kernel drains, and waits (griddepcontrol.wait) for its completion
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((nnz + 511) / 512));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (compensated)
-        k_gather_f32<true><<<gb, 256, 0, st>>>(nnz, ep.gptr, ep.kscr, vals);
+        e = cudaLaunchKernelEx(&cfg, k_gather_f32<true>, nnz, ep.gptr, (const float2*)ep.kscr, vals);
     else
-        k_gather_f32<false><<<gb, 256, 0, st>>>(nnz, ep.gptr, ep.kscr, vals);
+        e = cudaLaunchKernelEx(&cfg, k_gather_f32<false>, nnz, ep.gptr, (const float2*)ep.kscr, vals);
+    if (e != cudaSuccess) return e;
     if (evs) cudaEventRecord(evs[2], st);
     return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ struct Terms {
 struct TermsF {
     int wc[4], tc[4], use_coef[4];
     double scale[4];
+    float shi[4], slo[4];   // scale split into (hi, lo) floats
 };
 
 // Placement + basis evaluation at WQ (gauss = 0) or Gauss (gauss = 1) points:
