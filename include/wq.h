@@ -69,6 +69,7 @@ typedef enum { WQ_COUNT_MINMAX = 0 } wq_count_mode;
 typedef struct wq_ctx wq_ctx;
 typedef struct wq_basis wq_basis;
 typedef struct wq_rule wq_rule;
+typedef struct wq_batch wq_batch;
 
 /* Control mesh (host arrays, copied by wq_build_basis).
  *   dim          2 = planar domain (z ignored), 3 = surface in R^3
@@ -234,6 +235,38 @@ wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
  * prec), synchronising on stream.  Uses library-owned staging buffers. */
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
                            int32_t prec, void* h_vals, void* stream);
+
+/* Batched assembly of several independent rules (SURVEY config 5: many mesh
+ * instances of uneven size).  wq_batch_create concatenates the element tiles of
+ * k <= 256 rules (which must share the device, the weight components and the
+ * dimension; the rules must outlive the batch) and uploads that plan once.
+ * wq_assemble_batched then assembles operator `op` for all of them with ONE
+ * launch of the element kernel and ONE launch of the per-entry sums (FP32
+ * modes), reading h_coefs[r] (device pointer to rule r's coefficient at its WQ
+ * points, or null) and writing h_vals[r] (device pointer, float [nnz_r]); both
+ * pointer arrays are host arrays, read during the call (their contents go into
+ * the launch parameters, so the call allocates nothing and may be captured in a
+ * CUDA graph).  WQ_PREC_F64 falls back to one wq_assemble per rule.  The paper
+ * treats one mesh at a time; this entry point is the batching of many.  Errors:
+ * WQ_ERR_ARG (k out of range, mixed rules, null output, operator not built),
+ * WQ_ERR_OOM, WQ_ERR_CUDA. */
+wq_status wq_batch_create(int32_t k, const wq_rule* const* rules, wq_batch** out);
+void wq_batch_destroy(wq_batch* batch);
+wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* const* h_coefs, double alpha,
+                              int32_t prec, void* const* h_vals, void* stream);
+
+/* Checkpoint of a rule's expensive part.  wq_rule_save writes the FP64 weights
+ * of every built component, the Gauss moments and the weight statistics to a
+ * binary file (native byte order), with the build options and a fingerprint of
+ * the mesh (coordinates and quads).  wq_rule_load rebuilds the point plan and
+ * the basis tables for `basis` (seconds less: no moment assembly and no SVD) and
+ * takes the weights and moments from the file; it synchronises on the legacy
+ * default stream.  The paper computes weights once and reuses them (Sec. 4.3);
+ * the file format is this library's own.  Errors: WQ_ERR_ARG (cannot open or
+ * write the file, not a rule file, saved for a different mesh, truncated),
+ * WQ_ERR_CUDA, and the errors of wq_rule_build. */
+wq_status wq_rule_save(const wq_rule* rule, const char* path);
+wq_status wq_rule_load(wq_basis* basis, const char* path, wq_rule** out);
 
 /* Kernel timing of the assembly calls.  Instrumentation with no counterpart in
  * the paper (it serves the benchmark's per-kernel roofline): capacity > 0 makes

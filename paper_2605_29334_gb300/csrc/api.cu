@@ -3,9 +3,11 @@
 // assembly entry points.  Host set-up lives in host.cpp, kernels in k_*.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.h"
@@ -211,7 +213,49 @@ wq_status wq_point_counts(const wq_basis* basis, int32_t count_mode, int32_t* h_
     return WQ_OK;
 }
 
-wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out) {
+namespace {
+// Weights, moments and weight statistics of a saved rule (wq_rule_save / wq_rule_load).
+struct SavedRule {
+    std::vector<double> W;                 // [sum_r][nwc]
+    std::vector<std::vector<double>> mom;  // per built component, [nnz]
+    int32_t n_truncated[5], n_z_identity[5];
+    float setup_ms;
+};
+
+constexpr char kRuleMagic[8] = {'W', 'Q', 'R', 'U', 'L', 'E', '0', '1'};
+struct RuleFileHeader {
+    char magic[8];
+    uint32_t version, comps;
+    int32_t count_mode, max_sweeps;
+    double tol;
+    int64_t n, E, nnz, Q, G, sum_r;
+    int32_t nwc, dim;
+    uint64_t fingerprint;
+    int32_t n_truncated[5], n_z_identity[5];
+    float setup_ms;
+    int32_t pad;
+};
+
+// FNV-1a over the mesh that defines the spline space (coordinates and quads).
+uint64_t basis_fingerprint(const wqi::BasisHost& B) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t bytes) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t k = 0; k < bytes; ++k) {
+            h ^= c[k];
+            h *= 1099511628211ull;
+        }
+    };
+    mix(&B.dim, sizeof(B.dim));
+    mix(&B.n, sizeof(B.n));
+    mix(&B.E, sizeof(B.E));
+    mix(B.xyz.data(), B.xyz.size() * sizeof(double));
+    mix(B.topo.quads.data(), B.topo.quads.size() * sizeof(int32_t));
+    return h;
+}
+}  // namespace
+
+static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, const SavedRule* saved, wq_rule** out) {
     if (!basis || !opts || !out) return WQ_ERR_ARG;
     *out = nullptr;
     wq_ctx* ctx = basis->ctx;
@@ -240,6 +284,7 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     R->max_n_i = B.max_n_i;
     R->tol = tol;
     R->max_sweeps = sweeps;
+    R->count_mode = opts->count_mode;
     wq_status sst = WQ_OK;
     auto bail = [&](wq_status s) {
         delete R;
@@ -433,7 +478,7 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     R->n_sm = std::max(n_sm, 1);
     int n_cta = (int)std::min<int64_t>(n, (int64_t)std::max(n_sm, 1) * 8);
     double* d_scratch = nullptr;
-    if (!dalloc(R, d_scratch, (size_t)per_cta * n_cta, sst)) return bail(sst);
+    if (!saved && !dalloc(R, d_scratch, (size_t)per_cta * n_cta, sst)) return bail(sst);
 
     wqd::Elems& el = R->el;
     el.dim = B.dim;
@@ -464,6 +509,10 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     R->it_wq = {(int64_t)it_wq.size(), R->d_it_wq, R->d_kb_wq};
     R->it_gq = {(int64_t)it_gq.size(), R->d_it_gq, R->d_kb_gq};
     R->ep = {R->d_scat, R->d_gptr, R->d_kscr};
+    R->src_wq = {R->ep, R->d_table2, R->d_W2, nullptr, R->nnz, nc, R->nwc};
+    R->src_gq = {R->ep, R->d_gtable2, nullptr, R->d_gw, R->nnz, nc, R->nwc};
+    R->h_it_wq = it_wq;
+    R->h_kb_wq = kb_wq;
 
     // Gauss-Legendre 4-point rule on [0, 1] (closed form)
     {
@@ -494,7 +543,7 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     if (ce == cudaSuccess)
         ce = wqd::launch_eval(el, R->d_gp_elem, R->G, 1, R->d_gtable, R->d_gx, R->d_gw, R->d_status, st);
     // a4: Gauss moments per component (c = 1)
-    for (int c = 0; c < 5 && ce == cudaSuccess; ++c) {
+    for (int c = 0; c < 5 && ce == cudaSuccess && !saved; ++c) {
         if (R->wcidx[c] < 0) continue;
         wqd::Terms tm;
         tm.nt = 1;
@@ -505,7 +554,7 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     // a5: truncated-SVD weights per component
     std::vector<int32_t> rank(n);
     std::vector<uint8_t> zid(n);
-    for (int c = 0; c < 5 && ce == cudaSuccess; ++c) {
+    for (int c = 0; c < 5 && ce == cudaSuccess && !saved; ++c) {
         if (R->wcidx[c] < 0) continue;
         ce = wqd::launch_tsvd(el, rw, R->d_table, table_comp(R, c), R->d_mom[c], R->d_W, R->nwc, R->wcidx[c], tol,
                               sweeps, d_scratch, per_cta, n_cta, d_rank, d_zid, R->d_status, st);
@@ -520,6 +569,21 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
             }
             R->info.n_truncated[c] = trunc;
             R->info.n_z_identity[c] = zcount;
+        }
+    }
+    if (saved && ce == cudaSuccess) {
+        // weights and moments from the file (host buffers live until the synchronisation below)
+        ce = cudaMemcpyAsync(R->d_W, saved->W.data(), saved->W.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+        int k = 0;
+        for (int c = 0; c < 5 && ce == cudaSuccess; ++c) {
+            if (R->wcidx[c] < 0) continue;
+            ce = cudaMemcpyAsync(R->d_mom[c], saved->mom[k].data(), saved->mom[k].size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, st);
+            ++k;
+        }
+        for (int c = 0; c < 5; ++c) {
+            R->info.n_truncated[c] = saved->n_truncated[c];
+            R->info.n_z_identity[c] = saved->n_z_identity[c];
         }
     }
     // FP32 split copies for the mixed-precision assembly
@@ -544,6 +608,105 @@ wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out
     R->info.sum_r = R->sum_r;
     R->info.max_r = R->max_r;
     R->info.setup_ms = ms;
+    *out = R;
+    return WQ_OK;
+}
+
+wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out) {
+    return rule_build_impl(basis, opts, nullptr, out);
+}
+
+wq_status wq_rule_save(const wq_rule* rule, const char* path) {
+    if (!rule || !path) return WQ_ERR_ARG;
+    wq_ctx* ctx = rule->ctx;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    RuleFileHeader h{};
+    std::memcpy(h.magic, kRuleMagic, 8);
+    h.version = 1;
+    h.comps = rule->comps;
+    h.count_mode = rule->count_mode;
+    h.max_sweeps = rule->max_sweeps;
+    h.tol = rule->tol;
+    h.n = rule->n;
+    h.E = rule->E;
+    h.nnz = rule->nnz;
+    h.Q = rule->Q;
+    h.G = rule->G;
+    h.sum_r = rule->sum_r;
+    h.nwc = rule->nwc;
+    h.dim = rule->dim;
+    h.fingerprint = basis_fingerprint(rule->basis->B);
+    for (int c = 0; c < 5; ++c) {
+        h.n_truncated[c] = rule->info.n_truncated[c];
+        h.n_z_identity[c] = rule->info.n_z_identity[c];
+    }
+    h.setup_ms = rule->info.setup_ms;
+    std::vector<double> buf((size_t)rule->sum_r * rule->nwc);
+    CUDA_TRY(ctx, cudaMemcpy(buf.data(), rule->d_W, buf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, WQ_ERR_ARG, std::string("cannot open for writing: ") + path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    std::vector<double> mb((size_t)rule->nnz);
+    for (int c = 0; c < 5 && ok; ++c) {
+        if (rule->wcidx[c] < 0) continue;
+        if (cudaMemcpy(mb.data(), rule->d_mom[c], mb.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return fail(ctx, WQ_ERR_CUDA, "copying the moments failed");
+        }
+        ok = std::fwrite(mb.data(), sizeof(double), mb.size(), f) == mb.size();
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(ctx, WQ_ERR_ARG, std::string("write failed: ") + path);
+    return WQ_OK;
+}
+
+wq_status wq_rule_load(wq_basis* basis, const char* path, wq_rule** out) {
+    if (!basis || !path || !out) return WQ_ERR_ARG;
+    *out = nullptr;
+    wq_ctx* ctx = basis->ctx;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, WQ_ERR_ARG, std::string("cannot open: ") + path);
+    RuleFileHeader h{};
+    auto close_fail = [&](const std::string& msg) {
+        std::fclose(f);
+        return fail(ctx, WQ_ERR_ARG, msg);
+    };
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kRuleMagic, 8) != 0 || h.version != 1)
+        return close_fail("not a WQ rule file (version 1)");
+    const wqi::BasisHost& B = basis->B;
+    if (h.fingerprint != basis_fingerprint(B) || h.n != B.n || h.E != B.E || h.dim != B.dim ||
+        h.nnz != B.row_ptr[B.n])
+        return close_fail("rule file was saved for a different mesh");
+    if ((h.comps & ~31u) || h.comps == 0 || h.nwc < 1 || h.nwc > 5 || h.sum_r < 0)
+        return close_fail("corrupt rule file header");
+    SavedRule sv;
+    sv.W.resize((size_t)h.sum_r * h.nwc);
+    if (std::fread(sv.W.data(), sizeof(double), sv.W.size(), f) != sv.W.size()) return close_fail("truncated rule file");
+    for (int c = 0; c < 5; ++c)
+        if (h.comps & (1u << c)) {
+            sv.mom.emplace_back((size_t)h.nnz);
+            if (std::fread(sv.mom.back().data(), sizeof(double), (size_t)h.nnz, f) != (size_t)h.nnz)
+                return close_fail("truncated rule file");
+        }
+    std::fclose(f);
+    for (int c = 0; c < 5; ++c) {
+        sv.n_truncated[c] = h.n_truncated[c];
+        sv.n_z_identity[c] = h.n_z_identity[c];
+    }
+    sv.setup_ms = h.setup_ms;
+    wq_rule_opts opts{};
+    opts.comps = h.comps;
+    opts.count_mode = h.count_mode;
+    opts.tsvd_rel_tol = h.tol;
+    opts.max_sweeps = h.max_sweeps;
+    opts.stream = nullptr;
+    wq_rule* R = nullptr;
+    wq_status s = rule_build_impl(basis, &opts, &sv, &R);
+    if (s != WQ_OK) return s;
+    if (R->sum_r != h.sum_r || R->Q != h.Q || R->G != h.G) {
+        wq_rule_destroy(R);
+        return fail(ctx, WQ_ERR_ARG, "rule file does not match the rebuilt point plan");
+    }
     *out = R;
     return WQ_OK;
 }
@@ -627,9 +790,8 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
                                    nullptr, (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
         if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
     } else
-        e = wqd::launch_elem_f32(rule->it_wq, rule->ep, rule->nnz, tm, rule->nc, 0, rule->d_table2, rule->d_W2,
-                                 rule->nwc, nullptr, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32, st,
-                                 evs);
+        e = wqd::launch_elem_f32(rule->it_wq, rule->src_wq, tm, 0, (const double*)d_coef, (float*)d_vals,
+                                 prec == WQ_PREC_F32, st, evs);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
     return WQ_OK;
 }
@@ -650,8 +812,8 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
                                    (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
         if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
     } else
-        e = wqd::launch_elem_f32(rule->it_gq, rule->ep, rule->nnz, tm, rule->nc, 1, rule->d_gtable2, nullptr, 0,
-                                 rule->d_gw, (const double*)d_coef, (float*)d_vals, prec == WQ_PREC_F32, st, evs);
+        e = wqd::launch_elem_f32(rule->it_gq, rule->src_gq, tm, 1, (const double*)d_coef, (float*)d_vals,
+                                 prec == WQ_PREC_F32, st, evs);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
     return WQ_OK;
 }
@@ -686,6 +848,109 @@ wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d
                                             rule->d_table, d_u, d_u_old, dt, k0, k2, f, d_kappa, d_g,
                                             (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("heat fields launch: ") + cudaGetErrorString(e));
+    return WQ_OK;
+}
+
+wq_status wq_batch_create(int32_t k, const wq_rule* const* rules, wq_batch** out) {
+    if (!rules || !out || k < 1 || k > wqd::WQ_BATCH_MAX || !rules[0]) return WQ_ERR_ARG;
+    *out = nullptr;
+    wq_ctx* ctx = rules[0]->ctx;
+    for (int r = 0; r < k; ++r) {
+        if (!rules[r]) return fail(ctx, WQ_ERR_ARG, "null rule in batch");
+        if (rules[r]->ctx->device != ctx->device || rules[r]->comps != rules[0]->comps ||
+            rules[r]->dim != rules[0]->dim)
+            return fail(ctx, WQ_ERR_ARG, "batched rules must share the device, weight components and dimension");
+    }
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    wq_batch* Bt = new (std::nothrow) wq_batch();
+    if (!Bt) return fail(ctx, WQ_ERR_OOM, "host allocation failed");
+    Bt->ctx = ctx;
+    Bt->rules.assign(rules, rules + k);
+    // all tiles, ordered by their number of point chunks (long ones first), then by rule
+    struct T {
+        int4 it;
+        int32_t kb, r;
+    };
+    std::vector<T> all;
+    for (int r = 0; r < k; ++r)
+        for (size_t x = 0; x < rules[r]->h_it_wq.size(); ++x)
+            all.push_back({rules[r]->h_it_wq[x], rules[r]->h_kb_wq[x], r});
+    std::stable_sort(all.begin(), all.end(), [](const T& a, const T& b) {
+        return (((a.it.z >> 8) & 255) + 7) / 8 > (((b.it.z >> 8) & 255) + 7) / 8;
+    });
+    std::vector<int4> item(all.size());
+    std::vector<int32_t> kb(all.size()), irule(all.size());
+    for (size_t x = 0; x < all.size(); ++x) {
+        item[x] = all[x].it;
+        kb[x] = all[x].kb;
+        irule[x] = all[x].r;
+    }
+    std::vector<wqd::ElemSrc> src(k);
+    std::vector<int32_t> gr;
+    std::vector<int64_t> gs;
+    for (int r = 0; r < k; ++r) {
+        src[r] = rules[r]->src_wq;
+        for (int64_t b0 = 0; b0 < rules[r]->nnz; b0 += 512) {
+            gr.push_back(r);
+            gs.push_back(b0);
+        }
+    }
+    auto up = [&](auto*& d, const auto& v) {
+        using E = typename std::decay<decltype(v[0])>::type;
+        void* p = nullptr;
+        const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(E);
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return false;
+        Bt->bufs.push_back({p, bytes});
+        if (!v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
+        d = static_cast<E*>(p);
+        return true;
+    };
+    int4* d_item = nullptr;
+    int32_t *d_kb = nullptr, *d_irule = nullptr, *d_gr = nullptr;
+    int64_t* d_gs = nullptr;
+    wqd::ElemSrc* d_src = nullptr;
+    if (!up(d_item, item) || !up(d_kb, kb) || !up(d_irule, irule) || !up(d_src, src) || !up(d_gr, gr) ||
+        !up(d_gs, gs)) {
+        delete Bt;
+        return fail(ctx, WQ_ERR_OOM, "batch plan upload failed");
+    }
+    Bt->plan = {(int64_t)item.size(), d_item, d_kb, d_irule, d_src, (int64_t)gr.size(), d_gr, d_gs};
+    *out = Bt;
+    return WQ_OK;
+}
+
+void wq_batch_destroy(wq_batch* batch) {
+    if (batch && batch->ctx && batch->ctx->device >= 0) cudaSetDevice(batch->ctx->device);
+    delete batch;
+}
+
+wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* const* h_coefs, double alpha,
+                              int32_t prec, void* const* h_vals, void* stream) {
+    if (!batch || !h_vals) return WQ_ERR_ARG;
+    const int k = (int)batch->rules.size();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == WQ_PREC_F64) {   // the FP64 row kernel, one launch per rule
+        for (int r = 0; r < k; ++r) {
+            wq_status s = wq_assemble(batch->rules[r], op, h_coefs ? h_coefs[r] : nullptr, alpha, prec, h_vals[r],
+                                      stream);
+            if (s != WQ_OK) return s;
+        }
+        return WQ_OK;
+    }
+    if (prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST) return fail(batch->ctx, WQ_ERR_ARG, "unknown precision");
+    wqd::Terms tm;
+    if (!op_terms(batch->rules[0], op, alpha, true, tm))
+        return fail(batch->ctx, WQ_ERR_ARG, "operator needs weight sets that these rules did not build");
+    const double* coefs[wqd::WQ_BATCH_MAX];
+    float* vals[wqd::WQ_BATCH_MAX];
+    for (int r = 0; r < k; ++r) {
+        coefs[r] = h_coefs ? (const double*)h_coefs[r] : nullptr;
+        vals[r] = (float*)h_vals[r];
+        if (!vals[r]) return fail(batch->ctx, WQ_ERR_ARG, "null output in batch");
+    }
+    cudaError_t e = wqd::launch_elem_batch(batch->plan, coefs, vals, k, tm, prec == WQ_PREC_F32, st);
+    if (e != cudaSuccess) return fail(batch->ctx, WQ_ERR_CUDA, std::string("batched assembly: ") + cudaGetErrorString(e));
     return WQ_OK;
 }
 

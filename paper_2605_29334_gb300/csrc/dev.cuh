@@ -64,4 +64,36 @@ struct ElemPlan {
     float2* kscr;
 };
 
+// One rule's data for the FP32 element-major kernels.
+struct ElemSrc {
+    ElemPlan ep;
+    const float2* table2;   // split basis table at the item's points (WQ or Gauss)
+    const float2* W2e;      // element-major split weights (WQ items)
+    const double* gw;       // Gauss weights (Gauss items)
+    int64_t nnz;
+    int nc, nwc;
+};
+
+// Per-call device pointers, passed as a kernel parameter (N = 1 for one rule).
+constexpr int WQ_BATCH_MAX = 256;
+template <int N>
+struct PtrTable {
+    const double* coef[N];
+    float* vals[N];
+};
+
+// Several rules assembled by one launch of each kernel: the concatenated tiles
+// (item / kb / item_rule), the rules' data (src[k], device), and the blocks of the
+// per-entry sums (gblk_rule, gblk_start: 512 entries of one rule per block).
+struct BatchPlan {
+    int64_t n_items;
+    const int4* item;
+    const int32_t* kb;
+    const int32_t* item_rule;
+    const ElemSrc* src;
+    int64_t n_gblocks;
+    const int32_t* gblk_rule;
+    const int64_t* gblk_start;
+};
+
 }  // namespace wqd

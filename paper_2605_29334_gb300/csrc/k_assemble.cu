@@ -208,11 +208,9 @@ __device__ __forceinline__ float pow2_above_4x(float x) {
     return __uint_as_float(((bits >> 23) + 1u) << 23);
 }
 
-template <int NT, bool COMP, bool GAUSS>
+template <int NT, bool COMP, bool GAUSS, bool BATCH, int NP>
 __global__ void __launch_bounds__(EL_NWARP * 32, 6)
-    k_elem_f32(ElemItems it, ElemPlan ep, TermsF tm, int nc, const float2* __restrict__ table2,
-               const float2* __restrict__ W2e, int nwc, const double* __restrict__ gw,
-               const double* __restrict__ coef) {
+    k_elem_f32(ElemItems it, ElemSrc one, BatchPlan bp, const __grid_constant__ PtrTable<NP> pt, TermsF tm) {
     constexpr int QC = NT <= 2 ? 12 : 8;            // most points per staged chunk
     __shared__ __align__(16) float2 sT[EL_NWARP][QC * NT * 16];   // trial side [point][term][column]
     __shared__ __align__(16) float2 sS[EL_NWARP][QC * NT * 16];   // test side, then the products s
@@ -221,9 +219,17 @@ __global__ void __launch_bounds__(EL_NWARP * 32, 6)
     __shared__ __align__(16) int32_t sSlot[EL_NWARP][256];        // destination slots of the tile
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * EL_NWARP + wib;
-    if (k >= it.n) return;
-    const int4 d = it.item[k];
-    const int kb = it.kb[k];
+    if (k >= (BATCH ? bp.n_items : it.n)) return;
+    const int4 d = BATCH ? bp.item[k] : it.item[k];
+    const int kb = BATCH ? bp.kb[k] : it.kb[k];
+    const int ri = BATCH ? bp.item_rule[k] : 0;
+    const ElemSrc src = BATCH ? bp.src[ri] : one;
+    const ElemPlan ep = src.ep;
+    const int nc = src.nc, nwc = src.nwc;
+    const float2* __restrict__ table2 = src.table2;
+    const float2* __restrict__ W2e = src.W2e;
+    const double* __restrict__ gw = src.gw;
+    const double* __restrict__ coef = pt.coef[BATCH ? ri : 0];
     const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
     float2* T_ = sT[wib];
     float2* S_ = sS[wib];
@@ -389,12 +395,18 @@ __global__ void __launch_bounds__(EL_NWARP * 32, 6)
 // Phase 2: one thread per two consecutive CSR entries.  Their slots are contiguous;
 // they are fetched 8 at a time, all loads in flight together, and each is added
 // with TwoSum to the entry it belongs to (in slot order, i.e. support order).
-template <bool COMP>
-__global__ void __launch_bounds__(256) k_gather_f32(int64_t nnz, const int32_t* __restrict__ gptr,
-                                                    const float2* __restrict__ kscr, float* __restrict__ vals) {
+template <bool COMP, bool BATCH, int NP>
+__global__ void __launch_bounds__(256) k_gather_f32(ElemSrc one, BatchPlan bp, const __grid_constant__ PtrTable<NP> pt) {
     // launched as a programmatic dependent of the element kernel: wait for its results
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    const int64_t n = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int ri = BATCH ? bp.gblk_rule[blockIdx.x] : 0;
+    const int64_t base = BATCH ? bp.gblk_start[blockIdx.x] : (int64_t)blockIdx.x * 512;
+    const ElemSrc src = BATCH ? bp.src[ri] : one;
+    const int64_t nnz = src.nnz;
+    const int32_t* __restrict__ gptr = src.ep.gptr;
+    const float2* __restrict__ kscr = src.ep.kscr;
+    float* __restrict__ vals = pt.vals[BATCH ? ri : 0];
+    const int64_t n = base + 2 * threadIdx.x;
     if (n >= nnz) return;
     const int c0 = gptr[n], c1 = gptr[n + 1], c2 = gptr[min(n + 2, nnz)];
     float hi0 = 0.0f, lo0 = 0.0f, hi1 = 0.0f, lo1 = 0.0f;
@@ -423,15 +435,7 @@ __global__ void __launch_bounds__(256) k_gather_f32(int64_t nnz, const int32_t* 
     if (n + 1 < nnz) vals[n + 1] = hi1 + lo1;
 }
 
-cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz, const Terms& tm, int nc,
-                            int gauss, const float2* table2, const float2* W2e, int nwc, const double* gw,
-                            const double* coef, float* vals, bool compensated, cudaStream_t st,
-                            cudaEvent_t* evs) {
-    if (evs) cudaEventRecord(evs[0], st);
-    if (nnz == 0) {
-        if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
-        return cudaSuccess;
-    }
+static TermsF terms_f(const Terms& tm) {
     TermsF tf{};
     for (int t = 0; t < tm.nt; ++t) {
         tf.wc[t] = tm.t[t].wc;
@@ -441,15 +445,25 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz
         tf.shi[t] = (float)tm.t[t].scale;
         tf.slo[t] = (float)(tm.t[t].scale - (double)tf.shi[t]);
     }
-    const unsigned eb = (unsigned)((it.n + EL_NWARP - 1) / EL_NWARP);
-#define WQ_EL_CASE(N, C)                                                                                      \
-    do {                                                                                                      \
-        if (gauss)                                                                                            \
-            k_elem_f32<N, C, true><<<eb, EL_NWARP * 32, 0, st>>>(it, ep, tf, nc, table2, W2e, nwc, gw, coef); \
-        else                                                                                                  \
-            k_elem_f32<N, C, false><<<eb, EL_NWARP * 32, 0, st>>>(it, ep, tf, nc, table2, W2e, nwc, gw, coef); \
+    return tf;
+}
+
+// Element kernel, then the per-entry sums as a programmatic dependent launch (its
+// grid is set up while the element kernel drains and waits with griddepcontrol.wait).
+template <bool BATCH, int NP>
+static cudaError_t launch_elem_pair(const ElemItems& it, const ElemSrc& one, const BatchPlan& bp,
+                                    const PtrTable<NP>& pt, const Terms& tm, int gauss, bool compensated,
+                                    int64_t n_items, int64_t n_gblocks, cudaStream_t st, cudaEvent_t* evs) {
+    const TermsF tf = terms_f(tm);
+    const unsigned eb = (unsigned)((n_items + EL_NWARP - 1) / EL_NWARP);
+#define WQ_EL_CASE(N, C)                                                                                  \
+    do {                                                                                                  \
+        if (gauss)                                                                                        \
+            k_elem_f32<N, C, true, BATCH, NP><<<eb, EL_NWARP * 32, 0, st>>>(it, one, bp, pt, tf);         \
+        else                                                                                              \
+            k_elem_f32<N, C, false, BATCH, NP><<<eb, EL_NWARP * 32, 0, st>>>(it, one, bp, pt, tf);        \
     } while (0)
-    if (it.n > 0) {
+    if (n_items > 0) {
         switch (tm.nt * 2 + (compensated ? 1 : 0)) {
             case 2: WQ_EL_CASE(1, false); break;
             case 3: WQ_EL_CASE(1, true); break;
@@ -465,10 +479,9 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (evs) cudaEventRecord(evs[1], st);
-    // programmatic dependent launch: the sums' grid is set up while the element
-    // kernel drains, and waits (griddepcontrol.wait) for its completion
+    if (n_gblocks == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)((nnz + 511) / 512));
+    cfg.gridDim = dim3((unsigned)n_gblocks);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
@@ -478,12 +491,39 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (compensated)
-        e = cudaLaunchKernelEx(&cfg, k_gather_f32<true>, nnz, ep.gptr, (const float2*)ep.kscr, vals);
+        e = cudaLaunchKernelEx(&cfg, k_gather_f32<true, BATCH, NP>, one, bp, pt);
     else
-        e = cudaLaunchKernelEx(&cfg, k_gather_f32<false>, nnz, ep.gptr, (const float2*)ep.kscr, vals);
-    if (e != cudaSuccess) return e;
+        e = cudaLaunchKernelEx(&cfg, k_gather_f32<false, BATCH, NP>, one, bp, pt);
+    return e;
+}
+
+cudaError_t launch_elem_f32(const ElemItems& it, const ElemSrc& src, const Terms& tm, int gauss, const double* coef,
+                            float* vals, bool compensated, cudaStream_t st, cudaEvent_t* evs) {
+    if (evs) cudaEventRecord(evs[0], st);
+    cudaError_t e = cudaSuccess;
+    if (src.nnz > 0) {
+        PtrTable<1> pt;
+        pt.coef[0] = coef;
+        pt.vals[0] = vals;
+        e = launch_elem_pair<false, 1>(it, src, BatchPlan{}, pt, tm, gauss, compensated, it.n, (src.nnz + 511) / 512,
+                                       st, evs);
+    } else if (evs) {
+        cudaEventRecord(evs[1], st);
+    }
     if (evs) cudaEventRecord(evs[2], st);
-    return cudaGetLastError();
+    return e;
+}
+
+cudaError_t launch_elem_batch(const BatchPlan& bp, const double* const* coefs, float* const* vals, int k,
+                              const Terms& tm, bool compensated, cudaStream_t st) {
+    if (k < 1 || k > WQ_BATCH_MAX) return cudaErrorInvalidValue;
+    PtrTable<WQ_BATCH_MAX> pt{};
+    for (int r = 0; r < k; ++r) {
+        pt.coef[r] = coefs[r];
+        pt.vals[r] = vals[r];
+    }
+    return launch_elem_pair<true, WQ_BATCH_MAX>(ElemItems{}, ElemSrc{}, bp, pt, tm, 0, compensated, bp.n_items,
+                                                bp.n_gblocks, st, nullptr);
 }
 
 // Element-major split copy of the weights: row r of W (test function i, point q

@@ -46,10 +46,13 @@ cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm,
 // element tiles into the slot buffer, then one sum per CSR entry.  WQ items
 // (gauss = 0) read the test side from the element-major weights W2e; Gauss items
 // (gauss = 1) from the table, times the Gauss weights gw.  1..4 terms; float CSR values.
-cudaError_t launch_elem_f32(const ElemItems& it, const ElemPlan& ep, int64_t nnz, const Terms& tm, int nc,
-                            int gauss, const float2* table2, const float2* W2e, int nwc, const double* gw,
-                            const double* coef, float* vals, bool compensated, cudaStream_t st,
-                            cudaEvent_t* evs = nullptr);
+cudaError_t launch_elem_f32(const ElemItems& it, const ElemSrc& src, const Terms& tm, int gauss, const double* coef,
+                            float* vals, bool compensated, cudaStream_t st, cudaEvent_t* evs = nullptr);
+
+// The same for k <= WQ_BATCH_MAX rules with one launch of each kernel (WQ items;
+// the rules share their weight components and dimension, so one TermsF serves all).
+cudaError_t launch_elem_batch(const BatchPlan& bp, const double* const* coefs, float* const* vals, int k,
+                              const Terms& tm, bool compensated, cudaStream_t st);
 
 // Element-major split copy of the weights (W2e[dst[r]] = split(W[r]), nwc columns).
 cudaError_t launch_split_rows(const double* W, const int32_t* dst, float2* W2e, int64_t rows, int nwc, int n_sm,

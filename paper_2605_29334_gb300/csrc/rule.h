@@ -37,6 +37,7 @@ struct wq_rule {
     int max_n_i = 0, max_r = 0;
     double tol = 1e-12;
     int max_sweeps = 40;
+    int count_mode = 0;
     std::vector<wqi::DevBuf> bufs;
     // device arrays
     int32_t *d_m = nullptr, *d_nsub = nullptr, *d_side = nullptr, *d_pt_elem = nullptr, *d_gp_elem = nullptr;
@@ -56,6 +57,9 @@ struct wq_rule {
     int64_t kscr_len = 0;
     wqd::ElemItems it_wq{}, it_gq{};
     wqd::ElemPlan ep{};
+    wqd::ElemSrc src_wq{}, src_gq{};
+    std::vector<int4> h_it_wq;          // host copies of the WQ tiles (batched assembly)
+    std::vector<int32_t> h_kb_wq;
     int n_sm = 1;
     uint16_t* d_pos = nullptr;
     uint8_t* d_il = nullptr;
@@ -81,6 +85,18 @@ struct wq_rule {
 
     ~wq_rule() {
         for (auto ev : tev) cudaEventDestroy(ev);
+        for (auto& b : bufs)
+            if (b.p) cudaFree(b.p);
+    }
+};
+
+// Several rules assembled together (wq_batch_create / wq_assemble_batched).
+struct wq_batch {
+    wq_ctx* ctx = nullptr;
+    std::vector<const wq_rule*> rules;
+    std::vector<wqi::DevBuf> bufs;
+    wqd::BatchPlan plan{};
+    ~wq_batch() {
         for (auto& b : bufs)
             if (b.p) cudaFree(b.p);
     }

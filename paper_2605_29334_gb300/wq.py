@@ -85,6 +85,12 @@ EXPORTS = {
                                  C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_basis_functions": (C.c_int, [C.c_void_p, C.c_void_p]),
     "wq_rule_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "wq_rule_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "wq_batch_create": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "wq_batch_destroy": (None, [C.c_void_p]),
+    "wq_assemble_batched": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.c_double, C.c_int32,
+                                      C.POINTER(C.c_void_p), C.c_void_p]),
+    "wq_rule_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_void_p)]),
     "wq_rule_kernel_times": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
 }
 
@@ -216,22 +222,37 @@ class Basis:
 class Rule:
     """wq_rule_build: placement, basis tables, Gauss moments and TSVD weights on the device."""
 
-    def __init__(self, basis, comps=(COMP_N, COMP_X, COMP_Y), tol=1e-12, max_sweeps=0, stream=None):
+    def __init__(self, basis, comps=(COMP_N, COMP_X, COMP_Y), tol=1e-12, max_sweeps=0, stream=None, path=None):
+        """Build the rule, or (path given) load weights and moments saved by save()."""
         self.basis = basis
         self.ctx = basis.ctx
-        mask = 0
-        for c in comps:
-            mask |= 1 << int(c)
-        self.comps = tuple(comps)
-        opts = RuleOpts(mask, 0, float(tol), int(max_sweeps), _stream_handle(stream))
         h = C.c_void_p()
-        self.ctx.check(lib().wq_rule_build(basis.h, C.byref(opts), C.byref(h)))
-        self.h = h
+        if path is not None:
+            self.ctx.check(lib().wq_rule_load(basis.h, os.fsencode(path), C.byref(h)))
+            self.h = h
+        else:
+            mask = 0
+            for c in comps:
+                mask |= 1 << int(c)
+            opts = RuleOpts(mask, 0, float(tol), int(max_sweeps), _stream_handle(stream))
+            self.ctx.check(lib().wq_rule_build(basis.h, C.byref(opts), C.byref(h)))
+            self.h = h
         info = RuleInfo()
         self.ctx.check(lib().wq_rule_info_get(h, C.byref(info)))
         self.info = info
+        if path is not None:
+            comps = [c for c in range(5) if self._has_comp(c)]
+        self.comps = tuple(comps)
         self.Q, self.G, self.n, self.nnz = info.n_points, info.n_gauss, basis.n, basis.nnz
         self.basis_dim = basis.dim
+
+    def _has_comp(self, c):
+        w, wp = C.c_void_p(), C.c_void_p()
+        return lib().wq_rule_weights(self.h, int(c), C.byref(w), C.byref(wp)) == 0
+
+    def save(self, path):
+        """Write the weights, moments and weight statistics (wq_rule_save)."""
+        self.ctx.check(lib().wq_rule_save(self.h, os.fsencode(path)))
 
     def points(self):
         p, q = C.c_void_p(), C.c_int64()
@@ -356,3 +377,33 @@ class Rule:
         if getattr(self, "h", None):
             lib().wq_rule_destroy(self.h)
             self.h = None
+
+
+class Batch:
+    """wq_batch_create: several rules assembled by one launch per kernel."""
+
+    def __init__(self, rules):
+        self.rules = list(rules)
+        self.ctx = self.rules[0].ctx
+        arr = (C.c_void_p * len(self.rules))(*[r.h for r in self.rules])
+        h = C.c_void_p()
+        self.ctx.check(lib().wq_batch_create(len(self.rules), arr, C.byref(h)))
+        self.h = h
+
+    def assemble(self, op, coefs, alpha=0.0, prec=PREC_F32, outs=None, stream=None):
+        import torch
+        k = len(self.rules)
+        if outs is None:
+            dt = torch.float64 if prec == PREC_F64 else torch.float32
+            outs = [torch.empty(r.nnz, dtype=dt, device="cuda") for r in self.rules]
+        cp = (C.c_void_p * k)(*[c.data_ptr() if c is not None else None for c in coefs])
+        vp = (C.c_void_p * k)(*[o.data_ptr() for o in outs])
+        self.ctx.check(lib().wq_assemble_batched(self.h, int(op), cp, float(alpha), int(prec), vp,
+                                                 _stream_handle(stream)))
+        return outs
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().wq_batch_destroy(self.h)
+            self.h = None
+

@@ -503,3 +503,39 @@ def gaussian_bumps(seed, lo, hi, n=8, amp=0.5, width=0.1):
         d2 = np.sum((x[..., None, :] - c) ** 2, axis=-1)
         return amp * np.sum(np.exp(-d2 / (2 * s * s)), axis=-1)
     return f
+
+
+def instances(seed, count, e_min=500, e_max=50000):
+    """Independent planar instances of uneven size for batched assembly.
+
+    Element counts are drawn log-uniform in [e_min, e_max].  Each instance is
+    either a rotated-core mesh (nx, ny in 3..10, an even number of EPs of valence
+    3/5/6 up to 20) or a disk around one EP of valence 3..8, refined until its
+    size is nearest to the drawn count.  Returns a list of mesh dicts.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(count):
+        target = float(np.exp(rng.uniform(np.log(e_min), np.log(e_max))))
+        sub = int(rng.integers(1 << 30))
+        if rng.uniform() < 0.6:
+            nx, ny = int(rng.integers(3, 11)), int(rng.integers(3, 11))
+            interior = (nx - 1) * (ny - 1)
+            n_ep = int(min(20, max(2, 2 * int(rng.integers(1, max(2, interior // 3) + 1)))))
+            n_ep = min(n_ep, 2 * (interior // 3)) if interior >= 6 else 0
+            base = nx * ny
+            levels = int(np.clip(np.round(np.log(target / base) / np.log(4.0)), 0, 6))
+            mesh = None
+            while mesh is None and n_ep >= 2:
+                try:
+                    mesh = rotated(nx=nx, ny=ny, n_ep=n_ep, levels=levels, seed=sub, max_tries=300)
+                except RuntimeError:
+                    n_ep -= 2                       # fewer EPs when none can be drawn
+            out.append(mesh if mesh is not None else grid(nx, ny, seed=sub, jitter=0.02, levels=levels))
+        else:
+            mu = int(rng.integers(3, 9))
+            n = int(rng.integers(3, 7))
+            base = mu * n * n
+            levels = int(np.clip(np.round(np.log(target / base) / np.log(4.0)), 0, 6))
+            out.append(disk(mu=mu, n=n, seed=sub, levels=levels))
+    return out
