@@ -238,9 +238,10 @@ def bench_ours(args, rank, world):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": kname, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     else:
-        # the element-block kernel is bound by FP32 instruction issue: 12 FP32 instructions per
-        # split product with TwoSum (3 without); peak = 152 SMs x 128 FP32 lanes x max SM clock
-        per = 12 if prec == wq.PREC_F32 else 3
+        # the element-block kernel is bound by instruction issue: 6 FP32 instructions per split
+        # product with the extraction-compensated sum (3 without); peak = 152 SMs x 128 FP32
+        # lanes x max SM clock
+        per = 6 if prec == wq.PREC_F32 else 3
         kname = "k_elem_f32<2,%d,0>" % (1 if prec == wq.PREC_F32 else 0)
         peak = 152 * 128 * sm_mhz * 1e6 / 1e12
         achieved = per * work["products"] / t_k1 / 1e12
@@ -274,13 +275,123 @@ def bench_ours(args, rank, world):
     }
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
+    if not args.no_configs:
+        res["other_configs"] = other_configs(ctx, flush, max(args.steps // 20, 20), args.warmup)
     return res
+
+
+def _timed_pair(fn_wq, fn_gq, out_wq, out_gq, steps, warmup, flush):
+    import torch
+    t_wq = float(np.median(time_steps(lambda: fn_wq(out_wq), steps, warmup, flush)))
+    t_gq = float(np.median(time_steps(lambda: fn_gq(out_gq), steps, warmup, flush)))
+    torch.cuda.synchronize()
+    return t_wq, t_gq
+
+
+def other_configs(ctx, flush, steps, warmup):
+    """The other workloads of the method, same protocol (assembly only, L2 flushed, CUDA
+    events, median): WQ against Gauss on the same GPU at FP32 (compensated) and FP64,
+    with the FP32 error against the FP64 result.  Config 5 is a reduced batch (16
+    instances of 500-5,000 elements instead of 256 of 500-50,000), assembled by one
+    launch pair and compared with one call per instance."""
+    import torch
+    from paper_2605_29334_gb300 import wq
+    from wq_synth import meshes
+    out = {}
+
+    def one(name, mesh, comps, op, alpha, coef_fn):
+        t0 = time.perf_counter()
+        b = wq.Basis(ctx, mesh)
+        r = wq.Rule(b, comps=comps)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        cq = torch.tensor(coef_fn(r.points().cpu().numpy()), device="cuda")
+        cg = torch.tensor(coef_fn(r.gauss_points().cpu().numpy()), device="cuda")
+        o32 = [torch.empty(r.nnz, dtype=torch.float32, device="cuda") for _ in range(2)]
+        o64 = [torch.empty(r.nnz, dtype=torch.float64, device="cuda") for _ in range(2)]
+        f32 = _timed_pair(lambda o: r.assemble(op, cq, alpha=alpha, prec=wq.PREC_F32, out=o),
+                          lambda o: r.gq_assemble(op, cg, alpha=alpha, prec=wq.PREC_F32, out=o),
+                          o32[0], o32[1], steps, warmup, flush)
+        f64 = _timed_pair(lambda o: r.assemble(op, cq, alpha=alpha, prec=wq.PREC_F64, out=o),
+                          lambda o: r.gq_assemble(op, cg, alpha=alpha, prec=wq.PREC_F64, out=o),
+                          o64[0], o64[1], steps, warmup, flush)
+        a64 = o64[0].cpu().numpy()
+        err = float(np.max(np.abs(o32[0].cpu().numpy().astype(np.float64) - a64)) / np.max(np.abs(a64)))
+        out[name] = {"n_elements": b.E, "nnz": r.nnz, "n_points": r.Q, "n_gauss": r.G,
+                     "wq_f32_nnz_per_s": r.nnz / f32[0] * 1e3, "gq_f32_nnz_per_s": r.nnz / f32[1] * 1e3,
+                     "wq_f64_nnz_per_s": r.nnz / f64[0] * 1e3, "gq_f64_nnz_per_s": r.nnz / f64[1] * 1e3,
+                     "speedup_f32": f32[1] / f32[0], "speedup_f64": f64[1] / f64[0],
+                     "f32_rel_err_vs_f64": err, "setup_s": setup_s}
+        return b, r, cq
+
+    disk = meshes.disk(mu=5, n=6)
+    one("1_disk_mu5_mass_stiffness", disk, [wq.COMP_N, wq.COMP_X, wq.COMP_Y], wq.OP_HEAT_S, 1.0,
+        meshes.kappa_sines)
+    sph = meshes.cube_sphere(pre=3, levels=3)
+    one("3_sphere_biharmonic", sph, [wq.COMP_N, wq.COMP_LAP], wq.OP_BIHARM, 0.0,
+        lambda x: 1.0 + 0.25 * x[:, 0] * x[:, 1] + 0.1 * x[:, 2])
+    heat = make_mesh(levels=5)
+    u0 = meshes.gaussian_bumps(4001, heat["xyz"].min(0), heat["xyz"].max(0))
+    b4, r4, _ = one("4_heat_tangent_L5", heat, [wq.COMP_N, wq.COMP_X, wq.COMP_Y], wq.OP_HEAT_S, 100.0,
+                    lambda x: 1.0 + u0(x) ** 2)
+    # config 4: 20 Newton re-assemblies (point data, residual, tangent) replayed from one CUDA graph
+    u = torch.tensor(u0(b4.ctrl()), device="cuda")
+    u_old = u.clone()
+    kappa = torch.empty(r4.Q, dtype=torch.float64, device="cuda")
+    g = torch.empty((3, r4.Q), dtype=torch.float64, device="cuda")
+    res_v = torch.empty(r4.n, dtype=torch.float64, device="cuda")
+    S = torch.empty(r4.nnz, dtype=torch.float32, device="cuda")
+
+    def newton_reassembly():
+        for _ in range(20):
+            r4.heat_fields(u, u_old, 1e-2, 1.0, 1.0, 0.0, kappa=kappa, g=g)
+            r4.apply([wq.COMP_N, wq.COMP_X, wq.COMP_Y], g, out=res_v)
+            r4.assemble(wq.OP_HEAT_S, kappa, alpha=100.0, prec=wq.PREC_F32, out=S)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        newton_reassembly()
+    torch.cuda.current_stream().wait_stream(st)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        newton_reassembly()
+    tg = float(np.median(time_steps(graph.replay, 10, 2, flush)))
+    out["4_heat_tangent_L5"]["newton_20_iterations_graph_ms"] = tg
+    # config 5 (reduced): batched against per-instance calls and Gauss
+    ms = meshes.instances(5001, 16, 500, 5000)
+    bases = [wq.Basis(ctx, m) for m in ms]
+    rules = [wq.Rule(bb, comps=[wq.COMP_N, wq.COMP_X, wq.COMP_Y]) for bb in bases]
+    cqs = [torch.tensor(meshes.kappa_sines(rr.points().cpu().numpy()), device="cuda") for rr in rules]
+    cgs = [torch.tensor(meshes.kappa_sines(rr.gauss_points().cpu().numpy()), device="cuda") for rr in rules]
+    outs = [torch.empty(rr.nnz, dtype=torch.float32, device="cuda") for rr in rules]
+    batch = wq.Batch(rules)
+    nnz5 = 2 * sum(rr.nnz for rr in rules)             # mass + stiffness
+    def b_wq():
+        batch.assemble(wq.OP_MASS, cqs, prec=wq.PREC_F32, outs=outs)
+        batch.assemble(wq.OP_STIFF, cqs, prec=wq.PREC_F32, outs=outs)
+    def per_wq():
+        for rr, c, o in zip(rules, cqs, outs):
+            rr.assemble(wq.OP_MASS, c, prec=wq.PREC_F32, out=o)
+            rr.assemble(wq.OP_STIFF, c, prec=wq.PREC_F32, out=o)
+    def per_gq():
+        for rr, c, o in zip(rules, cgs, outs):
+            rr.gq_assemble(wq.OP_MASS, c, prec=wq.PREC_F32, out=o)
+            rr.gq_assemble(wq.OP_STIFF, c, prec=wq.PREC_F32, out=o)
+    tb = float(np.median(time_steps(b_wq, steps, warmup, flush)))
+    tp = float(np.median(time_steps(per_wq, steps, warmup, flush)))
+    tq = float(np.median(time_steps(per_gq, steps, warmup, flush)))
+    out["5_batched_16_instances"] = {"n_instances": len(rules), "n_elements": int(sum(bb.E for bb in bases)),
+                                     "nnz_mass_plus_stiffness": nnz5,
+                                     "wq_f32_batched_nnz_per_s": nnz5 / tb * 1e3,
+                                     "wq_f32_per_instance_nnz_per_s": nnz5 / tp * 1e3,
+                                     "gq_f32_per_instance_nnz_per_s": nnz5 / tq * 1e3}
+    return out
 
 
 # DRAM bytes (read + write) of one launch of the element-block kernel on this workload,
 # from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md), valid for the kernel
 # source it was taken on.
-ELEM_TRAFFIC = {"source_sha1": "d1a9be980e3633021aa0296aa8ba544841c07ea2", "k_elem_f32<2,1,0>": 60484352}
+ELEM_TRAFFIC = {"source_sha1": "a8e14ea017b9e64fb634bfc00456a00196dc0d84", "k_elem_f32<2,1,0>": 60780032}
 
 
 def _kernel_source_sha1():
@@ -370,6 +481,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "f32", "f32_fast", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (configs 1, 3, 4, 5)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

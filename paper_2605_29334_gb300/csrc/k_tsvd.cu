@@ -7,7 +7,7 @@
 // global scratch slice:
 //  1. gather A^T row-major by function (At[a][q]) and z from the point tables;
 //  2. one-sided (Hestenes) Jacobi on the n_i vectors At[a] (length r_i), round-
-//     robin pairs, one warp per pair, accumulating the rotations in Jt (so that
+//     robin pairs, four lanes per pair, accumulating the rotations in Jt (so that
 //     A^T J = [s_k v_k], U = J);  a sweep cap ends it with a status flag;
 //  3. s_k = |At[k]|, keep s_k >= tol s_max;  g = S_t^{-1} U_t^T b;
 //  4. G = Z V_t (columns z * At[k] / s_k), Householder QR G = Q R, then
@@ -72,15 +72,25 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
         zero_z = __syncthreads_or(zero_z);
         if (zero_z)
             for (int q = tid; q < r; q += bd) z[q] = 1.0;
-        // 2. one-sided Jacobi
+        // 2. one-sided Jacobi: groups of JG lanes per rotation pair (8 pairs per warp);
+        //    zeta = (be - al) / (2 ga) in FP64, the tangent from it in FP32 (hypotf; t =
+        //    1/(2 zeta) beyond 1e30), cos/sin in FP64 from that tangent (c = (1 + t^2)^-1/2
+        //    by two Newton steps from an FP32 seed, s = c t): every applied rotation is
+        //    orthogonal to FP64 rounding; the FP32 angle only costs convergence speed.
         const int np = (n + 1) & ~1;
         const double tolJ = fmax(2.220446049250313e-16 * sqrt((double)r), 1e-15);
+        const double tol2 = tolJ * tolJ;
+        constexpr int JG = 4;
+        const int gl = lane & (JG - 1), grp = lane / JG;
+        const int per_pass = nwarp * (32 / JG);
+        const int npairs = np / 2;
         int converged = (n < 2);
         for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
             int rotated = 0;
             for (int rnd = 0; rnd < np - 1; ++rnd) {
-                for (int k = warp; k < np / 2; k += nwarp) {
-                    int p, q;
+                for (int kb = 0; kb < npairs; kb += per_pass) {
+                    const int k = kb + warp * (32 / JG) + grp;
+                    int p = 0, q = 0;
                     if (k == 0) {
                         p = rnd;
                         q = np - 1;
@@ -88,34 +98,48 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
                         p = (rnd + k) % (np - 1);
                         q = (rnd - k + (np - 1)) % (np - 1);
                     }
-                    if (p >= n || q >= n) continue;
-                    double* ap = At + (int64_t)p * r;
-                    double* aq = At + (int64_t)q * r;
+                    const bool valid = k < npairs && p < n && q < n;
+                    double* ap = At + (int64_t)(valid ? p : 0) * r;
+                    double* aq = At + (int64_t)(valid ? q : 0) * r;
                     double al = 0.0, be = 0.0, ga = 0.0;
-                    for (int x = lane; x < r; x += 32) {
-                        const double u = ap[x], w = aq[x];
-                        al += u * u;
-                        be += w * w;
-                        ga += u * w;
-                    }
-                    al = warp_sum(al);
-                    be = warp_sum(be);
-                    ga = warp_sum(ga);
-                    if (al > 0.0 && be > 0.0 && fabs(ga) > tolJ * sqrt(al * be)) {
-                        const double zeta = (be - al) / (2.0 * ga);
-                        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-                        for (int x = lane; x < r; x += 32) {
+                    if (valid)
+                        for (int x = gl; x < r; x += JG) {
                             const double u = ap[x], w = aq[x];
-                            ap[x] = c * u - sn * w;
-                            aq[x] = sn * u + c * w;
+                            al = fma(u, u, al);
+                            be = fma(w, w, be);
+                            ga = fma(u, w, ga);
+                        }
+#pragma unroll
+                    for (int o = JG / 2; o >= 1; o >>= 1) {
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                    }
+                    if (valid && al > 0.0 && be > 0.0 && ga * ga > tol2 * (al * be)) {
+                        const double z = (be - al) / (2.0 * ga);
+                        double t;
+                        if (fabs(z) < 1e30) {
+                            const float zf = (float)z;
+                            t = (double)(copysignf(1.0f, zf) / (fabsf(zf) + hypotf(1.0f, zf)));
+                        } else {
+                            t = 0.5 / z;
+                        }
+                        const double qq = fma(t, t, 1.0);
+                        double c = (double)rsqrtf((float)qq);
+                        c = c * fma(-0.5 * qq, c * c, 1.5);
+                        c = c * fma(-0.5 * qq, c * c, 1.5);
+                        const double sn = c * t;
+                        for (int x = gl; x < r; x += JG) {
+                            const double u = ap[x], w = aq[x];
+                            ap[x] = fma(c, u, -sn * w);
+                            aq[x] = fma(sn, u, c * w);
                         }
                         double* jp = Jt + (int64_t)p * n;
                         double* jq = Jt + (int64_t)q * n;
-                        for (int x = lane; x < n; x += 32) {
+                        for (int x = gl; x < n; x += JG) {
                             const double u = jp[x], w = jq[x];
-                            jp[x] = c * u - sn * w;
-                            jq[x] = sn * u + c * w;
+                            jp[x] = fma(c, u, -sn * w);
+                            jq[x] = fma(sn, u, c * w);
                         }
                         rotated = 1;
                     }
