@@ -413,12 +413,16 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     };
     make_items(false, it_wq, kb_wq);
     make_items(true, it_gq, kb_gq);
-    std::vector<int32_t> wrow_dst(w_ptr[n]), scat(kptr[E]), gptr(R->nnz + 1, 0);
+    if (R->Q > INT32_MAX) return bail(fail(ctx, WQ_ERR_ARG, "too many points for 32-bit point indices"));
+    std::vector<int32_t> wrow_dst(w_ptr[n]), pt_of_w(w_ptr[n]), scat(kptr[E]), gptr(R->nnz + 1, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t r = w_ptr[i];
         for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
             const int32_t e = B.supp[s];
-            for (int q = 0; q < side[e] * side[e]; ++q) wrow_dst[r++] = (int32_t)(wbase[e] + (int64_t)q * m[e] + il[s]);
+            for (int q = 0; q < side[e] * side[e]; ++q) {
+                pt_of_w[r] = (int32_t)(pt_ptr[e] + q);
+                wrow_dst[r++] = (int32_t)(wbase[e] + (int64_t)q * m[e] + il[s]);
+            }
             for (int b = 0; b < m[e]; ++b) ++gptr[B.row_ptr[i] + pos[pos_ptr[s] + b] + 1];
         }
     }
@@ -454,6 +458,7 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         !upload(R, R->d_it_wq, it_wq, sst) || !upload(R, R->d_kb_wq, kb_wq, sst) ||
         !upload(R, R->d_it_gq, it_gq, sst) || !upload(R, R->d_kb_gq, kb_gq, sst) ||
         !upload(R, R->d_wrow_dst, wrow_dst, sst) || !upload(R, R->d_scat, scat, sst) ||
+        !upload(R, R->d_pt_of_w, pt_of_w, sst) ||
         !upload(R, R->d_gptr, gptr, sst))
         return bail(sst);
     if (!dalloc(R, R->d_table, (size_t)bt_ptr[E], sst) || !dalloc(R, R->d_gtable, (size_t)gbt_ptr[E], sst) ||
@@ -835,7 +840,7 @@ wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps,
             return fail(rule->ctx, WQ_ERR_ARG, "wq_apply: weight component not built into this rule");
         wc[t] = rule->wcidx[h_comps[t]];
     }
-    cudaError_t e = wqd::launch_apply(rule->rw, rule->d_desc_wq, n_terms, make_int4(wc[0], wc[1], wc[2], wc[3]),
+    cudaError_t e = wqd::launch_apply(rule->rw, rule->d_pt_of_w, n_terms, make_int4(wc[0], wc[1], wc[2], wc[3]),
                                       rule->d_W, rule->nwc, d_g, rule->Q, d_y, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("apply launch: ") + cudaGetErrorString(e));
     return WQ_OK;

@@ -188,39 +188,33 @@ cudaError_t launch_eval(const Elems& el, const int32_t* pt_elem, int64_t npts, i
 }
 
 // ---------------------------------------------------------------- interp
+// One thread per point: u_q = sum_j N_j(x_q) u_j and its gradient, summed over the
+// m_e functions of the point's element in local order (no cross-lane reductions:
+// FP64 adds are scarce on this GPU).
 __global__ void __launch_bounds__(256) k_interp(Elems el, const int32_t* __restrict__ pt_elem,
                                                 const int32_t* __restrict__ fns, const int64_t* __restrict__ fn_ptr,
                                                 int64_t Q, const double* __restrict__ table,
                                                 const double* __restrict__ u, double* __restrict__ uq,
                                                 double* __restrict__ grad) {
-    const int lane = threadIdx.x & 31;
-    const int64_t pt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pt >= Q) return;
     const int e = pt_elem[pt];
     const int m = el.m[e], nc = el.nc;
     const double* T = table + el.bt_ptr[e] + (pt - el.pt_ptr[e]) * nc * m;
+    const int32_t* f = fns + fn_ptr[e];
     double v = 0, gx = 0, gy = 0, gz = 0;
-    for (int jl = lane; jl < m; jl += 32) {
-        const double uj = u[fns[fn_ptr[e] + jl]];
-        v += uj * T[jl];
-        gx += uj * T[m + jl];
-        gy += uj * T[2 * m + jl];
-        if (nc == 5) gz += uj * T[3 * m + jl];
+    for (int jl = 0; jl < m; ++jl) {
+        const double uj = u[f[jl]];
+        v = fma(uj, T[jl], v);
+        gx = fma(uj, T[m + jl], gx);
+        gy = fma(uj, T[2 * m + jl], gy);
+        if (nc == 5) gz = fma(uj, T[3 * m + jl], gz);
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        v += __shfl_xor_sync(0xffffffffu, v, off);
-        gx += __shfl_xor_sync(0xffffffffu, gx, off);
-        gy += __shfl_xor_sync(0xffffffffu, gy, off);
-        gz += __shfl_xor_sync(0xffffffffu, gz, off);
-    }
-    if (lane == 0) {
-        uq[pt] = v;
-        if (grad) {
-            grad[pt * 3 + 0] = gx;
-            grad[pt * 3 + 1] = gy;
-            grad[pt * 3 + 2] = gz;
-        }
+    uq[pt] = v;
+    if (grad) {
+        grad[pt * 3 + 0] = gx;
+        grad[pt * 3 + 1] = gy;
+        grad[pt * 3 + 2] = gz;
     }
 }
 
@@ -228,8 +222,7 @@ cudaError_t launch_interp(const Elems& el, const int32_t* pt_elem, const int32_t
                           int64_t Q, const double* table, const double* u, double* uq, double* grad,
                           cudaStream_t st) {
     if (Q == 0) return cudaSuccess;
-    const int threads = 256, wpb = threads / 32;
-    k_interp<<<(unsigned)((Q + wpb - 1) / wpb), threads, 0, st>>>(el, pt_elem, fns, fn_ptr, Q, table, u, uq, grad);
+    k_interp<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(el, pt_elem, fns, fn_ptr, Q, table, u, uq, grad);
     return cudaGetLastError();
 }
 
@@ -266,81 +259,67 @@ __global__ void __launch_bounds__(256) k_heat_fields(Elems el, const int32_t* __
                                                      const double* __restrict__ table, const double* __restrict__ u,
                                                      const double* __restrict__ uo, double dt, double k0, double k2,
                                                      double f, double* __restrict__ kappa, double* __restrict__ g) {
-    const int lane = threadIdx.x & 31;
-    const int64_t pt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pt >= Q) return;
     const int e = pt_elem[pt];
     const int m = el.m[e], nc = el.nc;
     const double* T = table + el.bt_ptr[e] + (pt - el.pt_ptr[e]) * nc * m;
+    const int32_t* fl = fns + fn_ptr[e];
     double v = 0, vo = 0, gx = 0, gy = 0, gz = 0;
-    for (int jl = lane; jl < m; jl += 32) {
-        const int j = fns[fn_ptr[e] + jl];
-        const double uj = u[j];
-        v += uj * T[jl];
-        vo += uo[j] * T[jl];
-        gx += uj * T[m + jl];
-        gy += uj * T[2 * m + jl];
-        if (nc == 5) gz += uj * T[3 * m + jl];
+    for (int jl = 0; jl < m; ++jl) {
+        const int j = fl[jl];
+        const double uj = u[j], nj = T[jl];
+        v = fma(uj, nj, v);
+        vo = fma(uo[j], nj, vo);
+        gx = fma(uj, T[m + jl], gx);
+        gy = fma(uj, T[2 * m + jl], gy);
+        if (nc == 5) gz = fma(uj, T[3 * m + jl], gz);
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        v += __shfl_xor_sync(0xffffffffu, v, off);
-        vo += __shfl_xor_sync(0xffffffffu, vo, off);
-        gx += __shfl_xor_sync(0xffffffffu, gx, off);
-        gy += __shfl_xor_sync(0xffffffffu, gy, off);
-        gz += __shfl_xor_sync(0xffffffffu, gz, off);
-    }
-    if (lane == 0) {
-        const double k = k0 + k2 * v * v;
-        kappa[pt] = k;
-        g[pt] = (v - vo) / dt - f;
-        g[Q + pt] = k * gx;
-        g[2 * Q + pt] = k * gy;
-        if (nc == 5) g[3 * Q + pt] = k * gz;
-    }
+    const double k = k0 + k2 * v * v;
+    kappa[pt] = k;
+    g[pt] = (v - vo) / dt - f;
+    g[Q + pt] = k * gx;
+    g[2 * Q + pt] = k * gy;
+    if (nc == 5) g[3 * Q + pt] = k * gz;
 }
 
 cudaError_t launch_heat_fields(const Elems& el, const int32_t* pt_elem, const int32_t* fns, const int64_t* fn_ptr,
                                int64_t Q, const double* table, const double* u, const double* uo, double dt, double k0,
                                double k2, double f, double* kappa, double* g, cudaStream_t st) {
     if (Q == 0) return cudaSuccess;
-    const int threads = 256, wpb = threads / 32;
-    k_heat_fields<<<(unsigned)((Q + wpb - 1) / wpb), threads, 0, st>>>(el, pt_elem, fns, fn_ptr, Q, table, u, uo, dt,
-                                                                        k0, k2, f, kappa, g);
+    k_heat_fields<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(el, pt_elem, fns, fn_ptr, Q, table, u, uo, dt, k0, k2,
+                                                              f, kappa, g);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- WQ apply
-// Matrix-free WQ functional: y_i = sum_t sum_{q in pts(supp N_i)} w^{c_t}_iq g_t(x_q),
-// one warp per row, lanes over the points of each support element.
-__global__ void __launch_bounds__(256) k_apply(Rows rw, const int4* __restrict__ desc, int nt, int4 wc4,
+// Matrix-free WQ functional: y_i = sum_t sum_{q in pts(supp N_i)} w^{c_t}_iq g_t(x_q).
+// One warp per row; the row's weight rows [w_ptr[i], w_ptr[i+1]) are contiguous, so
+// lanes stride over them (coalesced), each with its point index pt_of_w[x]; one warp
+// reduction per row.
+__global__ void __launch_bounds__(256) k_apply(Rows rw, const int32_t* __restrict__ pt_of_w, int nt, int4 wc4,
                                                const double* __restrict__ W, int nwc, const double* __restrict__ g,
                                                int64_t Q, double* __restrict__ y) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= rw.n) return;
     const int wc[4] = {wc4.x, wc4.y, wc4.z, wc4.w};
-    int64_t woff = rw.w_ptr[i];
     double acc = 0.0;
-    for (int64_t s = rw.supp_ptr[i]; s < rw.supp_ptr[i + 1]; ++s) {
-        const int4 d = desc[s];
-        const int P = (d.z >> 8) & 255;
-        for (int q = lane; q < P; q += 32) {
-            const double* wrow = W + (woff + q) * nwc;
-            for (int t = 0; t < nt; ++t) acc += wrow[wc[t]] * g[t * Q + d.y + q];
-        }
-        woff += P;
+    for (int64_t x = rw.w_ptr[i] + lane; x < rw.w_ptr[i + 1]; x += 32) {
+        const double* wrow = W + x * nwc;
+        const int64_t q = pt_of_w[x];
+        for (int t = 0; t < nt; ++t) acc = fma(wrow[wc[t]], g[t * Q + q], acc);
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane == 0) y[i] = acc;
 }
 
-cudaError_t launch_apply(const Rows& rw, const int4* desc, int nt, int4 wc4, const double* W, int nwc,
+cudaError_t launch_apply(const Rows& rw, const int32_t* pt_of_w, int nt, int4 wc4, const double* W, int nwc,
                          const double* g, int64_t Q, double* y, cudaStream_t st) {
     if (rw.n == 0) return cudaSuccess;
     const int threads = 256, wpb = threads / 32;
-    k_apply<<<(unsigned)((rw.n + wpb - 1) / wpb), threads, 0, st>>>(rw, desc, nt, wc4, W, nwc, g, Q, y);
+    k_apply<<<(unsigned)((rw.n + wpb - 1) / wpb), threads, 0, st>>>(rw, pt_of_w, nt, wc4, W, nwc, g, Q, y);
     return cudaGetLastError();
 }
 

@@ -78,7 +78,7 @@ cudaError_t launch_heat_fields(const Elems& el, const int32_t* pt_elem, const in
                                double k2, double f, double* kappa, double* g, cudaStream_t st);
 
 // Matrix-free WQ functional y_i = sum_t sum_q w^{wc_t}_iq g[t][q] (weight columns in wc4, nt <= 4).
-cudaError_t launch_apply(const Rows& rw, const int4* desc, int nt, int4 wc4, const double* W, int nwc,
+cudaError_t launch_apply(const Rows& rw, const int32_t* pt_of_w, int nt, int4 wc4, const double* W, int nwc,
                          const double* g, int64_t Q, double* y, cudaStream_t st);
 
 // Convert double arrays to (hi, lo) float pairs.

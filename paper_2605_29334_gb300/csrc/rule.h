@@ -53,6 +53,7 @@ struct wq_rule {
     // element-major FP32 assembly
     int4 *d_it_wq = nullptr, *d_it_gq = nullptr;
     int32_t *d_kb_wq = nullptr, *d_kb_gq = nullptr, *d_wrow_dst = nullptr, *d_scat = nullptr, *d_gptr = nullptr;
+    int32_t* d_pt_of_w = nullptr;          // point index of every weight row
     float2* d_kscr = nullptr;
     int64_t kscr_len = 0;
     wqd::ElemItems it_wq{}, it_gq{};
