@@ -49,7 +49,10 @@ typedef enum {
     WQ_OP_MASS = 0,    /* sum_q w_iq c_q N_j(x_q)                                     */
     WQ_OP_STIFF = 1,   /* sum_q c_q sum_d w^d_iq d_d N_j(x_q), d over x,y (,z)         */
     WQ_OP_BIHARM = 2,  /* sum_q w^lap_iq c_q lap N_j(x_q)                              */
-    WQ_OP_HEAT_S = 3   /* alpha * MASS(c = 1) + STIFF(c), alpha = 1/(theta dt)           */
+    WQ_OP_HEAT_S = 3,  /* alpha * MASS(c = 1) + STIFF(c), alpha = 1/(theta dt)           */
+    WQ_OP_HEAT_J = 4   /* HEAT_S + sum_d sum_q w^d_iq c_{1+d,q} N_j(x_q): the exact Newton
+                          tangent of the WQ heat residual (Sec. 5.2), with coefficient rows
+                          c_0 = k(u), c_{1+d} = k'(u) d_d u (see wq_heat_fields)           */
 } wq_op;
 
 /* Weight / table components. */
@@ -191,19 +194,21 @@ wq_status wq_rule_table(const wq_rule* rule, int32_t gauss, const double** d_tab
  * component comp (Sec. 2, "entries of b are precomputed"), into d_vals [nnz]. */
 wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* stream);
 
-/* WQ row-wise assembly (Eqs. 9, 11, 12, S):
- *   d_coef  [Q] coefficient c(x_q) at the WQ points (device)
- *   alpha   scalar of WQ_OP_HEAT_S (ignored otherwise)
+/* WQ assembly (Eqs. 9, 11, 12, S):
+ *   d_coef  coefficient at the WQ points (device): [Q], or [1 + dim][Q] rows for
+ *           WQ_OP_HEAT_J (row 0: k(u), row 1 + d: k'(u) d_d u); null means 1
+ *   alpha   scalar of WQ_OP_HEAT_S / WQ_OP_HEAT_J (ignored otherwise)
  *   prec    wq_prec; d_vals [nnz] double (F64) or float (F32), caller-owned.
- * No allocation, no host synchronisation; asynchronous on stream.  WQ_PREC_F32
- * splits the coefficient into a rule-owned buffer first (two kernel launches),
- * so F32 assemblies on one rule must not overlap on the GPU.
- * Errors: WQ_ERR_ARG (op not built into this rule, bad precision). */
+ * No allocation, no host synchronisation; asynchronous on stream.  The FP32
+ * modes launch two kernels (element blocks, then per-entry sums) through a
+ * rule-owned slot buffer, so FP32 assemblies on one rule must not overlap on the
+ * GPU.  Errors: WQ_ERR_ARG (op not built into this rule, bad precision). */
 wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha,
                       int32_t prec, void* d_vals, void* stream);
 
 /* Same operator by element-wise 4x4 Gauss quadrature (the paper's reference,
- * Table 2 right column), coefficient at the Gauss points d_coef [G]. */
+ * Table 2 right column), coefficient at the Gauss points d_coef [G] (rows of G
+ * for WQ_OP_HEAT_J). */
 wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha,
                          int32_t prec, void* d_vals, void* stream);
 
@@ -221,9 +226,11 @@ wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps,
  * variables d_u, d_u_old [n]:  d_kappa [Q] = k0 + k2 u(x_q)^2 (the coefficient
  * of the tangent S, Eq. S), d_g [1 + dim][Q] with g_0 = (u - u_old)/dt - f and
  * g_{1+d} = kappa d_d u, so that wq_apply(N, x, y[, z]) gives the residual R_A
- * of Eq. heat_residual_discrete.  No allocation; asynchronous on stream. */
+ * of Eq. heat_residual_discrete.  With jacobian != 0, d_kappa is [1 + dim][Q]
+ * and rows 1 + d hold k'(u) d_d u = 2 k2 u d_d u: the coefficient rows of
+ * WQ_OP_HEAT_J.  No allocation; asynchronous on stream. */
 wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d_u_old, double dt, double k0,
-                         double k2, double f, double* d_kappa, double* d_g, void* stream);
+                         double k2, double f, int32_t jacobian, double* d_kappa, double* d_g, void* stream);
 
 /* Control-variable id of every function (host) [n]: < n_vertices: the vertex
  * of a vertex-based function; otherwise n_vertices + 4 * (rank of the enriched
@@ -232,7 +239,8 @@ wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
 
 /* Host-buffer round trip for end-to-end use: copies h_coef [Q] to the device,
  * assembles, copies the CSR values back to h_vals [nnz] (double or float by
- * prec), synchronising on stream.  Uses library-owned staging buffers. */
+ * prec), synchronising on stream.  Uses library-owned staging buffers; operators
+ * with one coefficient row only (not WQ_OP_HEAT_J). */
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
                            int32_t prec, void* h_vals, void* stream);
 

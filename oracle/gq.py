@@ -102,6 +102,25 @@ def assemble(basis, comps, coef=None, row_ptr=None, col=None, gdata=None):
     return vals
 
 
+def assemble_terms(basis, terms, row_ptr=None, col=None, gdata=None):
+    """sum over terms (test comp, trial comp, coef) of the Gauss integrals
+    int coef(x) D_test N_i D_trial N_j (coef a callable of physical x [P,3], or None
+    for 1) on the S_i pattern: the mixed form needed by the exact heat tangent
+    (Sec. 5.2), where the test side carries a gradient and the trial side a value."""
+    if row_ptr is None:
+        row_ptr, col = pattern(basis)
+    pos = _positions(basis, row_ptr, col)
+    vals = np.zeros(len(col))
+    for e in range(basis.E):
+        d = gdata[e] if gdata is not None else gauss_data(basis, e)
+        K = np.zeros((basis.m(e), basis.m(e)))
+        for test, trial, coef in terms:
+            c = np.ones(len(d["w"])) if coef is None else coef(d["x"])
+            K += (comp_values(d, test) * (d["w"] * c)) @ comp_values(d, trial).T
+        vals[pos[e]] += K.ravel()
+    return vals
+
+
 def _positions(basis, row_ptr, col):
     """For each element, flat CSR positions of its m x m local pairs (i, j)."""
     out = []

@@ -172,9 +172,12 @@ class Rule:
 
     # ----------------------------------------------------------- 6. assembly
     def assemble(self, terms):
-        """terms: list of (comp, coef [Q]) -> CSR values on the S_i pattern."""
+        """terms: list of (comp, coef [Q]) or (test comp, trial comp, coef [Q]) -> CSR
+        values on the S_i pattern:  A_ij = sum_terms sum_q w^{test}_iq coef_q D_{trial} N_j(x_q)
+        (Sec. 4.1; a 2-tuple uses the same component on both sides)."""
         B = self.basis
         vals = np.zeros(len(self.col))
+        terms = [t if len(t) == 3 else (t[0], t[0], t[1]) for t in terms]
         for i in range(B.n):
             r0, r1 = self.row_ptr[i], self.row_ptr[i + 1]
             cols = self.col[r0:r1]
@@ -184,9 +187,9 @@ class Rule:
                 p0, p1 = self.pt_ptr[e], self.pt_ptr[e + 1]
                 P = p1 - p0
                 pos = np.searchsorted(cols, B.elem_fns[e])
-                for comp, coef in terms:
-                    wc = self.weights[comp][off:off + P] * coef[p0:p1]
-                    acc[pos] += comp_values(self.data[e], comp) @ wc
+                for wcomp, tcomp, coef in terms:
+                    wc = self.weights[wcomp][off:off + P] * coef[p0:p1]
+                    acc[pos] += comp_values(self.data[e], tcomp) @ wc
                 off += P
             vals[r0:r1] = acc
         return vals
@@ -217,6 +220,26 @@ class Rule:
             for c in grads:
                 R[i] += self.weights[c][sl] @ (kappa(uq[q]) * gq[q, "xyz".index(c)])
         return R
+
+
+    def heat_tangent(self, u, dt, kappa, dkappa, exact=True):
+        """Newton tangent of heat_residual at u (Sec. 5.2, theta = 1) as assembly terms.
+
+        dR_i/du_j = Q_i(N_j)/dt + sum_d Q^d_i(k(u) d_d N_j) + sum_d Q^d_i(k'(u) d_d u N_j):
+        the derivative of the WQ residual itself (weights fixed), so Newton on the WQ
+        system converges quadratically.  exact=False drops the last (non-symmetric)
+        sum, which leaves the paper's S (eq. S)."""
+        uq, gq = self.interp(u)
+        k = kappa(uq)
+        terms = [("N", "N", np.full(self.Q, 1.0 / dt))]
+        grads = [c for c in self.comps if c in "xyz"]
+        for c in grads:
+            terms.append((c, c, k))
+        if exact:
+            dk = dkappa(uq)
+            for c in grads:
+                terms.append((c, "N", dk * gq[:, "xyz".index(c)]))
+        return terms
 
 
 def tsvd_weights(A, z, b, tol=TSVD_TOL, driver="gesdd"):

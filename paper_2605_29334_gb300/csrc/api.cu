@@ -76,26 +76,42 @@ int table_comp(const wq_rule* R, int comp) {
     }
 }
 
-// Terms of an operator; returns false if a needed weight set is missing.
-bool op_terms(const wq_rule* R, int op, double alpha, bool need_weights, wqd::Terms& tm) {
+// Terms of an operator; returns false if a needed weight set is missing.  Each term
+// pairs a test component (WQ weight set / Gauss test table) with a trial table
+// component and a coefficient row (-1: the constant scale); npts = the number of
+// points of the coefficient rows (WQ or Gauss).
+bool op_terms(const wq_rule* R, int op, double alpha, bool need_weights, wqd::Terms& tm, int64_t npts) {
     tm.nt = 0;
-    auto add = [&](int comp, int use_coef, double scale) -> bool {
-        int tc = table_comp(R, comp);
-        if (tc < 0) return false;
-        int wc = R->wcidx[comp];
+    tm.cstride = npts;
+    auto add = [&](int test, int trial, int crow, double scale) -> bool {
+        const int sc = table_comp(R, test), tc = table_comp(R, trial);
+        if (sc < 0 || tc < 0) return false;
+        const int wc = R->wcidx[test];
         if (need_weights && wc < 0) return false;
-        tm.t[tm.nt++] = {wc < 0 ? 0 : wc, tc, use_coef, scale};
+        tm.t[tm.nt++] = {wc < 0 ? 0 : wc, tc, sc, crow, scale};
         return true;
     };
+    const int grads[3] = {WQ_COMP_X, WQ_COMP_Y, WQ_COMP_Z};
+    const int nd = R->dim == 3 ? 3 : 2;
     switch (op) {
-        case WQ_OP_MASS: return add(WQ_COMP_N, 1, 1.0);
+        case WQ_OP_MASS: return add(WQ_COMP_N, WQ_COMP_N, 0, 1.0);
         case WQ_OP_STIFF:
-            if (!add(WQ_COMP_X, 1, 1.0) || !add(WQ_COMP_Y, 1, 1.0)) return false;
-            return R->dim == 3 ? add(WQ_COMP_Z, 1, 1.0) : true;
-        case WQ_OP_BIHARM: return add(WQ_COMP_LAP, 1, 1.0);
+            for (int d = 0; d < nd; ++d)
+                if (!add(grads[d], grads[d], 0, 1.0)) return false;
+            return true;
+        case WQ_OP_BIHARM: return add(WQ_COMP_LAP, WQ_COMP_LAP, 0, 1.0);
         case WQ_OP_HEAT_S:
-            if (!add(WQ_COMP_N, 0, alpha) || !add(WQ_COMP_X, 1, 1.0) || !add(WQ_COMP_Y, 1, 1.0)) return false;
-            return R->dim == 3 ? add(WQ_COMP_Z, 1, 1.0) : true;
+            if (!add(WQ_COMP_N, WQ_COMP_N, -1, alpha)) return false;
+            for (int d = 0; d < nd; ++d)
+                if (!add(grads[d], grads[d], 0, 1.0)) return false;
+            return true;
+        case WQ_OP_HEAT_J:
+            if (!add(WQ_COMP_N, WQ_COMP_N, -1, alpha)) return false;
+            for (int d = 0; d < nd; ++d)
+                if (!add(grads[d], grads[d], 0, 1.0)) return false;
+            for (int d = 0; d < nd; ++d)
+                if (!add(grads[d], WQ_COMP_N, 1 + d, 1.0)) return false;
+            return true;
         default: return false;
     }
 }
@@ -552,7 +568,8 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         if (R->wcidx[c] < 0) continue;
         wqd::Terms tm;
         tm.nt = 1;
-        tm.t[0] = {0, table_comp(R, c), 0, 1.0};
+        tm.t[0] = {0, table_comp(R, c), table_comp(R, c), 0, 1.0};
+        tm.cstride = R->G;
         ce = wqd::launch_rowasm_f64(rw, R->d_desc_gq, tm, nc, 1, R->d_gtable, nullptr, 0, R->d_gw, nullptr,
                                     R->d_mom[c], R->max_n_i, st);
     }
@@ -782,7 +799,7 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
                       void* stream) {
     if (!rule || !d_vals) return WQ_ERR_ARG;
     wqd::Terms tm;
-    if (!op_terms(rule, op, alpha, true, tm))
+    if (!op_terms(rule, op, alpha, true, tm, rule->Q))
         return fail(rule->ctx, WQ_ERR_ARG, "operator needs weight sets that this rule did not build");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
@@ -805,7 +822,7 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
                          void* d_vals, void* stream) {
     if (!rule || !d_vals) return WQ_ERR_ARG;
     wqd::Terms tm;
-    if (!op_terms(rule, op, alpha, false, tm)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
+    if (!op_terms(rule, op, alpha, false, tm, rule->G)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
     cudaError_t e;
     cudaStream_t st = (cudaStream_t)stream;
     if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST)
@@ -847,10 +864,10 @@ wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps,
 }
 
 wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d_u_old, double dt, double k0, double k2,
-                         double f, double* d_kappa, double* d_g, void* stream) {
+                         double f, int32_t jacobian, double* d_kappa, double* d_g, void* stream) {
     if (!rule || !d_u || !d_u_old || !d_kappa || !d_g || !(dt > 0)) return WQ_ERR_ARG;
     cudaError_t e = wqd::launch_heat_fields(rule->el, rule->d_pt_elem, rule->d_fns, rule->d_fn_ptr, rule->Q,
-                                            rule->d_table, d_u, d_u_old, dt, k0, k2, f, d_kappa, d_g,
+                                            rule->d_table, d_u, d_u_old, dt, k0, k2, f, jacobian != 0, d_kappa, d_g,
                                             (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("heat fields launch: ") + cudaGetErrorString(e));
     return WQ_OK;
@@ -945,8 +962,11 @@ wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* con
     }
     if (prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST) return fail(batch->ctx, WQ_ERR_ARG, "unknown precision");
     wqd::Terms tm;
-    if (!op_terms(batch->rules[0], op, alpha, true, tm))
+    if (!op_terms(batch->rules[0], op, alpha, true, tm, 0))
         return fail(batch->ctx, WQ_ERR_ARG, "operator needs weight sets that these rules did not build");
+    for (int t = 0; t < tm.nt; ++t)
+        if (tm.t[t].crow > 0)
+            return fail(batch->ctx, WQ_ERR_ARG, "batched assembly takes operators with one coefficient row");
     const double* coefs[wqd::WQ_BATCH_MAX];
     float* vals[wqd::WQ_BATCH_MAX];
     for (int r = 0; r < k; ++r) {
@@ -1003,6 +1023,7 @@ wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids) {
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha, int32_t prec,
                            void* h_vals, void* stream) {
     if (!rule || !h_coef || !h_vals) return WQ_ERR_ARG;
+    if (op == WQ_OP_HEAT_J) return fail(rule->ctx, WQ_ERR_ARG, "wq_assemble_host takes one coefficient row");
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(rule->ctx, cudaMemcpyAsync(rule->d_coef_stage, h_coef, rule->Q * sizeof(double), cudaMemcpyHostToDevice, st));
     wq_status s = wq_assemble(rule, op, rule->d_coef_stage, alpha, prec, rule->d_vals_stage, stream);

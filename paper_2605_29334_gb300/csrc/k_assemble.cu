@@ -62,12 +62,12 @@ __global__ void __launch_bounds__(128, 6) k_rowasm_f64(Rows rw, const int4* __re
             double sv[NT];
             if (lane < nq) {
                 const int q = q0 + lane;
-                const double c = coef ? coef[d.y + q] : 1.0;
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    const double a = tm.t[t].use_coef ? c : tm.t[t].scale;
+                    const int cr = tm.t[t].crow;
+                    const double a = cr < 0 ? tm.t[t].scale : (coef ? coef[cr * tm.cstride + d.y + q] : 1.0);
                     if (GAUSS)
-                        sv[t] = gw[d.y + q] * a * tb[((int64_t)q * nc + tm.t[t].tc) * m + il];
+                        sv[t] = gw[d.y + q] * a * tb[((int64_t)q * nc + tm.t[t].sc) * m + il];
                     else
                         sv[t] = W[(woff + q) * nwc + tm.t[t].wc] * a;
                 }
@@ -108,11 +108,11 @@ __global__ void __launch_bounds__(128, 6) k_rowasm_f64(Rows rw, const int4* __re
                 double a2 = 0.0;
                 for (int q = 0; q < P; ++q) {
                     const double* tq = tb + (int64_t)q * nc * m;
-                    const double c = coef ? coef[d.y + q] : 1.0;
 #pragma unroll
                     for (int t = 0; t < NT; ++t) {
-                        const double a = tm.t[t].use_coef ? c : tm.t[t].scale;
-                        const double sq = GAUSS ? gw[d.y + q] * a * tq[tm.t[t].tc * m + il]
+                        const int cr = tm.t[t].crow;
+                        const double a = cr < 0 ? tm.t[t].scale : (coef ? coef[cr * tm.cstride + d.y + q] : 1.0);
+                        const double sq = GAUSS ? gw[d.y + q] * a * tq[tm.t[t].sc * m + il]
                                                 : W[(woff + q) * nwc + tm.t[t].wc] * a;
                         a2 = fma(sq, tq[tm.t[t].tc * m + j], a2);
                     }
@@ -133,17 +133,23 @@ cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm,
     const int threads = 128, wpb = threads / 32;
     const unsigned blocks = (unsigned)((rw.n + wpb - 1) / wpb);
     const size_t smem = (size_t)wpb * max_n_i * sizeof(double);
+    // more than 4 terms run as 8 (the extra terms are zero: constant scale 0)
+    Terms tp = tm;
+    const int ntk = tm.nt <= 4 ? tm.nt : 8;
+    for (int t = tm.nt; t < ntk; ++t) tp.t[t] = {0, 0, 0, -1, 0.0};
 #define WQ_F64_CASE(G, N) \
-    k_rowasm_f64<G, N><<<blocks, threads, smem, st>>>(rw, desc, tm, nc, table, W, nwc, gw, coef, vals, max_n_i)
-    switch (tm.nt + 4 * (gauss ? 1 : 0)) {
+    k_rowasm_f64<G, N><<<blocks, threads, smem, st>>>(rw, desc, tp, nc, table, W, nwc, gw, coef, vals, max_n_i)
+    switch (ntk + 8 * (gauss ? 1 : 0)) {
         case 1: WQ_F64_CASE(0, 1); break;
         case 2: WQ_F64_CASE(0, 2); break;
         case 3: WQ_F64_CASE(0, 3); break;
         case 4: WQ_F64_CASE(0, 4); break;
-        case 5: WQ_F64_CASE(1, 1); break;
-        case 6: WQ_F64_CASE(1, 2); break;
-        case 7: WQ_F64_CASE(1, 3); break;
-        default: WQ_F64_CASE(1, 4); break;
+        case 8: WQ_F64_CASE(0, 8); break;
+        case 9: WQ_F64_CASE(1, 1); break;
+        case 10: WQ_F64_CASE(1, 2); break;
+        case 11: WQ_F64_CASE(1, 3); break;
+        case 12: WQ_F64_CASE(1, 4); break;
+        default: WQ_F64_CASE(1, 8); break;
     }
 #undef WQ_F64_CASE
     return cudaGetLastError();
@@ -211,10 +217,10 @@ __device__ __forceinline__ float pow2_above_4x(float x) {
 template <int NT, bool COMP, bool GAUSS, bool BATCH, int NP>
 __global__ void __launch_bounds__(EL_NWARP * 32, 6)
     k_elem_f32(ElemItems it, ElemSrc one, BatchPlan bp, const __grid_constant__ PtrTable<NP> pt, TermsF tm) {
-    constexpr int QC = NT <= 2 ? 12 : 8;            // most points per staged chunk
+    constexpr int QC = NT <= 2 ? 12 : (NT <= 4 ? 8 : 4);   // most points per staged chunk
     __shared__ __align__(16) float2 sT[EL_NWARP][QC * NT * 16];   // trial side [point][term][column]
     __shared__ __align__(16) float2 sS[EL_NWARP][QC * NT * 16];   // test side, then the products s
-    __shared__ __align__(16) double sD[EL_NWARP][2 * QC];         // coefficients, Gauss weights
+    __shared__ __align__(16) double sD[EL_NWARP][5 * QC];         // coefficient rows 0..3, Gauss weights
     __shared__ __align__(16) float2 sC[EL_NWARP][QC * NT];        // split multipliers per (point, term)
     __shared__ __align__(16) int32_t sSlot[EL_NWARP][256];        // destination slots of the tile
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -270,34 +276,49 @@ __global__ void __launch_bounds__(EL_NWARP * 32, 6)
                 if (bok) cp_async8(T_ + (qq * NT + t) * 16 + bl, tb + (tcol + qo + tm.tc[t] * m));
                 if (aok) {
                     if (GAUSS)
-                        cp_async8(S_ + (qq * NT + t) * 16 + bl, tb + (trow + qo + tm.tc[t] * m));
+                        cp_async8(S_ + (qq * NT + t) * 16 + bl, tb + (trow + qo + tm.sc[t] * m));
                     else
                         cp_async8(S_ + (qq * NT + t) * 16 + bl, wb + (wrow + (q0 + 2 * j) * mnwc + tm.wc[t]));
                 }
             }
         }
         if (lane < nq) {
-            if (coef) cp_async8(D_ + lane, coef + d.y + q0 + lane);
-            if (GAUSS) cp_async8(D_ + QC + lane, gw + d.y + q0 + lane);
+            if (coef)
+                for (int cr = 0; cr < tm.ncrow; ++cr)
+                    cp_async8(D_ + cr * QC + lane, coef + cr * tm.cstride + d.y + q0 + lane);
+            if (GAUSS) cp_async8(D_ + 4 * QC + lane, gw + d.y + q0 + lane);
         }
         cp_async_wait_all();
         __syncwarp();
         if (lane < nq) {
-            const double cq = coef ? D_[lane] : 1.0;
             if (GAUSS) {
-                const double g = D_[QC + lane];
+                const double g = D_[4 * QC + lane];
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    const double v = g * (tm.use_coef[t] ? cq : tm.scale[t]);
+                    const int cr = tm.crow[t];
+                    const double v = g * (cr < 0 ? tm.scale[t] : (coef ? D_[cr * QC + lane] : 1.0));
                     const float vh = (float)v;
                     C_[lane * NT + t] = make_float2(vh, (float)(v - (double)vh));
                 }
-            } else {
+            } else if (tm.ncrow <= 1) {
+                const double cq = coef ? D_[lane] : 1.0;
                 const float ch = (float)cq;
                 const float2 cs = make_float2(ch, (float)(cq - (double)ch));   // split once per point
 #pragma unroll
                 for (int t = 0; t < NT; ++t)
-                    C_[lane * NT + t] = tm.use_coef[t] ? cs : make_float2(tm.shi[t], tm.slo[t]);
+                    C_[lane * NT + t] = tm.crow[t] >= 0 ? cs : make_float2(tm.shi[t], tm.slo[t]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const int cr = tm.crow[t];
+                    if (cr < 0) {
+                        C_[lane * NT + t] = make_float2(tm.shi[t], tm.slo[t]);
+                    } else {
+                        const double cq = coef ? D_[cr * QC + lane] : 1.0;
+                        const float ch = (float)cq;
+                        C_[lane * NT + t] = make_float2(ch, (float)(cq - (double)ch));
+                    }
+                }
             }
         }
         __syncwarp();
@@ -435,15 +456,19 @@ __global__ void __launch_bounds__(256) k_gather_f32(ElemSrc one, BatchPlan bp, c
     if (n + 1 < nnz) vals[n + 1] = hi1 + lo1;
 }
 
-static TermsF terms_f(const Terms& tm) {
+static TermsF terms_f(const Terms& tm, int ntk) {
     TermsF tf{};
-    for (int t = 0; t < tm.nt; ++t) {
-        tf.wc[t] = tm.t[t].wc;
-        tf.tc[t] = tm.t[t].tc;
-        tf.use_coef[t] = tm.t[t].use_coef;
-        tf.scale[t] = tm.t[t].scale;
-        tf.shi[t] = (float)tm.t[t].scale;
-        tf.slo[t] = (float)(tm.t[t].scale - (double)tf.shi[t]);
+    tf.cstride = tm.cstride;
+    for (int t = 0; t < ntk; ++t) {
+        const bool real = t < tm.nt;
+        tf.wc[t] = real ? tm.t[t].wc : 0;
+        tf.tc[t] = real ? tm.t[t].tc : 0;
+        tf.sc[t] = real ? tm.t[t].sc : 0;
+        tf.crow[t] = real ? tm.t[t].crow : -1;
+        tf.scale[t] = real ? tm.t[t].scale : 0.0;   // padding terms contribute zero
+        tf.shi[t] = (float)tf.scale[t];
+        tf.slo[t] = (float)(tf.scale[t] - (double)tf.shi[t]);
+        tf.ncrow = std::max(tf.ncrow, tf.crow[t] + 1);
     }
     return tf;
 }
@@ -454,7 +479,8 @@ template <bool BATCH, int NP>
 static cudaError_t launch_elem_pair(const ElemItems& it, const ElemSrc& one, const BatchPlan& bp,
                                     const PtrTable<NP>& pt, const Terms& tm, int gauss, bool compensated,
                                     int64_t n_items, int64_t n_gblocks, cudaStream_t st, cudaEvent_t* evs) {
-    const TermsF tf = terms_f(tm);
+    const int ntk = tm.nt <= 4 ? tm.nt : 8;         // more than 4 terms run as 8 (zero padding)
+    const TermsF tf = terms_f(tm, ntk);
     const unsigned eb = (unsigned)((n_items + EL_NWARP - 1) / EL_NWARP);
 #define WQ_EL_CASE(N, C)                                                                                  \
     do {                                                                                                  \
@@ -464,7 +490,7 @@ static cudaError_t launch_elem_pair(const ElemItems& it, const ElemSrc& one, con
             k_elem_f32<N, C, false, BATCH, NP><<<eb, EL_NWARP * 32, 0, st>>>(it, one, bp, pt, tf);        \
     } while (0)
     if (n_items > 0) {
-        switch (tm.nt * 2 + (compensated ? 1 : 0)) {
+        switch (ntk * 2 + (compensated ? 1 : 0)) {
             case 2: WQ_EL_CASE(1, false); break;
             case 3: WQ_EL_CASE(1, true); break;
             case 4: WQ_EL_CASE(2, false); break;
@@ -472,7 +498,9 @@ static cudaError_t launch_elem_pair(const ElemItems& it, const ElemSrc& one, con
             case 6: WQ_EL_CASE(3, false); break;
             case 7: WQ_EL_CASE(3, true); break;
             case 8: WQ_EL_CASE(4, false); break;
-            default: WQ_EL_CASE(4, true); break;
+            case 9: WQ_EL_CASE(4, true); break;
+            case 16: WQ_EL_CASE(8, false); break;
+            default: WQ_EL_CASE(8, true); break;
         }
     }
 #undef WQ_EL_CASE

@@ -251,14 +251,16 @@ namespace wqd {
 // Point data of the nonlinear heat problem (paper Sec. 5, theta = 1):
 //   u_q = sum_j N_j(x_q) u_j, grad u_q likewise, uo_q from u_old;
 //   kappa_q = k0 + k2 u_q^2 (coefficient of the tangent S, Eq. S),
-//   g[0][q] = (u_q - uo_q) / dt - f,   g[1 + d][q] = kappa_q d_d u_q
+//   g[0][q] = (u_q - uo_q) / dt - f,   g[1 + d][q] = kappa_q d_d u_q,
+//   and (jacobian) kappa[1 + d][q] = k'(u_q) d_d u_q for the exact tangent
 // (the residual R_A = Q_A((u - u_old)/dt - f) + sum_d Q^d_A(kappa d_d u)).
 __global__ void __launch_bounds__(256) k_heat_fields(Elems el, const int32_t* __restrict__ pt_elem,
                                                      const int32_t* __restrict__ fns,
                                                      const int64_t* __restrict__ fn_ptr, int64_t Q,
                                                      const double* __restrict__ table, const double* __restrict__ u,
                                                      const double* __restrict__ uo, double dt, double k0, double k2,
-                                                     double f, double* __restrict__ kappa, double* __restrict__ g) {
+                                                     double f, bool jacobian, double* __restrict__ kappa,
+                                                     double* __restrict__ g) {
     const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pt >= Q) return;
     const int e = pt_elem[pt];
@@ -277,6 +279,12 @@ __global__ void __launch_bounds__(256) k_heat_fields(Elems el, const int32_t* __
     }
     const double k = k0 + k2 * v * v;
     kappa[pt] = k;
+    if (jacobian) {   // k'(u) d_d u, the coefficient rows of the exact tangent
+        const double dk = 2.0 * k2 * v;
+        kappa[Q + pt] = dk * gx;
+        kappa[2 * Q + pt] = dk * gy;
+        if (nc == 5) kappa[3 * Q + pt] = dk * gz;
+    }
     g[pt] = (v - vo) / dt - f;
     g[Q + pt] = k * gx;
     g[2 * Q + pt] = k * gy;
@@ -285,10 +293,10 @@ __global__ void __launch_bounds__(256) k_heat_fields(Elems el, const int32_t* __
 
 cudaError_t launch_heat_fields(const Elems& el, const int32_t* pt_elem, const int32_t* fns, const int64_t* fn_ptr,
                                int64_t Q, const double* table, const double* u, const double* uo, double dt, double k0,
-                               double k2, double f, double* kappa, double* g, cudaStream_t st) {
+                               double k2, double f, bool jacobian, double* kappa, double* g, cudaStream_t st) {
     if (Q == 0) return cudaSuccess;
     k_heat_fields<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(el, pt_elem, fns, fn_ptr, Q, table, u, uo, dt, k0, k2,
-                                                              f, kappa, g);
+                                                              f, jacobian, kappa, g);
     return cudaGetLastError();
 }
 

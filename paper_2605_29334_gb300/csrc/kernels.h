@@ -8,21 +8,26 @@
 
 namespace wqd {
 
-// One assembly term: weight column wc (WQ) / table component tc, multiplied by
-// the point coefficient (use_coef) or by the constant scale.
+// One assembly term: WQ weight column wc / Gauss test table component sc on the
+// test side, trial table component tc, multiplied by coefficient row crow of the
+// caller's coefficient array (rows cstride apart; -1: the constant scale).
+constexpr int WQ_MAX_TERMS = 8;
 struct Term {
-    int wc, tc, use_coef;
+    int wc, tc, sc, crow;
     double scale;
 };
 struct Terms {
     int nt;
-    Term t[4];
+    Term t[WQ_MAX_TERMS];
+    int64_t cstride;   // entries between coefficient rows (the number of points)
 };
-// The same terms for the FP32 kernels.
+// The same terms for the FP32 kernels (constant scales also split into (hi, lo)).
 struct TermsF {
-    int wc[4], tc[4], use_coef[4];
-    double scale[4];
-    float shi[4], slo[4];   // scale split into (hi, lo) floats
+    int wc[WQ_MAX_TERMS], tc[WQ_MAX_TERMS], sc[WQ_MAX_TERMS], crow[WQ_MAX_TERMS];
+    double scale[WQ_MAX_TERMS];
+    float shi[WQ_MAX_TERMS], slo[WQ_MAX_TERMS];
+    int ncrow;         // coefficient rows read (max crow + 1)
+    int64_t cstride;
 };
 
 // Placement + basis evaluation at WQ (gauss = 0) or Gauss (gauss = 1) points:
@@ -75,7 +80,7 @@ cudaError_t launch_interp(const Elems& el, const int32_t* pt_elem, const int32_t
 // Heat point fields (Sec. 5): kappa [Q] = k0 + k2 u^2; g [1 + dim][Q] residual data.
 cudaError_t launch_heat_fields(const Elems& el, const int32_t* pt_elem, const int32_t* fns, const int64_t* fn_ptr,
                                int64_t Q, const double* table, const double* u, const double* uo, double dt, double k0,
-                               double k2, double f, double* kappa, double* g, cudaStream_t st);
+                               double k2, double f, bool jacobian, double* kappa, double* g, cudaStream_t st);
 
 // Matrix-free WQ functional y_i = sum_t sum_q w^{wc_t}_iq g[t][q] (weight columns in wc4, nt <= 4).
 cudaError_t launch_apply(const Rows& rw, const int32_t* pt_of_w, int nt, int4 wc4, const double* W, int nwc,

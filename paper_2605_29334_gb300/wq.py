@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libwq.so")
 
 WQ_OK, WQ_ERR_ARG, WQ_ERR_MESH, WQ_ERR_ILLPOSED, WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE, WQ_ERR_CUDA, \
     WQ_ERR_OOM, WQ_ERR_NO_DEVICE = range(9)
-OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S = range(4)
+OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S, OP_HEAT_J = range(5)
 COMP_N, COMP_X, COMP_Y, COMP_Z, COMP_LAP = range(5)
 PREC_F64, PREC_F32, PREC_F32_FAST = 0, 1, 2
 TYPE_NAMES = ["passive", "boundary", "irregular", "enriched_transition", "transition", "enriched_regular", "regular"]
@@ -82,7 +82,7 @@ EXPORTS = {
     "wq_rule_weights_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "wq_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_heat_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
-                                 C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+                                 C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_basis_functions": (C.c_int, [C.c_void_p, C.c_void_p]),
     "wq_rule_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "wq_rule_save": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -332,16 +332,17 @@ class Rule:
                                       _stream_handle(stream)))
         return out
 
-    def heat_fields(self, u, u_old, dt, k0=1.0, k2=1.0, f=0.0, kappa=None, g=None, stream=None):
-        """kappa(u) = k0 + k2 u^2 at the WQ points and the residual point data g [1 + dim, Q]."""
+    def heat_fields(self, u, u_old, dt, k0=1.0, k2=1.0, f=0.0, kappa=None, g=None, jacobian=False, stream=None):
+        """kappa(u) = k0 + k2 u^2 at the WQ points ([Q], or [1 + dim, Q] with the rows
+        k'(u) d_d u when jacobian) and the residual point data g [1 + dim, Q]."""
         import torch
         ng = 1 + (3 if self.basis_dim == 3 else 2)
         if kappa is None:
-            kappa = torch.empty(self.Q, dtype=torch.float64, device="cuda")
+            kappa = torch.empty((ng, self.Q) if jacobian else self.Q, dtype=torch.float64, device="cuda")
         if g is None:
             g = torch.empty((ng, self.Q), dtype=torch.float64, device="cuda")
         self.ctx.check(lib().wq_heat_fields(self.h, C.c_void_p(u.data_ptr()), C.c_void_p(u_old.data_ptr()),
-                                            float(dt), float(k0), float(k2), float(f),
+                                            float(dt), float(k0), float(k2), float(f), int(bool(jacobian)),
                                             C.c_void_p(kappa.data_ptr()), C.c_void_p(g.data_ptr()),
                                             _stream_handle(stream)))
         return kappa, g

@@ -217,3 +217,43 @@ def test_assemble_host_roundtrip(case, W):
     torch.cuda.synchronize()
     host = r.assemble_host(1, kap)
     assert np.array_equal(dev, host)
+
+
+def _dk(d):
+    """Smooth stand-ins for the rows k'(u) d_d u of the exact heat tangent."""
+    return lambda x: 0.3 * np.sin(1.7 * x[:, d] + 0.4 * d) + 0.2 * np.cos(x[:, (d + 1) % 3])
+
+
+def test_heat_tangent_operator(case, W):
+    """WQ_OP_HEAT_J (Sec. 5.2): alpha * mass + stiffness(k) + sum_d (w^d, N; k' d_d u),
+    the exact Newton tangent of the WQ heat residual, against the oracle's mixed
+    terms (WQ) and Gauss mixed integrals (GQ), FP64 and FP32."""
+    import torch
+    from oracle import gq
+    comps = case["comps"]
+    grads = [c for c in ("x", "y", "z") if c in comps]
+    if "N" not in comps or len(grads) < 2:
+        pytest.skip("needs N and gradient weights")
+    R, r = case["R"], case["r"]
+    alpha = 7.5
+    dks = [_dk(d) for d in range(len(grads))]
+    kap_q = _kappa(R.x)
+    terms = ([("N", "N", np.full(R.Q, alpha))] + [(g, g, kap_q) for g in grads]
+             + [(g, "N", dks[d](R.x)) for d, g in enumerate(grads)])
+    ref = R.assemble(terms)
+    spread = max(nerr(case["R2"].assemble(terms), ref), nerr(case["R3"].assemble(terms), ref))
+    coef = torch.tensor(np.stack([kap_q] + [f(R.x) for f in dks]), device="cuda")
+    got = r.assemble(W.OP_HEAT_J, coef, alpha=alpha, prec=W.PREC_F64).cpu().numpy()
+    assert nerr(got, ref) < fp64_tol(spread), (nerr(got, ref), fp64_tol(spread))
+    got32 = r.assemble(W.OP_HEAT_J, coef, alpha=alpha, prec=W.PREC_F32).cpu().numpy()
+    assert nerr(got32, got) < 1e-6, nerr(got32, got)
+    # the same operator by Gauss quadrature
+    gx = r.gauss_points().cpu().numpy()
+    gterms = ([("N", "N", lambda x: np.full(len(x), alpha))] + [(g, g, _kappa) for g in grads]
+              + [(g, "N", dks[d]) for d, g in enumerate(grads)])
+    gref = gq.assemble_terms(R.basis, gterms, row_ptr=R.row_ptr, col=R.col)
+    gcoef = torch.tensor(np.stack([_kappa(gx)] + [f(gx) for f in dks]), device="cuda")
+    ggot = r.gq_assemble(W.OP_HEAT_J, gcoef, alpha=alpha, prec=W.PREC_F64).cpu().numpy()
+    assert nerr(ggot, gref) < 1e-12, nerr(ggot, gref)
+    ggot32 = r.gq_assemble(W.OP_HEAT_J, gcoef, alpha=alpha, prec=W.PREC_F32).cpu().numpy()
+    assert nerr(ggot32, gref) < 1e-6, nerr(ggot32, gref)

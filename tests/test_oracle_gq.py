@@ -121,3 +121,21 @@ def test_table3_gauss_count_identity():
     nsub = np.array([B.elem_coef[e].shape[1] for e in range(B.E)])
     I = int(np.sum(B.topo.irregular[B.elements]))
     assert int(np.sum(16 * nsub)) == 16 * B.E + 48 * I
+
+
+def test_mixed_terms_pin():
+    """assemble_terms: a (c, c) term equals assemble([c]); swapping the test and
+    trial components of a mixed term gives the transposed matrix (on the
+    symmetric pattern S_i)."""
+    from oracle.basis import Basis
+    from oracle import gq
+    B = Basis(meshes.disk(mu=5, n=4))
+    rp, col = gq.pattern(B)
+    kap = lambda x: 1.0 + 0.5 * np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1])
+    a = gq.assemble(B, ["x"], coef=kap, row_ptr=rp, col=col)
+    b = gq.assemble_terms(B, [("x", "x", kap)], row_ptr=rp, col=col)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
+    xn = gq.to_dense(B.n, rp, col, gq.assemble_terms(B, [("x", "N", kap)], row_ptr=rp, col=col))
+    nx = gq.to_dense(B.n, rp, col, gq.assemble_terms(B, [("N", "x", kap)], row_ptr=rp, col=col))
+    assert np.max(np.abs(xn - nx.T)) <= 1e-14 * np.max(np.abs(xn))
+    assert np.max(np.abs(xn - xn.T)) > 1e-3 * np.max(np.abs(xn))      # genuinely non-symmetric

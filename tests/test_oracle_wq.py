@@ -147,3 +147,35 @@ def test_assembly_rowsums_and_mass_sums(disk_rule):
         lhs = Mw[R.row_ptr[i]:R.row_ptr[i + 1]].sum()
         rhs = R.weights["N"][R.w_ptr[i]:R.w_ptr[i + 1]] @ kap[q]
         assert abs(lhs - rhs) < 1e-14
+
+
+def test_heat_tangent_is_the_residual_derivative(disk_rule):
+    """The exact tangent (Sec. 5.2) is the derivative of the WQ residual: pinned by
+    central differences of heat_residual, column by column (the residual itself is
+    a plain sum of weights times point data).  With exact=False the non-symmetric
+    k'(u) part is missing, so the same check fails by the size of that part."""
+    R = disk_rule
+    B = R.basis
+    rng = np.random.Generator(np.random.PCG64(31))
+    u = 0.5 + 0.3 * rng.standard_normal(B.n)
+    u_old = u + 0.05 * rng.standard_normal(B.n)
+    dt = 0.1
+    kap = lambda v: 1.0 + v * v
+    dkap = lambda v: 2.0 * v
+    J = R.assemble(R.heat_tangent(u, dt, kap, dkap, exact=True))
+    S = R.assemble(R.heat_tangent(u, dt, kap, dkap, exact=False))
+    h = 1e-6
+    worst_J = worst_S = 0.0
+    for j in range(0, B.n, 23):
+        e = np.zeros(B.n)
+        e[j] = h
+        col = (R.heat_residual(u + e, u_old, dt, kap) - R.heat_residual(u - e, u_old, dt, kap)) / (2 * h)
+        for i in np.nonzero(col)[0]:
+            r0, r1 = R.row_ptr[i], R.row_ptr[i + 1]
+            k = r0 + np.searchsorted(R.col[r0:r1], j)
+            assert k < r1 and R.col[k] == j          # the derivative lives on the pattern S_i
+            worst_J = max(worst_J, abs(J[k] - col[i]))
+            worst_S = max(worst_S, abs(S[k] - col[i]))
+    scale = np.max(np.abs(J))
+    assert worst_J < 1e-7 * scale, worst_J / scale
+    assert worst_S > 1e-4 * scale
