@@ -67,7 +67,10 @@ typedef enum {
 } wq_prec;
 
 /* Point-count rule (Sec. 4.2). */
-typedef enum { WQ_COUNT_MINMAX = 0 } wq_count_mode;
+/* Per-element point counts (Sec. 4.2): the min-max rule of eq. qp_allocation, or
+ * Table 2's fixed values by element type (3 x 3 / 4 x 4 near high-valence or
+ * clustered EPs); both followed by the well-posedness repair. */
+typedef enum { WQ_COUNT_MINMAX = 0, WQ_COUNT_TABLE2 = 1 } wq_count_mode;
 
 typedef struct wq_ctx wq_ctx;
 typedef struct wq_basis wq_basis;

@@ -46,15 +46,52 @@ import numpy as np
 
 from .geometry import eval_element
 from .gq import pattern, assemble as gq_assemble, comp_values
-from .topology import REGULAR, BOUNDARY
+from .topology import REGULAR, BOUNDARY, IRREGULAR, ENR_TRANSITION, TRANSITION, ENR_REGULAR
 
 TSVD_TOL = 1e-12
 
 
 # ---------------------------------------------------------------- 1. counts
-def point_counts(basis, row_ptr=None):
+def table2_counts(basis):
+    """Table 2's fixed sides: regular 2, boundary 4, irregular 4, enriched
+    transition 4, non-enriched transition and enriched regular 3, or 4 next to
+    high-valence (>= 7) or clustered EPs.  Reading of "clustered": at least two
+    EPs among the vertices of the elements in the union of the supports of the
+    functions active on the element (the note under Table 2)."""
+    T = basis.topo
+    E = basis.E
+    et = basis.etype
+    side = np.zeros(E, dtype=np.int64)
+    fixed = {REGULAR: 2, BOUNDARY: 4, IRREGULAR: 4, ENR_TRANSITION: 4}
+    for e in range(E):
+        t = int(et[e])
+        if t in fixed:
+            side[e] = fixed[t]
+            continue
+        region = set()
+        for i in basis.elem_fns[e]:
+            region.update(int(k) for k in basis.supp[i])
+        verts = set()
+        for k in region:
+            verts.update(int(v) for v in T.quads[basis.elements[k]])
+        eps = [v for v in verts if T.is_ep[v]]
+        high = any(T.valence[v] >= 7 for v in eps)
+        side[e] = 4 if (len(eps) >= 2 or high) else 3
+    return side
+
+
+def point_counts(basis, row_ptr=None, mode="minmax"):
+    """Sides of the per-element point grids (Sec. 4.2).  mode "minmax": the
+    min-max rule of eq. qp_allocation; mode "table2": Table 2's fixed values.
+    Both end with the same repair (raise the non-regular element with most
+    functions while some test function has fewer points than n_i), which the
+    paper prescribes when the table's numbers are not well posed."""
     if row_ptr is None:
         row_ptr, _ = pattern(basis)
+    if mode == "table2":
+        return _repair(basis, row_ptr, table2_counts(basis))
+    if mode != "minmax":
+        raise ValueError("unknown count mode")
     E = basis.E
     et = basis.etype
     isR = (et == REGULAR) | (et == BOUNDARY)
@@ -80,6 +117,15 @@ def point_counts(basis, row_ptr=None):
             while s * s * den < int(m[k]) * num:
                 s += 1
             side[k] = max(side[k], s)
+    return _repair(basis, row_ptr, side)
+
+
+def _repair(basis, row_ptr, side):
+    et = basis.etype
+    isR = (et == REGULAR) | (et == BOUNDARY)
+    m = np.array([basis.m(e) for e in range(basis.E)], dtype=np.int64)
+    n_i = np.diff(row_ptr)
+    side = np.asarray(side, dtype=np.int64).copy()
     changed = True
     while changed:
         changed = False
@@ -104,11 +150,11 @@ def local_points(s):
 class Rule:
     """Everything the weight computation and assembly need, built from a Basis."""
 
-    def __init__(self, basis, comps, tol=TSVD_TOL, side=None):
+    def __init__(self, basis, comps, tol=TSVD_TOL, side=None, count_mode="minmax"):
         self.basis = basis
         self.comps = list(comps)
         self.row_ptr, self.col = pattern(basis)
-        self.side = point_counts(basis, self.row_ptr) if side is None else np.asarray(side)
+        self.side = point_counts(basis, self.row_ptr, count_mode) if side is None else np.asarray(side)
         E = basis.E
         self.pt_ptr = np.zeros(E + 1, dtype=np.int64)
         self.pt_ptr[1:] = np.cumsum(self.side ** 2)

@@ -598,18 +598,58 @@ bool build_basis(const wq_mesh_desc& mesh, BasisHost& B, Error& err) {
 }
 
 // ---------------------------------------------- min-max counts (Sec. 4.2)
+// Table 2's fixed sides; non-enriched transition and enriched regular elements get
+// 4 x 4 when two or more EPs, or one of valence >= 7, lie among the vertices of the
+// union of the supports of the functions active on the element, else 3 x 3.
+static void table2_sides(const BasisHost& B, std::vector<int32_t>& side) {
+    const Topology& T = B.topo;
+    side.assign(B.E, 2);
+    std::vector<int64_t> mark_e(B.E, -1), mark_v(T.V, -1);
+    for (int64_t e = 0; e < B.E; ++e) {
+        switch (B.etype[e]) {
+            case REGULAR: side[e] = 2; continue;
+            case BOUNDARY: case IRREGULAR: case ENR_TRANSITION: side[e] = 4; continue;
+            default: break;
+        }
+        int n_ep = 0;
+        bool high = false;
+        for (int64_t p = B.fn_ptr[e]; p < B.fn_ptr[e + 1]; ++p) {
+            const int32_t i = B.fns[p];
+            for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
+                const int32_t k = B.supp[s];
+                if (mark_e[k] == e) continue;
+                mark_e[k] = e;
+                const int32_t f = B.elem_face[k];
+                for (int c = 0; c < 4; ++c) {
+                    const int32_t v = T.quads[(int64_t)f * 4 + c];
+                    if (mark_v[v] == e) continue;
+                    mark_v[v] = e;
+                    if (T.is_ep[v]) {
+                        ++n_ep;
+                        high = high || T.valence[v] >= 7;
+                    }
+                }
+            }
+        }
+        side[e] = (n_ep >= 2 || high) ? 4 : 3;
+    }
+}
+
 bool point_counts(const BasisHost& B, int mode, std::vector<int32_t>& side, Error& err) {
-    if (mode != WQ_COUNT_MINMAX) {
+    if (mode != WQ_COUNT_MINMAX && mode != WQ_COUNT_TABLE2) {
         err = {WQ_ERR_ARG, "unknown count mode"};
         return false;
     }
     const int64_t E = B.E;
-    side.assign(E, 2);
     std::vector<uint8_t> isR(E);
-    for (int64_t e = 0; e < E; ++e) {
-        isR[e] = (B.etype[e] == REGULAR || B.etype[e] == BOUNDARY);
-        if (B.etype[e] == BOUNDARY) side[e] = 4;
+    for (int64_t e = 0; e < E; ++e) isR[e] = (B.etype[e] == REGULAR || B.etype[e] == BOUNDARY);
+    if (mode == WQ_COUNT_TABLE2) {
+        table2_sides(B, side);
+        return repair_counts(B, isR, side, err);
     }
+    side.assign(E, 2);
+    for (int64_t e = 0; e < E; ++e)
+        if (B.etype[e] == BOUNDARY) side[e] = 4;
     for (int64_t i = 0; i < B.n; ++i) {
         int64_t n_i = B.row_ptr[i + 1] - B.row_ptr[i];
         int64_t er = 0, eb = 0, den = 0;
@@ -631,6 +671,12 @@ bool point_counts(const BasisHost& B, int mode, std::vector<int32_t>& side, Erro
             side[k] = std::max<int32_t>(side[k], (int32_t)sk);
         }
     }
+    return repair_counts(B, isR, side, err);
+}
+
+// Raise the non-regular element with most functions (lowest id on ties) of every
+// test function with fewer points than n_i until all are well posed (Sec. 4.2).
+bool repair_counts(const BasisHost& B, const std::vector<uint8_t>& isR, std::vector<int32_t>& side, Error& err) {
     bool changed = true;
     while (changed) {
         changed = false;

@@ -78,5 +78,6 @@ struct BasisHost {
 bool build_topology(const wq_mesh_desc& mesh, Topology& T, Error& err);
 bool build_basis(const wq_mesh_desc& mesh, BasisHost& B, Error& err);
 bool point_counts(const BasisHost& B, int mode, std::vector<int32_t>& side, Error& err);
+bool repair_counts(const BasisHost& B, const std::vector<uint8_t>& isR, std::vector<int32_t>& side, Error& err);
 
 }  // namespace wqi

@@ -208,9 +208,10 @@ class Basis:
         self.ctx.check(lib().wq_basis_functions(self.h, _ptr(out)))
         return out
 
-    def point_counts(self):
+    def point_counts(self, mode=0):
+        """Sides of the per-element point grids (wq_count_mode: 0 min-max, 1 Table 2)."""
         side = np.zeros(self.E, dtype=np.int32)
-        self.ctx.check(lib().wq_point_counts(self.h, 0, _ptr(side)))
+        self.ctx.check(lib().wq_point_counts(self.h, int(mode), _ptr(side)))
         return side
 
     def __del__(self):
@@ -222,7 +223,8 @@ class Basis:
 class Rule:
     """wq_rule_build: placement, basis tables, Gauss moments and TSVD weights on the device."""
 
-    def __init__(self, basis, comps=(COMP_N, COMP_X, COMP_Y), tol=1e-12, max_sweeps=0, stream=None, path=None):
+    def __init__(self, basis, comps=(COMP_N, COMP_X, COMP_Y), tol=1e-12, max_sweeps=0, stream=None, path=None,
+                 count_mode=0):
         """Build the rule, or (path given) load weights and moments saved by save()."""
         self.basis = basis
         self.ctx = basis.ctx
@@ -234,7 +236,7 @@ class Rule:
             mask = 0
             for c in comps:
                 mask |= 1 << int(c)
-            opts = RuleOpts(mask, 0, float(tol), int(max_sweeps), _stream_handle(stream))
+            opts = RuleOpts(mask, int(count_mode), float(tol), int(max_sweeps), _stream_handle(stream))
             self.ctx.check(lib().wq_rule_build(basis.h, C.byref(opts), C.byref(h)))
             self.h = h
         info = RuleInfo()

@@ -59,6 +59,7 @@ def test_host_setup_matches_oracle(wq, name):
     rp2, col2 = gq.pattern(B)
     assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
     assert np.array_equal(b.point_counts(), owq.point_counts(B, rp2))
+    assert np.array_equal(b.point_counts(1), owq.point_counts(B, rp2, "table2"))
 
 
 def test_type_counts_and_info(wq):

@@ -179,3 +179,20 @@ def test_heat_tangent_is_the_residual_derivative(disk_rule):
     scale = np.max(np.abs(J))
     assert worst_J < 1e-7 * scale, worst_J / scale
     assert worst_S > 1e-4 * scale
+
+
+def test_table2_mode_on_disk_and_well_posed():
+    """Table 2 mode: on the valence-5 disk (one EP, no clustering) it gives the
+    same sides as the min-max rule (Table 2's values); on meshes with clustered
+    or high-valence EPs it uses 4 x 4 there, and every test function stays well
+    posed (r_i >= n_i, Sec. 4.2)."""
+    B = Basis(meshes.disk(mu=5, n=6))
+    rp, _ = gq.pattern(B)
+    assert np.array_equal(wq.point_counts(B, rp, "table2"), wq.point_counts(B, rp))
+    for mesh in (meshes.disk(mu=8, n=4, levels=1), meshes.rotated(levels=1)):
+        B = Basis(mesh)
+        rp, _ = gq.pattern(B)
+        side = wq.point_counts(B, rp, "table2")
+        for i in range(B.n):
+            assert sum(int(side[k]) ** 2 for k in B.supp[i]) >= rp[i + 1] - rp[i]
+        assert set(np.unique(side)) <= {2, 3, 4, 5, 6}
