@@ -223,6 +223,9 @@ __global__ void __launch_bounds__(EL_NWARP * 32, 6)
     __shared__ __align__(16) double sD[EL_NWARP][5 * QC];         // coefficient rows 0..3, Gauss weights
     __shared__ __align__(16) float2 sC[EL_NWARP][QC * NT];        // split multipliers per (point, term)
     __shared__ __align__(16) int32_t sSlot[EL_NWARP][256];        // destination slots of the tile
+    // every block of this grid has started once the last wave runs: from then on the
+    // per-entry sums (a programmatic dependent) may be scheduled into freed slots
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * EL_NWARP + wib;
     if (k >= (BATCH ? bp.n_items : it.n)) return;
@@ -418,8 +421,7 @@ __global__ void __launch_bounds__(EL_NWARP * 32, 6)
 // with TwoSum to the entry it belongs to (in slot order, i.e. support order).
 template <bool COMP, bool BATCH, int NP>
 __global__ void __launch_bounds__(256) k_gather_f32(ElemSrc one, BatchPlan bp, const __grid_constant__ PtrTable<NP> pt) {
-    // launched as a programmatic dependent of the element kernel: wait for its results
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    // launched as a programmatic dependent of the element kernel (see the wait below)
     const int ri = BATCH ? bp.gblk_rule[blockIdx.x] : 0;
     const int64_t base = BATCH ? bp.gblk_start[blockIdx.x] : (int64_t)blockIdx.x * 512;
     const ElemSrc src = BATCH ? bp.src[ri] : one;
@@ -428,8 +430,15 @@ __global__ void __launch_bounds__(256) k_gather_f32(ElemSrc one, BatchPlan bp, c
     const float2* __restrict__ kscr = src.ep.kscr;
     float* __restrict__ vals = pt.vals[BATCH ? ri : 0];
     const int64_t n = base + 2 * threadIdx.x;
+    // the slot ranges do not depend on the element kernel: read them before waiting for it
+    int c0 = 0, c1 = 0, c2 = 0;
+    if (n < nnz) {
+        c0 = gptr[n];
+        c1 = gptr[n + 1];
+        c2 = gptr[min(n + 2, nnz)];
+    }
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     if (n >= nnz) return;
-    const int c0 = gptr[n], c1 = gptr[n + 1], c2 = gptr[min(n + 2, nnz)];
     float hi0 = 0.0f, lo0 = 0.0f, hi1 = 0.0f, lo1 = 0.0f;
     for (int cb = c0; cb < c2; cb += 8) {
         float2 v[8];
