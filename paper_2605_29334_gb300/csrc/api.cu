@@ -482,7 +482,8 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         !dalloc(R, R->d_gw, (size_t)R->G, sst) || !dalloc(R, R->d_W, (size_t)R->sum_r * R->nwc, sst) ||
         !dalloc(R, R->d_status, 1, sst) || !dalloc(R, R->d_table2, (size_t)bt_ptr[E], sst) ||
         !dalloc(R, R->d_gtable2, (size_t)gbt_ptr[E], sst) ||
-        !dalloc(R, R->d_W2, (size_t)R->sum_r * R->nwc, sst) || !dalloc(R, R->d_coef_stage, (size_t)R->Q, sst) ||
+        !dalloc(R, R->d_W2, (size_t)R->sum_r * R->nwc, sst) || !dalloc(R, R->d_We, (size_t)R->sum_r * R->nwc, sst) ||
+        !dalloc(R, R->d_coef_stage, (size_t)R->Q, sst) ||
         !dalloc(R, R->d_vals_stage, (size_t)R->nnz, sst) ||
         !dalloc(R, R->d_kscr, (size_t)std::max<int64_t>(R->kscr_len, 1), sst))
         return bail(sst);
@@ -532,6 +533,10 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     R->ep = {R->d_scat, R->d_gptr, R->d_kscr};
     R->src_wq = {R->ep, R->d_table2, R->d_W2, nullptr, R->nnz, nc, R->nwc};
     R->src_gq = {R->ep, R->d_gtable2, nullptr, R->d_gw, R->nnz, nc, R->nwc};
+    R->src64_wq = {R->d_scat, R->d_gptr, reinterpret_cast<double*>(R->d_kscr), R->d_table, R->d_We, nullptr, R->nnz,
+                   nc, R->nwc};
+    R->src64_gq = {R->d_scat, R->d_gptr, reinterpret_cast<double*>(R->d_kscr), R->d_gtable, nullptr, R->d_gw, R->nnz,
+                   nc, R->nwc};
     R->h_it_wq = it_wq;
     R->h_kb_wq = kb_wq;
 
@@ -612,6 +617,7 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_table, R->d_table2, bt_ptr[E], st);
     if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gtable, R->d_gtable2, gbt_ptr[E], st);
     if (ce == cudaSuccess) ce = wqd::launch_split_rows(R->d_W, R->d_wrow_dst, R->d_W2, R->sum_r, R->nwc, R->n_sm, st);
+    if (ce == cudaSuccess) ce = wqd::launch_copy_rows(R->d_W, R->d_wrow_dst, R->d_We, R->sum_r, R->nwc, R->n_sm, st);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev1, st);
     unsigned hstat = 0;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstat, R->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -806,12 +812,9 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
     if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     cudaEvent_t* evs = rule->next_timing_events();
-    if (prec == WQ_PREC_F64) {
-        if (evs) cudaEventRecord(evs[0], st);
-        e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_wq, tm, rule->nc, 0, rule->d_table, rule->d_W, rule->nwc,
-                                   nullptr, (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
-        if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
-    } else
+    if (prec == WQ_PREC_F64)
+        e = wqd::launch_elem_f64(rule->it_wq, rule->src64_wq, tm, 0, (const double*)d_coef, (double*)d_vals, st, evs);
+    else
         e = wqd::launch_elem_f32(rule->it_wq, rule->src_wq, tm, 0, (const double*)d_coef, (float*)d_vals,
                                  prec == WQ_PREC_F32, st, evs);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));
@@ -828,12 +831,9 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
     if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     cudaEvent_t* evs = rule->next_timing_events();
-    if (prec == WQ_PREC_F64) {
-        if (evs) cudaEventRecord(evs[0], st);
-        e = wqd::launch_rowasm_f64(rule->rw, rule->d_desc_gq, tm, rule->nc, 1, rule->d_gtable, nullptr, 0, rule->d_gw,
-                                   (const double*)d_coef, (double*)d_vals, rule->max_n_i, st);
-        if (evs) cudaEventRecord(evs[1], st), cudaEventRecord(evs[2], st);
-    } else
+    if (prec == WQ_PREC_F64)
+        e = wqd::launch_elem_f64(rule->it_gq, rule->src64_gq, tm, 1, (const double*)d_coef, (double*)d_vals, st, evs);
+    else
         e = wqd::launch_elem_f32(rule->it_gq, rule->src_gq, tm, 1, (const double*)d_coef, (float*)d_vals,
                                  prec == WQ_PREC_F32, st, evs);
     if (e != cudaSuccess) return fail(rule->ctx, WQ_ERR_CUDA, std::string("assembly launch: ") + cudaGetErrorString(e));

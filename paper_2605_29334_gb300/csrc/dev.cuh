@@ -74,6 +74,18 @@ struct ElemSrc {
     int nc, nwc;
 };
 
+// One rule's data for the FP64 element-major kernels (the slot buffer holds doubles).
+struct ElemSrc64 {
+    const int32_t* scat;
+    const int32_t* gptr;
+    double* kscr;
+    const double* table;    // basis table at the item's points (WQ or Gauss)
+    const double* We;       // element-major FP64 weights (WQ items)
+    const double* gw;       // Gauss weights (Gauss items)
+    int64_t nnz;
+    int nc, nwc;
+};
+
 // Per-call device pointers, passed as a kernel parameter (N = 1 for one rule).
 constexpr int WQ_BATCH_MAX = 256;
 template <int N>

@@ -563,6 +563,198 @@ cudaError_t launch_elem_batch(const BatchPlan& bp, const double* const* coefs, f
                                                 bp.n_gblocks, st, nullptr);
 }
 
+// ------------------------------------------------------------------ FP64 element-major
+// The same tiles and slot map in FP64: K_e[a][b] = sum_{q,t} s^t_aq T^t_qb with
+// s = w c (WQ) or w_q |J_q| c D N_a (Gauss), one FMA per product, no compensation
+// (FP64 sums of a few tens of products), the block entries in the slot buffer as
+// doubles, then one plain per-entry sum in support order.  Bound by the FP64 pipes
+// (2 FMA per cycle per SM on this GPU).
+template <int NT, bool GAUSS>
+__global__ void __launch_bounds__(EL_NWARP * 32, 6)
+    k_elem_f64(ElemItems it, ElemSrc64 src, const double* __restrict__ coef, Terms tm) {
+    constexpr int QC = NT <= 2 ? 12 : (NT <= 4 ? 8 : 4);
+    __shared__ __align__(16) double sT[EL_NWARP][QC * NT * 16];
+    __shared__ __align__(16) double sS[EL_NWARP][QC * NT * 16];
+    __shared__ __align__(16) double sD[EL_NWARP][5 * QC];
+    __shared__ __align__(16) int32_t sSlot[EL_NWARP][256];
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * EL_NWARP + wib;
+    if (k >= it.n) return;
+    const int4 d = it.item[k];
+    const int kb = it.kb[k];
+    const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
+    double* T_ = sT[wib];
+    double* S_ = sS[wib];
+    double* D_ = sD[wib];
+    int32_t* SL = sSlot[wib];
+    const int bl = lane & 15, half = lane >> 4, rbase = 8 * half;
+    const int b = b0 + bl;
+    const bool bok = b < m, aok = a0 + bl < m;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int a = a0 + rbase + r;
+        if (bok && a < m) cp_async4(SL + (rbase + r) * 16 + bl, src.scat + kb + a * m + b);
+    }
+    int ncrow = 0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) ncrow = max(ncrow, tm.t[t].crow + 1);
+    double acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = 0.0;
+    const int nch = (P + QC - 1) / QC;
+    const int qc = (P + nch - 1) / nch;
+    const double* tb = src.table + d.x;
+    const int ncm = src.nc * m;
+    const int tcol = half * ncm + b0 + bl, trow = half * ncm + a0 + bl;
+    const double* wb = src.We + (int64_t)d.w * src.nwc;
+    const int wrow = (half * m + a0 + bl) * src.nwc, mnwc = m * src.nwc;
+    for (int q0 = 0; q0 < P; q0 += qc) {
+        const int nq = min(qc, P - q0);
+        const int nj = (nq + 1 - half) >> 1;
+        __syncwarp();
+        for (int j = 0; j < nj; ++j) {
+            const int qq = half + 2 * j;
+            const int qo = (q0 + 2 * j) * ncm;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                if (bok) cp_async8(T_ + (qq * NT + t) * 16 + bl, tb + (tcol + qo + tm.t[t].tc * m));
+                if (aok) {
+                    if (GAUSS)
+                        cp_async8(S_ + (qq * NT + t) * 16 + bl, tb + (trow + qo + tm.t[t].sc * m));
+                    else
+                        cp_async8(S_ + (qq * NT + t) * 16 + bl, wb + (wrow + (q0 + 2 * j) * mnwc + tm.t[t].wc));
+                }
+            }
+        }
+        if (lane < nq) {
+            if (coef)
+                for (int cr = 0; cr < ncrow; ++cr)
+                    cp_async8(D_ + cr * QC + lane, coef + cr * tm.cstride + d.y + q0 + lane);
+            if (GAUSS) cp_async8(D_ + 4 * QC + lane, src.gw + d.y + q0 + lane);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        // products s in place (rows beyond m are zeroed)
+        for (int j = 0; j < nj; ++j) {
+            const int qq = half + 2 * j;
+            const double g = GAUSS ? D_[4 * QC + qq] : 1.0;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                double* sp = S_ + (qq * NT + t) * 16 + bl;
+                const int cr = tm.t[t].crow;
+                const double c = cr < 0 ? tm.t[t].scale : (coef ? D_[cr * QC + qq] : 1.0);
+                *sp = aok ? *sp * (g * c) : 0.0;
+            }
+        }
+        __syncwarp();
+        if (bok) {
+#pragma unroll 2
+            for (int qq = 0; qq < nq; ++qq) {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const double T = T_[(qq * NT + t) * 16 + bl];
+                    const double2* srow = reinterpret_cast<const double2*>(S_ + (qq * NT + t) * 16 + rbase);
+#pragma unroll
+                    for (int r2 = 0; r2 < 4; ++r2) {
+                        const double2 sv = srow[r2];
+                        acc[2 * r2] = fma(sv.x, T, acc[2 * r2]);
+                        acc[2 * r2 + 1] = fma(sv.y, T, acc[2 * r2 + 1]);
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    if (bok) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (a0 + rbase + r < m) src.kscr[SL[(rbase + r) * 16 + bl]] = acc[r];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gather_f64(int64_t nnz, const int32_t* __restrict__ gptr,
+                                                    const double* __restrict__ kscr, double* __restrict__ vals) {
+    const int64_t n = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    int c0 = 0, c1 = 0, c2 = 0;
+    if (n < nnz) {
+        c0 = gptr[n];
+        c1 = gptr[n + 1];
+        c2 = gptr[min(n + 2, nnz)];
+    }
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if (n >= nnz) return;
+    double s0 = 0.0, s1 = 0.0;
+    for (int c = c0; c < c1; ++c) s0 += kscr[c];
+    for (int c = c1; c < c2; ++c) s1 += kscr[c];
+    vals[n] = s0;
+    if (n + 1 < nnz) vals[n + 1] = s1;
+}
+
+cudaError_t launch_elem_f64(const ElemItems& it, const ElemSrc64& src, const Terms& tm, int gauss,
+                            const double* coef, double* vals, cudaStream_t st, cudaEvent_t* evs) {
+    if (evs) cudaEventRecord(evs[0], st);
+    cudaError_t e = cudaSuccess;
+    if (src.nnz > 0 && it.n > 0) {
+        Terms tp = tm;
+        const int ntk = tm.nt <= 4 ? tm.nt : 8;
+        for (int t = tm.nt; t < ntk; ++t) tp.t[t] = {0, 0, 0, -1, 0.0};
+        const unsigned eb = (unsigned)((it.n + EL_NWARP - 1) / EL_NWARP);
+#define WQ_E64_CASE(N)                                                                                   \
+    do {                                                                                                 \
+        if (gauss)                                                                                       \
+            k_elem_f64<N, true><<<eb, EL_NWARP * 32, 0, st>>>(it, src, coef, tp);                        \
+        else                                                                                             \
+            k_elem_f64<N, false><<<eb, EL_NWARP * 32, 0, st>>>(it, src, coef, tp);                       \
+    } while (0)
+        switch (ntk) {
+            case 1: WQ_E64_CASE(1); break;
+            case 2: WQ_E64_CASE(2); break;
+            case 3: WQ_E64_CASE(3); break;
+            case 4: WQ_E64_CASE(4); break;
+            default: WQ_E64_CASE(8); break;
+        }
+#undef WQ_E64_CASE
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (evs) cudaEventRecord(evs[1], st);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)((src.nnz + 511) / 512));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_gather_f64, src.nnz, src.gptr, (const double*)src.kscr, vals);
+    } else if (evs) {
+        cudaEventRecord(evs[1], st);
+    }
+    if (evs) cudaEventRecord(evs[2], st);
+    return e;
+}
+
+// Element-major copy of the FP64 weights (We[dst[r]] = W[r], nwc columns).
+__global__ void k_copy_rows(const double* __restrict__ W, const int32_t* __restrict__ dst, double* __restrict__ We,
+                            int64_t rows, int nwc) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < rows * nwc;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = x / nwc, c = x - r * nwc;
+        We[(int64_t)dst[r] * nwc + c] = W[x];
+    }
+}
+
+cudaError_t launch_copy_rows(const double* W, const int32_t* dst, double* We, int64_t rows, int nwc, int n_sm,
+                             cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((rows * nwc + 255) / 256, (int64_t)std::max(n_sm, 1) * 16);
+    k_copy_rows<<<blocks, 256, 0, st>>>(W, dst, We, rows, nwc);
+    return cudaGetLastError();
+}
+
 // Element-major split copy of the weights: row r of W (test function i, point q
 // of element e) goes to W2e row dst[r] = wbase_e + q m_e + a(i, e).
 __global__ void k_split_rows(const double* __restrict__ W, const int32_t* __restrict__ dst, float2* __restrict__ W2e,

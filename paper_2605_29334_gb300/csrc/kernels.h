@@ -59,6 +59,13 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemSrc& src, const Terms
 cudaError_t launch_elem_batch(const BatchPlan& bp, const double* const* coefs, float* const* vals, int k,
                               const Terms& tm, bool compensated, cudaStream_t st);
 
+// FP64 element-major assembly (same tiles and slot map; FMA sums; double CSR values).
+cudaError_t launch_elem_f64(const ElemItems& it, const ElemSrc64& src, const Terms& tm, int gauss,
+                            const double* coef, double* vals, cudaStream_t st, cudaEvent_t* evs = nullptr);
+// Element-major copy of the FP64 weights (We[dst[r]] = W[r], nwc columns).
+cudaError_t launch_copy_rows(const double* W, const int32_t* dst, double* We, int64_t rows, int nwc, int n_sm,
+                             cudaStream_t st);
+
 // Element-major split copy of the weights (W2e[dst[r]] = split(W[r]), nwc columns).
 cudaError_t launch_split_rows(const double* W, const int32_t* dst, float2* W2e, int64_t rows, int nwc, int n_sm,
                               cudaStream_t st);

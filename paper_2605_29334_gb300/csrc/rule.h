@@ -59,6 +59,8 @@ struct wq_rule {
     wqd::ElemItems it_wq{}, it_gq{};
     wqd::ElemPlan ep{};
     wqd::ElemSrc src_wq{}, src_gq{};
+    wqd::ElemSrc64 src64_wq{}, src64_gq{};
+    double* d_We = nullptr;                // element-major FP64 weights [wbase_e + q m_e + a][nwc]
     std::vector<int4> h_it_wq;          // host copies of the WQ tiles (batched assembly)
     std::vector<int32_t> h_kb_wq;
     int n_sm = 1;
