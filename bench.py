@@ -233,10 +233,15 @@ def bench_ours(args, rank, world):
     t_k2 = float(np.mean(kt[:, 1])) / 1e3 if len(kt) else float("nan")
     step_bytes = work["hbm_bytes_f64"] if prec == wq.PREC_F64 else work["hbm_bytes_f32"]
     if prec == wq.PREC_F64:
-        kname = "k_rowasm_f64"
-        achieved = step_bytes / t_k1 / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": kname, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+        # FP64 element blocks: one FMA (2 flops) per product; peak = 152 SMs x 2 FP64 FMA per
+        # cycle (ncu's sustained rate on this GPU) x 2 flops x max SM clock
+        kname = "k_elem_f64<2,0>"
+        peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = 2 * work["products"] / t_k1 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s FP64", "frac": achieved / peak,
+                "traffic": None, "kernel": kname,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/cycle x 2 x %.0f MHz" % sm_mhz,
+                "kernel_ms": t_k1 * 1e3, "gather_ms": t_k2 * 1e3}
     else:
         # the element-block kernel is bound by instruction issue: 6 FP32 instructions per split
         # product with the extraction-compensated sum (3 without); peak = 152 SMs x 128 FP32
@@ -391,7 +396,7 @@ def other_configs(ctx, flush, steps, warmup):
 # DRAM bytes (read + write) of one launch of the element-block kernel on this workload,
 # from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md), valid for the kernel
 # source it was taken on.
-ELEM_TRAFFIC = {"source_sha1": "a8e14ea017b9e64fb634bfc00456a00196dc0d84", "k_elem_f32<2,1,0>": 60780032}
+ELEM_TRAFFIC = {"source_sha1": "2c9de6c26eeae7bdd76e72b016d28a78add00d69", "k_elem_f32<2,1,0>": 60834048}
 
 
 def _kernel_source_sha1():
