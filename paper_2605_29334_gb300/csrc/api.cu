@@ -383,17 +383,15 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
     }
-    // packed per-(row, support element) descriptors for the assembly kernels
+    // packed per-(row, support element) descriptors of the Gauss moment kernel
     if (bt_ptr[E] > INT32_MAX || gbt_ptr[E] > INT32_MAX || pos_ptr[R->nsupp] > INT32_MAX || R->G > INT32_MAX)
         return bail(fail(ctx, WQ_ERR_ARG, "mesh too large for 32-bit table offsets"));
-    std::vector<int4> desc_wq(R->nsupp), desc_gq(R->nsupp);
+    std::vector<int4> desc_gq(R->nsupp);
     for (int64_t i = 0; i < n; ++i)
         for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
             const int32_t e = B.supp[s];
             if (m[e] > 255 || side[e] * side[e] > 255)
                 return bail(fail(ctx, WQ_ERR_ARG, "element with more than 255 functions or points"));
-            desc_wq[s] = make_int4((int)bt_ptr[e], (int)pt_ptr[e], m[e] | (side[e] * side[e]) << 8 | il[s] << 16,
-                                   (int)pos_ptr[s]);
             desc_gq[s] = make_int4((int)gbt_ptr[e], (int)gp_ptr[e], m[e] | (16 * nsub[e]) << 8 | il[s] << 16,
                                    (int)pos_ptr[s]);
         }
@@ -469,7 +467,7 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         !upload(R, R->d_supp_ptr, B.supp_ptr, sst) || !upload(R, R->d_supp, B.supp, sst) ||
         !upload(R, R->d_pos_ptr, pos_ptr, sst) || !upload(R, R->d_pos, pos, sst) || !upload(R, R->d_il, il, sst) ||
         !upload(R, R->d_w_ptr, w_ptr, sst) || !upload(R, R->d_fn_ptr, B.fn_ptr, sst) ||
-        !upload(R, R->d_order, order, sst) || !upload(R, R->d_desc_wq, desc_wq, sst) ||
+        !upload(R, R->d_order, order, sst) ||
         !upload(R, R->d_desc_gq, desc_gq, sst) || !upload(R, R->d_fns, B.fns, sst) ||
         !upload(R, R->d_it_wq, it_wq, sst) || !upload(R, R->d_kb_wq, kb_wq, sst) ||
         !upload(R, R->d_it_gq, it_gq, sst) || !upload(R, R->d_kb_gq, kb_gq, sst) ||
@@ -571,12 +569,8 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     // a4: Gauss moments per component (c = 1)
     for (int c = 0; c < 5 && ce == cudaSuccess && !saved; ++c) {
         if (R->wcidx[c] < 0) continue;
-        wqd::Terms tm;
-        tm.nt = 1;
-        tm.t[0] = {0, table_comp(R, c), table_comp(R, c), 0, 1.0};
-        tm.cstride = R->G;
-        ce = wqd::launch_rowasm_f64(rw, R->d_desc_gq, tm, nc, 1, R->d_gtable, nullptr, 0, R->d_gw, nullptr,
-                                    R->d_mom[c], R->max_n_i, st);
+        ce = wqd::launch_moments_f64(rw, R->d_desc_gq, table_comp(R, c), nc, R->d_gtable, R->d_gw, R->d_mom[c],
+                                     R->max_n_i, st);
     }
     // a5: truncated-SVD weights per component
     std::vector<int32_t> rank(n);

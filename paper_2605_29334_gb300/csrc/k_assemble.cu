@@ -1,18 +1,12 @@
-// Row-wise assembly (paper Eqs. 9, 11, 12 and the WQ form of Eq. S):
-//     A_ij = sum_{q in pts(supp N_i)} sum_t  s^t_iq * D_{c_t} N_j(x_q),
-//     s^t_iq = w^{c_t}_iq * a_t(x_q)                    (WQ: weights of row i)
-//     s^t_ig = w_g |J_g| a_t(x_g) * D_{c_t} N_i(x_g)     (Gauss: test function value)
-// One warp per test function (row) i; the row's n_i values are accumulated in
-// shared memory and written once (no atomics, deterministic).  The warp walks
-// the elements of supp N_i; for each element the per-point products s^t are
-// formed once, lane-parallel (lane q <-> point q), and broadcast by shuffles.
-// Functions go to lanes: for m_e <= 16 the two half-warps take alternate points
-// and are merged at the end of the element (all 32 lanes busy), otherwise one
-// lane per function.  Positions of one element's functions in row i are
-// distinct, so lanes never collide in the row accumulator.
-//
-// Per support entry a packed descriptor {table offset, first point, m | P << 8 |
-// il << 16, position offset} replaces the chain of dependent index loads.
+// Assembly kernels.
+//  * k_moments_f64 (rule build): the Gauss component matrices G^c (c = 1) that are
+//    the moments b of the weight systems (Sec. 2, Sec. 4.3), row-wise: one warp per
+//    test function i, the row's n_i values accumulated in shared memory and written
+//    once; per support element the products w_g |J_g| D_c N_i(x_g) are formed once,
+//    lane-parallel, and broadcast by shuffles; for m_e <= 16 the two half-warps take
+//    alternate points.
+//  * k_elem_f32 / k_gather_f32 and k_elem_f64 / k_gather_f64: WQ and Gauss operators
+//    (Eqs. 9, 11, 12, S and the exact heat tangent) element-major (see below).
 #include <algorithm>
 
 #include "kernels.h"
@@ -30,14 +24,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// ------------------------------------------------------------------ FP64
-template <int GAUSS, int NT>
-__global__ void __launch_bounds__(128, 6) k_rowasm_f64(Rows rw, const int4* __restrict__ desc, Terms tm, int nc,
-                                                       const double* __restrict__ table,
-                                                       const double* __restrict__ W, int nwc,
-                                                       const double* __restrict__ gw,
-                                                       const double* __restrict__ coef,
-                                                       double* __restrict__ vals, int max_n_i) {
+// ------------------------------------------------------------------ Gauss moments
+__global__ void __launch_bounds__(128, 6) k_moments_f64(Rows rw, const int4* __restrict__ desc, int tc, int nc,
+                                                        const double* __restrict__ table,
+                                                        const double* __restrict__ gw, double* __restrict__ vals,
+                                                        int max_n_i) {
     extern __shared__ double sh_acc[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
@@ -47,9 +38,7 @@ __global__ void __launch_bounds__(128, 6) k_rowasm_f64(Rows rw, const int4* __re
     const int r0 = rw.row_ptr[i], n_i = rw.row_ptr[i + 1] - r0;
     for (int x = lane; x < n_i; x += 32) acc[x] = 0.0;
     __syncwarp();
-    int64_t woff = GAUSS ? 0 : rw.w_ptr[i];
-    const int64_t s0 = rw.supp_ptr[i], s1 = rw.supp_ptr[i + 1];
-    for (int64_t s = s0; s < s1; ++s) {
+    for (int64_t s = rw.supp_ptr[i]; s < rw.supp_ptr[i + 1]; ++s) {
         const int4 d = desc[s];
         const int m = d.z & 255, P = (d.z >> 8) & 255, il = (d.z >> 16) & 255;
         const double* tb = table + d.x;
@@ -59,42 +48,20 @@ __global__ void __launch_bounds__(128, 6) k_rowasm_f64(Rows rw, const int4* __re
         double a0 = 0.0, a1 = 0.0;   // lanes own function jl0 (and jl0 + 32)
         for (int q0 = 0; q0 < P; q0 += 32) {
             const int nq = min(32, P - q0);
-            double sv[NT];
-            if (lane < nq) {
-                const int q = q0 + lane;
-#pragma unroll
-                for (int t = 0; t < NT; ++t) {
-                    const int cr = tm.t[t].crow;
-                    const double a = cr < 0 ? tm.t[t].scale : (coef ? coef[cr * tm.cstride + d.y + q] : 1.0);
-                    if (GAUSS)
-                        sv[t] = gw[d.y + q] * a * tb[((int64_t)q * nc + tm.t[t].sc) * m + il];
-                    else
-                        sv[t] = W[(woff + q) * nwc + tm.t[t].wc] * a;
-                }
-            } else {
-#pragma unroll
-                for (int t = 0; t < NT; ++t) sv[t] = 0.0;
-            }
+            double sv = 0.0;
+            if (lane < nq) sv = gw[d.y + q0 + lane] * tb[((int64_t)(q0 + lane) * nc + tc) * m + il];
             if (half) {
                 for (int qq = 0; qq < nq; qq += 2) {
                     const int q = qq + hs;
-                    const bool ok = q < nq && jl0 < m;
-                    const double* tq = tb + (int64_t)(q0 + q) * nc * m + jl0;
-#pragma unroll
-                    for (int t = 0; t < NT; ++t) {
-                        const double sq = __shfl_sync(0xffffffffu, sv[t], q & 31);
-                        if (ok) a0 = fma(sq, tq[tm.t[t].tc * m], a0);
-                    }
+                    const double sq = __shfl_sync(0xffffffffu, sv, q & 31);
+                    if (q < nq && jl0 < m) a0 = fma(sq, tb[((int64_t)(q0 + q) * nc + tc) * m + jl0], a0);
                 }
             } else {
                 for (int q = 0; q < nq; ++q) {
-                    const double* tq = tb + (int64_t)(q0 + q) * nc * m;
-#pragma unroll
-                    for (int t = 0; t < NT; ++t) {
-                        const double sq = __shfl_sync(0xffffffffu, sv[t], q);
-                        if (jl0 < m) a0 = fma(sq, tq[tm.t[t].tc * m + jl0], a0);
-                        if (jl0 + 32 < m) a1 = fma(sq, tq[tm.t[t].tc * m + jl0 + 32], a1);
-                    }
+                    const double sq = __shfl_sync(0xffffffffu, sv, q);
+                    const double* tq = tb + ((int64_t)(q0 + q) * nc + tc) * m;
+                    if (jl0 < m) a0 = fma(sq, tq[jl0], a0);
+                    if (jl0 + 32 < m) a1 = fma(sq, tq[jl0 + 32], a1);
                 }
             }
         }
@@ -107,51 +74,24 @@ __global__ void __launch_bounds__(128, 6) k_rowasm_f64(Rows rw, const int4* __re
             for (int j = jl0 + 64; j < m; j += 32) {   // m > 64: rare, recompute per function
                 double a2 = 0.0;
                 for (int q = 0; q < P; ++q) {
-                    const double* tq = tb + (int64_t)q * nc * m;
-#pragma unroll
-                    for (int t = 0; t < NT; ++t) {
-                        const int cr = tm.t[t].crow;
-                        const double a = cr < 0 ? tm.t[t].scale : (coef ? coef[cr * tm.cstride + d.y + q] : 1.0);
-                        const double sq = GAUSS ? gw[d.y + q] * a * tq[tm.t[t].sc * m + il]
-                                                : W[(woff + q) * nwc + tm.t[t].wc] * a;
-                        a2 = fma(sq, tq[tm.t[t].tc * m + j], a2);
-                    }
+                    const double* tq = tb + ((int64_t)q * nc + tc) * m;
+                    a2 = fma(gw[d.y + q] * tq[il], tq[j], a2);
                 }
                 acc[pos[j]] += a2;
             }
         }
-        if (!GAUSS) woff += P;
         __syncwarp();
     }
     for (int x = lane; x < n_i; x += 32) vals[r0 + x] = acc[x];
 }
 
-cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm, int nc, int gauss,
-                              const double* table, const double* W, int nwc, const double* gw, const double* coef,
-                              double* vals, int max_n_i, cudaStream_t st) {
+cudaError_t launch_moments_f64(const Rows& rw, const int4* desc, int tc, int nc, const double* table,
+                               const double* gw, double* vals, int max_n_i, cudaStream_t st) {
     if (rw.n == 0) return cudaSuccess;
     const int threads = 128, wpb = threads / 32;
     const unsigned blocks = (unsigned)((rw.n + wpb - 1) / wpb);
     const size_t smem = (size_t)wpb * max_n_i * sizeof(double);
-    // more than 4 terms run as 8 (the extra terms are zero: constant scale 0)
-    Terms tp = tm;
-    const int ntk = tm.nt <= 4 ? tm.nt : 8;
-    for (int t = tm.nt; t < ntk; ++t) tp.t[t] = {0, 0, 0, -1, 0.0};
-#define WQ_F64_CASE(G, N) \
-    k_rowasm_f64<G, N><<<blocks, threads, smem, st>>>(rw, desc, tp, nc, table, W, nwc, gw, coef, vals, max_n_i)
-    switch (ntk + 8 * (gauss ? 1 : 0)) {
-        case 1: WQ_F64_CASE(0, 1); break;
-        case 2: WQ_F64_CASE(0, 2); break;
-        case 3: WQ_F64_CASE(0, 3); break;
-        case 4: WQ_F64_CASE(0, 4); break;
-        case 8: WQ_F64_CASE(0, 8); break;
-        case 9: WQ_F64_CASE(1, 1); break;
-        case 10: WQ_F64_CASE(1, 2); break;
-        case 11: WQ_F64_CASE(1, 3); break;
-        case 12: WQ_F64_CASE(1, 4); break;
-        default: WQ_F64_CASE(1, 8); break;
-    }
-#undef WQ_F64_CASE
+    k_moments_f64<<<blocks, threads, smem, st>>>(rw, desc, tc, nc, table, gw, vals, max_n_i);
     return cudaGetLastError();
 }
 

@@ -36,16 +36,10 @@ struct TermsF {
 cudaError_t launch_eval(const Elems& el, const int32_t* pt_elem, int64_t npts, int gauss,
                         double* table, double* xout, double* wout, unsigned* status, cudaStream_t st);
 
-// Row-wise assembly of a sum of terms into CSR values (FP64).
-//   desc [#supp] per (row, support element): {table offset, first point,
-//   m | P << 8 | il << 16, position offset};
-//   gauss = 0: weights W [sum_r][nwc] at the WQ points, coef at WQ points;
-//   gauss = 1: Gauss weights gw (area element included) times the test
-//              function's table value, coef at Gauss points.
-// coef may be null (all terms then use their scale).
-cudaError_t launch_rowasm_f64(const Rows& rw, const int4* desc, const Terms& tm, int nc, int gauss,
-                              const double* table, const double* W, int nwc, const double* gw, const double* coef,
-                              double* vals, int max_n_i, cudaStream_t st);
+// Gauss component matrices G^c (c = 1) row-wise: the moments b of the weight
+// systems, table component tc, Gauss weights gw (area element included).
+cudaError_t launch_moments_f64(const Rows& rw, const int4* desc, int tc, int nc, const double* table,
+                               const double* gw, double* vals, int max_n_i, cudaStream_t st);
 
 // FP32 element-major assembly (split products; compensated = TwoSum sums):
 // element tiles into the slot buffer, then one sum per CSR entry.  WQ items

@@ -48,7 +48,7 @@ struct wq_rule {
     int32_t *d_row_ptr = nullptr, *d_col = nullptr, *d_supp = nullptr, *d_fns = nullptr;
     int64_t *d_supp_ptr = nullptr, *d_pos_ptr = nullptr, *d_w_ptr = nullptr;
     int32_t* d_order = nullptr;
-    int4 *d_desc_wq = nullptr, *d_desc_gq = nullptr;
+    int4* d_desc_gq = nullptr;            // per (row, support element): Gauss table offset, points, m/P/il, positions
 
     // element-major FP32 assembly
     int4 *d_it_wq = nullptr, *d_it_gq = nullptr;
