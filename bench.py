@@ -163,13 +163,17 @@ def bench_ours(args, rank, world):
     torch.cuda.synchronize()
     a64 = out64.cpu().numpy()
     rel = {}
-    for name, pm in (("f32", wq.PREC_F32), ("f32_fast", wq.PREC_F32_FAST)):
-        rule.assemble(wq.OP_STIFF, coef, prec=pm, out=out32)
+    modes = {"f64": wq.PREC_F64, "f32": wq.PREC_F32, "f32_fast": wq.PREC_F32_FAST, "tc": wq.PREC_TC}
+    for name in ("tc", "f32", "f32_fast"):
+        rule.assemble(wq.OP_STIFF, coef, prec=modes[name], out=out32)
         torch.cuda.synchronize()
         rel[name] = float(np.max(np.abs(out32.cpu().numpy().astype(np.float64) - a64)) / np.max(np.abs(a64)))
-    modes = {"f64": wq.PREC_F64, "f32": wq.PREC_F32, "f32_fast": wq.PREC_F32_FAST}
     if args.prec == "auto":
-        choice = "f32_fast" if rel["f32_fast"] <= 1e-6 else ("f32" if rel["f32"] <= 1e-6 else "f64")
+        # the fastest mode within the 1e-6 bar (short flushed trial of each), else FP64
+        trial = {name: float(np.median(time_steps(
+            lambda pm=modes[name]: rule.assemble(wq.OP_STIFF, coef, prec=pm, out=out32), 50, 5, flush)))
+            for name in ("tc", "f32", "f32_fast") if rel[name] <= 1e-6}
+        choice = min(trial, key=trial.get) if trial else "f64"
     else:
         choice = args.prec
     prec = modes[choice]
@@ -206,6 +210,10 @@ def bench_ours(args, rank, world):
                              args.warmup, flush),
         "gq_f32": time_steps(lambda: rule.gq_assemble(wq.OP_STIFF, coef_g, prec=wq.PREC_F32, out=out32), nc,
                              args.warmup, flush),
+        "wq_tc": time_steps(lambda: rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_TC, out=out32), nc,
+                            args.warmup, flush),
+        "gq_tc": time_steps(lambda: rule.gq_assemble(wq.OP_STIFF, coef_g, prec=wq.PREC_TC, out=out32), nc,
+                            args.warmup, flush),
     }
     comp_ms = {k: float(np.mean(v)) for k, v in comp_ms.items()}
     # end to end through the C ABI with pinned host buffers
@@ -232,7 +240,22 @@ def bench_ours(args, rank, world):
     t_k1 = float(np.mean(kt[:, 0])) / 1e3 if len(kt) else float("nan")
     t_k2 = float(np.mean(kt[:, 1])) / 1e3 if len(kt) else float("nan")
     step_bytes = work["hbm_bytes_f64"] if prec == wq.PREC_F64 else work["hbm_bytes_f32"]
-    if prec == wq.PREC_F64:
+    if prec == wq.PREC_TC:
+        # tensor-core element blocks: the SIMT work is per (row, point, term) and the
+        # contraction runs on the tensor pipe, so the kernel's binding roofline is the
+        # bytes it must move: test-side weights, trial-side slices, coefficients, slot
+        # map, tile descriptors and the slot writes
+        kname = "k_elem_tc<2,0>"
+        achieved = work["tc_elem_bytes"] / t_k1 / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": ELEM_TRAFFIC.get(kname) if _kernel_source_sha1("k_tc.cu") == ELEM_TRAFFIC.get(
+                    "k_tc.cu") else None,
+                "kernel": kname, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "kernel_ms": t_k1 * 1e3, "gather_ms": t_k2 * 1e3, "kernel_algorithmic_bytes": work["tc_elem_bytes"],
+                "instrumented_step_ms": float(np.mean(ms_inst)),
+                "kernel_share_of_step": t_k1 / (float(np.mean(ms_inst)) / 1e3),
+                "step_hbm_frac": step_bytes / mean_s / 1e9 / hbm, "step_algorithmic_bytes": step_bytes}
+    elif prec == wq.PREC_F64:
         # FP64 element blocks: one FMA (2 flops) per product; peak = 152 SMs x 2 FP64 FMA per
         # cycle (ncu's sustained rate on this GPU) x 2 flops x max SM clock
         kname = "k_elem_f64<2,0>"
@@ -250,7 +273,8 @@ def bench_ours(args, rank, world):
         kname = "k_elem_f32<2,%d,0>" % (1 if prec == wq.PREC_F32 else 0)
         peak = 152 * 128 * sm_mhz * 1e6 / 1e12
         achieved = per * work["products"] / t_k1 / 1e12
-        traffic = ELEM_TRAFFIC.get(kname) if _kernel_source_sha1() == ELEM_TRAFFIC.get("source_sha1") else None
+        traffic = ELEM_TRAFFIC.get(kname) if _kernel_source_sha1("k_assemble.cu") == ELEM_TRAFFIC.get(
+            "k_assemble.cu") else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 lane-instructions/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (MEASURED_PEAKS.json sm_max_mhz)" % sm_mhz,
@@ -261,17 +285,19 @@ def bench_ours(args, rank, world):
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == wq.PREC_F64 else "f32", "precision_mode": choice, "data": "synthetic",
+        "dtype": {"f64": "f64", "tc": "bf16 (4-slice split operands, f32 accumulate)"}.get(choice, "f32"),
+        "precision_mode": choice, "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_functions": basis.n, "n_elements": basis.E, "nnz": nnz,
                    "n_points": rule.Q, "n_gauss": rule.G, "op": "stiffness", "l2": "flushed (256 MB write) before "
                    "every timed step; timed = the assembly call only", "parallelism": "independent instance per GPU"},
         "rel_err_vs_f64": rel,
-        "gpu_launches": args.steps * (1 if prec == wq.PREC_F64 else 2),
+        "gpu_launches": args.steps * 2,
         "roofline": roof,
         "comparators": dict({k + "_ms": v for k, v in comp_ms.items()},
                             **{k + "_nnz_per_s": nnz / (v / 1e3) for k, v in comp_ms.items()},
                             speedup_wq_over_gq_f64=comp_ms["gq_f64"] / comp_ms["wq_f64"],
-                            speedup_wq_over_gq_f32=comp_ms["gq_f32"] / comp_ms["wq_f32"]),
+                            speedup_wq_over_gq_f32=comp_ms["gq_f32"] / comp_ms["wq_f32"],
+                            speedup_wq_over_gq_tc=comp_ms["gq_tc"] / comp_ms["wq_tc"]),
         "setup": {"host_basis_ms": host_ms, "rule_build_wall_ms": build_ms, "rule_build_device_ms": rule.info.setup_ms,
                   "n_truncated_x": rule.info.n_truncated[1], "n_z_identity_x": rule.info.n_z_identity[1]},
         "e2e": {"value": nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(rule.Q * 8),
@@ -322,11 +348,17 @@ def other_configs(ctx, flush, steps, warmup):
                           o64[0], o64[1], steps, warmup, flush)
         a64 = o64[0].cpu().numpy()
         err = float(np.max(np.abs(o32[0].cpu().numpy().astype(np.float64) - a64)) / np.max(np.abs(a64)))
+        tc = _timed_pair(lambda o: r.assemble(op, cq, alpha=alpha, prec=wq.PREC_TC, out=o),
+                         lambda o: r.gq_assemble(op, cg, alpha=alpha, prec=wq.PREC_TC, out=o),
+                         o32[0], o32[1], steps, warmup, flush)
+        err_tc = float(np.max(np.abs(o32[0].cpu().numpy().astype(np.float64) - a64)) / np.max(np.abs(a64)))
         out[name] = {"n_elements": b.E, "nnz": r.nnz, "n_points": r.Q, "n_gauss": r.G,
                      "wq_f32_nnz_per_s": r.nnz / f32[0] * 1e3, "gq_f32_nnz_per_s": r.nnz / f32[1] * 1e3,
                      "wq_f64_nnz_per_s": r.nnz / f64[0] * 1e3, "gq_f64_nnz_per_s": r.nnz / f64[1] * 1e3,
                      "speedup_f32": f32[1] / f32[0], "speedup_f64": f64[1] / f64[0],
-                     "f32_rel_err_vs_f64": err, "setup_s": setup_s}
+                     "f32_rel_err_vs_f64": err, "setup_s": setup_s,
+                     "wq_tc_nnz_per_s": r.nnz / tc[0] * 1e3, "gq_tc_nnz_per_s": r.nnz / tc[1] * 1e3,
+                     "speedup_tc": tc[1] / tc[0], "tc_rel_err_vs_f64": err_tc}
         return b, r, cq
 
     disk = meshes.disk(mu=5, n=6)
@@ -396,12 +428,12 @@ def other_configs(ctx, flush, steps, warmup):
 # DRAM bytes (read + write) of one launch of the element-block kernel on this workload,
 # from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md), valid for the kernel
 # source it was taken on.
-ELEM_TRAFFIC = {"source_sha1": "2c9de6c26eeae7bdd76e72b016d28a78add00d69", "k_elem_f32<2,1,0>": 60834048}
+ELEM_TRAFFIC = {"k_assemble.cu": "2c9de6c26eeae7bdd76e72b016d28a78add00d69", "k_elem_f32<2,1,0>": 60834048}
 
 
-def _kernel_source_sha1():
+def _kernel_source_sha1(name):
     import hashlib
-    with open(os.path.join(ROOT, "paper_2605_29334_gb300", "csrc", "k_assemble.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2605_29334_gb300", "csrc", name), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
@@ -423,7 +455,14 @@ def assembly_work(rule, basis, n_terms):
     f64 = weights + tables + coef + int(np.sum(m * m)) * 2 + int(np.sum(m)) * 16 + (n + 1) * 20 + rule.nnz * 8
     n_tiles = int(np.sum(((m + 15) // 16) ** 2))
     f32 = weights + tables + coef + int(np.sum(m * m)) * 4 + (rule.nnz + 1) * 4 + n_tiles * 20 + rule.nnz * 4
-    return {"products": products, "hbm_bytes_f64": int(f64), "hbm_bytes_f32": int(f32)}
+    # tensor-core element kernel: split weights (8 B per used value), trial slices (per tile,
+    # term and 8 points: 32 lanes x 32 B), coefficients, slot map, tile descriptors
+    # (2 x int4 + kb) and the slot writes (float pairs)
+    P8 = (P + 7) // 8 * 8
+    tc_elem = (weights + int(np.sum(((m + 15) // 16) ** 2 * P8)) * n_terms * 128 + coef
+               + int(np.sum(m * m)) * 4 + n_tiles * 36 + int(np.sum(m * m)) * 8)
+    return {"products": products, "hbm_bytes_f64": int(f64), "hbm_bytes_f32": int(f32),
+            "tc_elem_bytes": int(tc_elem)}
 
 
 def cpu_baseline(args, seconds=12.0):
@@ -484,7 +523,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="auto", choices=["auto", "f32", "f32_fast", "f64"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "tc", "f32", "f32_fast", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (configs 1, 3, 4, 5)")
     args = ap.parse_args()

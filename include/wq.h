@@ -62,8 +62,13 @@ typedef enum { WQ_COMP_N = 0, WQ_COMP_X = 1, WQ_COMP_Y = 2, WQ_COMP_Z = 3, WQ_CO
 typedef enum {
     WQ_PREC_F64 = 0,      /* FP64 weights, tables and accumulation; CSR values double */
     WQ_PREC_F32 = 1,      /* FP32 split (hi/lo) products, error-free (TwoSum) accumulation; float values */
-    WQ_PREC_F32_FAST = 2  /* FP32 split products, plain FP32 sums (operators with <= 2 terms); float
+    WQ_PREC_F32_FAST = 2, /* FP32 split products, plain FP32 sums (operators with <= 2 terms); float
                              values; its error depends on the cancellation in the rows -- measure it */
+    WQ_PREC_TC = 3        /* element blocks on the tensor cores: both operands scaled per row /
+                             element and split into four 8-bit bf16 slices, slice pairs up to level 3
+                             summed exactly in FP32 (integers below 2^24; error-free transformation
+                             of Ozaki et al.), per-entry sums as WQ_PREC_F32; float values, error
+                             ~2^-32 of each tile's product scale; needs <= 64 points per element */
 } wq_prec;
 
 /* Point-count rule (Sec. 4.2). */
@@ -257,7 +262,7 @@ wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef
  * points, or null) and writing h_vals[r] (device pointer, float [nnz_r]); both
  * pointer arrays are host arrays, read during the call (their contents go into
  * the launch parameters, so the call allocates nothing and may be captured in a
- * CUDA graph).  WQ_PREC_F64 falls back to one wq_assemble per rule.  The paper
+ * CUDA graph).  WQ_PREC_F64 and WQ_PREC_TC run one wq_assemble per rule.  The paper
  * treats one mesh at a time; this entry point is the batching of many.  Errors:
  * WQ_ERR_ARG (k out of range, mixed rules, null output, operator not built),
  * WQ_ERR_OOM, WQ_ERR_CUDA. */

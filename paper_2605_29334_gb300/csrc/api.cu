@@ -406,8 +406,8 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     if (kptr[E] > INT32_MAX || wbase[E] > INT32_MAX)
         return bail(fail(ctx, WQ_ERR_ARG, "mesh too large for 32-bit element block offsets"));
     std::vector<int4> it_wq, it_gq;
-    std::vector<int32_t> kb_wq, kb_gq;
-    auto make_items = [&](bool gauss, std::vector<int4>& item, std::vector<int32_t>& kb) {
+    std::vector<int32_t> kb_wq, kb_gq, ie_wq, ie_gq;
+    auto make_items = [&](bool gauss, std::vector<int4>& item, std::vector<int32_t>& kb, std::vector<int32_t>& ie) {
         auto npts = [&](int64_t e) { return gauss ? 16 * nsub[e] : side[e] * side[e]; };
         auto chunks = [&](int64_t e) { return (npts(e) + 7) / 8; };
         std::vector<int32_t> by_work(E);
@@ -423,10 +423,37 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
                                              m[e] | npts(e) << 8 | (a0 / 16) << 16 | (b0 / 16) << 20,
                                              (int)wbase[e]));
                     kb.push_back((int32_t)kptr[e]);
+                    ie.push_back(e);
                 }
     };
-    make_items(false, it_wq, kb_wq);
-    make_items(true, it_gq, kb_gq);
+    make_items(false, it_wq, kb_wq, ie_wq);
+    make_items(true, it_gq, kb_gq, ie_gq);
+    // tensor-core contraction: per element {table offset, points, weight row, first
+    // function} and the offsets of its trial-side slices (nc components x column
+    // blocks x half-chunks x 256 words); per tile {first function, slice offset,
+    // element, points rounded up to 8}
+    std::vector<int4> tcel_wq(E), tcel_gq(E), it2_wq(it_wq.size()), it2_gq(it_gq.size());
+    std::vector<int64_t> bsp_wq(E + 1, 0), bsp_gq(E + 1, 0);
+    R->tc_ok = true;
+    for (int64_t e = 0; e < E; ++e) {
+        const int pw = side[e] * side[e], pg = 16 * nsub[e], ncb = (m[e] + 15) / 16;
+        if (pw > 64 || pg > 64) R->tc_ok = false;
+        tcel_wq[e] = make_int4((int)bt_ptr[e], pw, (int)wbase[e], (int)B.fn_ptr[e]);
+        tcel_gq[e] = make_int4((int)gbt_ptr[e], pg, (int)wbase[e], (int)B.fn_ptr[e]);
+        bsp_wq[e + 1] = bsp_wq[e] + (int64_t)nc * ncb * ((pw + 7) / 8) * 256;
+        bsp_gq[e + 1] = bsp_gq[e] + (int64_t)nc * ncb * ((pg + 7) / 8) * 256;
+    }
+    if (bsp_wq[E] > INT32_MAX || bsp_gq[E] > INT32_MAX || B.fn_ptr[E] > INT32_MAX) R->tc_ok = false;
+    for (size_t x = 0; x < it_wq.size(); ++x) {
+        const int32_t e = ie_wq[x];
+        it2_wq[x] = make_int4((int)B.fn_ptr[e], (int)bsp_wq[e], e, (side[e] * side[e] + 7) / 8 * 8);
+    }
+    for (size_t x = 0; x < it_gq.size(); ++x) {
+        const int32_t e = ie_gq[x];
+        it2_gq[x] = make_int4((int)B.fn_ptr[e], (int)bsp_gq[e], e, (16 * nsub[e] + 7) / 8 * 8);
+    }
+    R->bs_words_wq = bsp_wq[E];
+    R->bs_words_gq = bsp_gq[E];
     if (R->Q > INT32_MAX) return bail(fail(ctx, WQ_ERR_ARG, "too many points for 32-bit point indices"));
     std::vector<int32_t> wrow_dst(w_ptr[n]), pt_of_w(w_ptr[n]), scat(kptr[E]), gptr(R->nnz + 1, 0);
     for (int64_t i = 0; i < n; ++i) {
@@ -473,7 +500,16 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         !upload(R, R->d_it_gq, it_gq, sst) || !upload(R, R->d_kb_gq, kb_gq, sst) ||
         !upload(R, R->d_wrow_dst, wrow_dst, sst) || !upload(R, R->d_scat, scat, sst) ||
         !upload(R, R->d_pt_of_w, pt_of_w, sst) ||
-        !upload(R, R->d_gptr, gptr, sst))
+        !upload(R, R->d_gptr, gptr, sst) || !upload(R, R->d_tcel_wq, tcel_wq, sst) ||
+        !upload(R, R->d_tcel_gq, tcel_gq, sst) || !upload(R, R->d_bsp_wq, bsp_wq, sst) ||
+        !upload(R, R->d_bsp_gq, bsp_gq, sst) || !upload(R, R->d_it2_wq, it2_wq, sst) ||
+        !upload(R, R->d_it2_gq, it2_gq, sst))
+        return bail(sst);
+    if (R->tc_ok &&
+        (!dalloc(R, R->d_bs_wq, (size_t)bsp_wq[E], sst) || !dalloc(R, R->d_bs_gq, (size_t)bsp_gq[E], sst) ||
+         !dalloc(R, R->d_fexp_wq, (size_t)E * nc, sst) || !dalloc(R, R->d_fexp_gq, (size_t)E * nc, sst) ||
+         !dalloc(R, R->d_vmax_wq, (size_t)B.fn_ptr[E] * R->nwc, sst) ||
+         !dalloc(R, R->d_vmax_gq, (size_t)B.fn_ptr[E] * nc, sst) || !dalloc(R, R->d_gw2, (size_t)R->G, sst)))
         return bail(sst);
     if (!dalloc(R, R->d_table, (size_t)bt_ptr[E], sst) || !dalloc(R, R->d_gtable, (size_t)gbt_ptr[E], sst) ||
         !dalloc(R, R->d_x, (size_t)R->Q * 3, sst) || !dalloc(R, R->d_gx, (size_t)R->G * 3, sst) ||
@@ -535,6 +571,12 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
                    nc, R->nwc};
     R->src64_gq = {R->d_scat, R->d_gptr, reinterpret_cast<double*>(R->d_kscr), R->d_gtable, nullptr, R->d_gw, R->nnz,
                    nc, R->nwc};
+    R->tc_wq = {R->d_scat, R->d_kscr, R->d_gptr, R->d_W2, nullptr, R->d_bs_wq, R->d_fexp_wq, R->d_vmax_wq,
+                R->nnz, nc, R->nwc};
+    R->tc_gq = {R->d_scat, R->d_kscr, R->d_gptr, R->d_gtable2, R->d_gw2, R->d_bs_gq, R->d_fexp_gq, R->d_vmax_gq,
+                R->nnz, nc, R->nwc};
+    R->tit_wq = {(int64_t)it_wq.size(), R->d_it_wq, R->d_kb_wq, R->d_it2_wq};
+    R->tit_gq = {(int64_t)it_gq.size(), R->d_it_gq, R->d_kb_gq, R->d_it2_gq};
     R->h_it_wq = it_wq;
     R->h_kb_wq = kb_wq;
 
@@ -612,6 +654,16 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gtable, R->d_gtable2, gbt_ptr[E], st);
     if (ce == cudaSuccess) ce = wqd::launch_split_rows(R->d_W, R->d_wrow_dst, R->d_W2, R->sum_r, R->nwc, R->n_sm, st);
     if (ce == cudaSuccess) ce = wqd::launch_copy_rows(R->d_W, R->d_wrow_dst, R->d_We, R->sum_r, R->nwc, R->n_sm, st);
+    // trial-side slices and test-side bounds of the tensor-core contraction
+    if (R->tc_ok) {
+        if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gw, R->d_gw2, R->G, st);
+        if (ce == cudaSuccess)
+            ce = wqd::launch_tc_prep(E, nc, R->nwc, R->d_m, R->d_table, R->d_We,
+                                     {R->d_tcel_wq, R->d_bsp_wq, R->d_bs_wq, R->d_fexp_wq, R->d_vmax_wq}, st);
+        if (ce == cudaSuccess)
+            ce = wqd::launch_tc_prep(E, nc, R->nwc, R->d_m, R->d_gtable, nullptr,
+                                     {R->d_tcel_gq, R->d_bsp_gq, R->d_bs_gq, R->d_fexp_gq, R->d_vmax_gq}, st);
+    }
     if (ce == cudaSuccess) ce = cudaEventRecord(ev1, st);
     unsigned hstat = 0;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstat, R->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -803,11 +855,15 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
         return fail(rule->ctx, WQ_ERR_ARG, "operator needs weight sets that this rule did not build");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
-    if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST)
+    if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST && prec != WQ_PREC_TC)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
+    if (prec == WQ_PREC_TC && !rule->tc_ok)
+        return fail(rule->ctx, WQ_ERR_ARG, "WQ_PREC_TC needs at most 64 points per element");
     cudaEvent_t* evs = rule->next_timing_events();
     if (prec == WQ_PREC_F64)
         e = wqd::launch_elem_f64(rule->it_wq, rule->src64_wq, tm, 0, (const double*)d_coef, (double*)d_vals, st, evs);
+    else if (prec == WQ_PREC_TC)
+        e = wqd::launch_elem_tc(rule->tit_wq, rule->tc_wq, tm, 0, (const double*)d_coef, (float*)d_vals, st, evs);
     else
         e = wqd::launch_elem_f32(rule->it_wq, rule->src_wq, tm, 0, (const double*)d_coef, (float*)d_vals,
                                  prec == WQ_PREC_F32, st, evs);
@@ -822,11 +878,15 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
     if (!op_terms(rule, op, alpha, false, tm, rule->G)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
     cudaError_t e;
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST)
+    if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST && prec != WQ_PREC_TC)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
+    if (prec == WQ_PREC_TC && !rule->tc_ok)
+        return fail(rule->ctx, WQ_ERR_ARG, "WQ_PREC_TC needs at most 64 points per element");
     cudaEvent_t* evs = rule->next_timing_events();
     if (prec == WQ_PREC_F64)
         e = wqd::launch_elem_f64(rule->it_gq, rule->src64_gq, tm, 1, (const double*)d_coef, (double*)d_vals, st, evs);
+    else if (prec == WQ_PREC_TC)
+        e = wqd::launch_elem_tc(rule->tit_gq, rule->tc_gq, tm, 1, (const double*)d_coef, (float*)d_vals, st, evs);
     else
         e = wqd::launch_elem_f32(rule->it_gq, rule->src_gq, tm, 1, (const double*)d_coef, (float*)d_vals,
                                  prec == WQ_PREC_F32, st, evs);
@@ -946,7 +1006,7 @@ wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* con
     if (!batch || !h_vals) return WQ_ERR_ARG;
     const int k = (int)batch->rules.size();
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == WQ_PREC_F64) {   // the FP64 row kernel, one launch per rule
+    if (prec == WQ_PREC_F64 || prec == WQ_PREC_TC) {   // one launch pair per rule
         for (int r = 0; r < k; ++r) {
             wq_status s = wq_assemble(batch->rules[r], op, h_coefs ? h_coefs[r] : nullptr, alpha, prec, h_vals[r],
                                       stream);

@@ -86,6 +86,44 @@ struct ElemSrc64 {
     int nc, nwc;
 };
 
+// Tensor-core element contraction (WQ_PREC_TC).  Per tile, it2[k] = {first function
+// of the element in the per-function arrays, offset of the element's trial-side slices
+// in bs (words), element, P rounded up to 8}.  The trial side of element e (table
+// component c, column block cb of 16 functions, half-chunk hh of 8 points) is stored
+// in mma fragment order: 32 lanes x 8 words, word nt * 4 + l of lane (g, t4) holding
+// slice l of T[q][n] for q = 8 hh + 2 t4 (low half) and q + 1 (high half), column
+// n = 16 cb + 8 nt + g, as bf16 integers of T 2^(8 - f_ec) (f_ec = fexp[e nc + c],
+// 2^f_ec >= max |T| over the element).  vmax[(fn + a) nv + v] bounds the test-side
+// values of local function a over the element's points (v: weight column, or
+// table component for Gauss items).
+struct TcItems {
+    int64_t n;
+    const int4* item;
+    const int32_t* kb;
+    const int4* it2;
+};
+struct TcSrc {
+    const int32_t* scat;
+    float2* kscr;
+    const int32_t* gptr;
+    const float2* vsrc;     // test side: element-major split weights (WQ) or split table (Gauss)
+    const float2* gw2;      // split Gauss weights (Gauss items)
+    const uint32_t* bs;     // trial-side slices
+    const int32_t* fexp;    // [E][nc]
+    const float* vmax;      // [sum_e m_e][nv]
+    int64_t nnz;
+    int nc, nwc;
+};
+// Set-up of the trial-side slices: el[e] = {table offset, points, element-major weight
+// row (WQ), first function}; bs_ptr[e] = the element's slice offset (words).
+struct TcPrep {
+    const int4* el;
+    const int64_t* bs_ptr;
+    uint32_t* bs;
+    int32_t* fexp;
+    float* vmax;
+};
+
 // Per-call device pointers, passed as a kernel parameter (N = 1 for one rule).
 constexpr int WQ_BATCH_MAX = 256;
 template <int N>

@@ -405,23 +405,6 @@ __global__ void __launch_bounds__(256) k_gather_f32(ElemSrc one, BatchPlan bp, c
     if (n + 1 < nnz) vals[n + 1] = hi1 + lo1;
 }
 
-static TermsF terms_f(const Terms& tm, int ntk) {
-    TermsF tf{};
-    tf.cstride = tm.cstride;
-    for (int t = 0; t < ntk; ++t) {
-        const bool real = t < tm.nt;
-        tf.wc[t] = real ? tm.t[t].wc : 0;
-        tf.tc[t] = real ? tm.t[t].tc : 0;
-        tf.sc[t] = real ? tm.t[t].sc : 0;
-        tf.crow[t] = real ? tm.t[t].crow : -1;
-        tf.scale[t] = real ? tm.t[t].scale : 0.0;   // padding terms contribute zero
-        tf.shi[t] = (float)tf.scale[t];
-        tf.slo[t] = (float)(tf.scale[t] - (double)tf.shi[t]);
-        tf.ncrow = std::max(tf.ncrow, tf.crow[t] + 1);
-    }
-    return tf;
-}
-
 // Element kernel, then the per-entry sums as a programmatic dependent launch (its
 // grid is set up while the element kernel drains and waits with griddepcontrol.wait).
 template <bool BATCH, int NP>
@@ -429,7 +412,7 @@ static cudaError_t launch_elem_pair(const ElemItems& it, const ElemSrc& one, con
                                     const PtrTable<NP>& pt, const Terms& tm, int gauss, bool compensated,
                                     int64_t n_items, int64_t n_gblocks, cudaStream_t st, cudaEvent_t* evs) {
     const int ntk = tm.nt <= 4 ? tm.nt : 8;         // more than 4 terms run as 8 (zero padding)
-    const TermsF tf = terms_f(tm, ntk);
+    const TermsF tf = make_terms_f(tm, ntk);
     const unsigned eb = (unsigned)((n_items + EL_NWARP - 1) / EL_NWARP);
 #define WQ_EL_CASE(N, C)                                                                                  \
     do {                                                                                                  \
@@ -489,6 +472,25 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemSrc& src, const Terms
     }
     if (evs) cudaEventRecord(evs[2], st);
     return e;
+}
+
+cudaError_t launch_gather_f32(const ElemSrc& src, float* vals, bool compensated, cudaStream_t st) {
+    if (src.nnz == 0) return cudaSuccess;
+    PtrTable<1> pt;
+    pt.coef[0] = nullptr;
+    pt.vals[0] = vals;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((src.nnz + 511) / 512));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (compensated) return cudaLaunchKernelEx(&cfg, k_gather_f32<true, false, 1>, src, BatchPlan{}, pt);
+    return cudaLaunchKernelEx(&cfg, k_gather_f32<false, false, 1>, src, BatchPlan{}, pt);
 }
 
 cudaError_t launch_elem_batch(const BatchPlan& bp, const double* const* coefs, float* const* vals, int k,

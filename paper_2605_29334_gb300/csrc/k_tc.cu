@@ -1,0 +1,411 @@
+// Element contraction on the tensor cores, error-free (WQ_PREC_TC).
+//
+// The element blocks of Eqs. 9, 11, 12 and S,
+//     K_e[a][b] = sum_{t, q} s^t_{aq} T^t_{qb}
+// (s: weights times coefficient, or Gauss weight times coefficient times test
+// function; T: trial table), are small dense products: 16 x 16 tiles with K =
+// (terms) x (points of e) mostly 16..32.  They go to the tensor cores through an
+// error-free splitting of the operands (the idea of Ozaki, Ogita, Oishi and Rump,
+// "Error-free transformations of matrix multiplication by using fast routines of
+// matrix multiplication and its applications", Numer. Algorithms 59, 2012):
+//  * the trial side of element e, component c, is scaled by 2^(8 - f), 2^f >= max|T|
+//    over the element, and rounded into 4 slices of 8 bits, T 2^(8-f) =
+//    sum_l b_l 2^(-8 l) with integers |b_0| <= 256, |b_l| <= 128 (exact bf16), to
+//    2^-25 of 256 (set-up, from the FP64 table);
+//  * the test side of row a is scaled by 2^(f_t + 8 - E_a), 2^E_a >= max_{t,q} |s^t_aq|
+//    2^(f_t) (the bound from per-function maxima of the weights and the largest
+//    coefficient of the element), and sliced the same way at run time from the split
+//    (hi, lo) products;
+//  * every product a_k b_l of bf16 integers is exact, and a level sum
+//    D_d = sum_{k + l = d} sum_K a_k b_l has |D_d| < 2^24 for K <= 160, so the FP32
+//    accumulation of the MMA is exact (integers below 2^24);
+//  * K_e[a][b] = 2^(E_a - 16) sum_{d <= 3} 2^(-8 d) D_d, the pairs with k + l > 3
+//    dropped (below 2^-32 of the tile's product scale).
+// On the 10,240-element Poisson workload this gives ~1e-8 normwise against FP64 (the
+// level-3 cut and the final FP32 rounding), the compensated SIMT path's accuracy at a
+// fraction of its instructions: the SIMT work is per (row, point, term) -- split
+// product and 4 slices, ~25 instructions -- instead of per (row, column, point, term).
+//
+// One warp per 16 x 16 tile (the FP32 path's tiles and slot map).  Lane (g, t4) =
+// (lane / 4, lane % 4) builds the m16n8k16 A fragments of its rows g, g + 8 at the
+// points 2 t4, 2 t4 + 1 of each half-chunk of 8 points (one term per half-chunk; each
+// term's points padded to a multiple of 8), loads the trial fragments precomputed in
+// that order (two 16-byte loads per half-chunk), and runs 10 slice pairs x 2 n-tiles
+// of mma.sync per chunk of 16 into 4 level accumulators.  Every 10 chunks the
+// levels are folded into a running (hi, lo) pair (TwoSum), so any K is exact.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace wqd {
+
+constexpr int TC_NWARP = 4;     // warps per block
+constexpr int TC_PMAX = 64;     // points per element (WQ side^2, Gauss 16 nsub)
+constexpr int TC_SEG = 10;      // chunks per exact segment: K <= 160
+
+__device__ __forceinline__ float tc_warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ void tc_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// 2^e as a float (0 below the normal range, clamped above).
+__device__ __forceinline__ float exp2i(int e) {
+    e = min(e, 127);
+    return e < -126 ? 0.0f : __int_as_float((e + 127) << 23);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Four 8-bit slices of y = yh + yl (|y| <= 256): k_s = rint of the remainder, the
+// remainder kept as an unevaluated sum (yh - k_s is exact) and scaled by 2^8.
+__device__ __forceinline__ void slice4(float yh, float yl, float (&k)[4]) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float v = rintf(yh + yl);
+        k[s] = v;
+        yh = (yh - v) * 256.0f;
+        yl = yl * 256.0f;
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float2 pick4(const float2 (&c)[4], int i) {
+    float2 v = c[0];
+    v = i == 1 ? c[1] : v;
+    v = i == 2 ? c[2] : v;
+    v = i == 3 ? c[3] : v;
+    return v;
+}
+
+template <int NT, bool GAUSS>
+__global__ void __launch_bounds__(TC_NWARP * 32, 4)
+    k_elem_tc(TcItems it, TcSrc src, const double* __restrict__ coef, TermsF tm) {
+    __shared__ __align__(16) float2 sMul[TC_NWARP][NT][TC_PMAX];   // per-term multipliers at the points
+    __shared__ int sTerm[TC_NWARP][NT][3];                          // test column, slice block, f_t + 8
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * TC_NWARP + wib;
+    if (k >= it.n) return;
+    const int4 d = it.item[k];
+    const int4 d2 = it.it2[k];
+    const int kb = it.kb[k];
+    const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
+    const int hpt = d2.w >> 3, ncb = (m + 15) >> 4;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int nt = tm.nt, nc = src.nc, nv = GAUSS ? src.nc : src.nwc;
+
+    // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1
+    // of both n-tiles): issued first, used at the end
+    int slot[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        const int a = a0 + g + 8 * (x >> 2), b = b0 + 8 * ((x >> 1) & 1) + 2 * t4 + (x & 1);
+        slot[x] = (a < m && b < m) ? __ldg(src.scat + kb + a * m + b) : -1;
+    }
+
+    // per-term multipliers (split pairs) at the element's points, zero up to P8
+    float2(*M)[TC_PMAX] = sMul[wib];
+    float cmax[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) cmax[t] = 0.0f;
+    for (int q = lane; q < 8 * hpt; q += 32) {
+        float2 cr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            cr[r] = make_float2(0.0f, 0.0f);
+            if (r < tm.ncrow && q < P) {
+                const double v = coef ? coef[r * tm.cstride + d.y + q] : 1.0;
+                const float h = __double2float_rn(v);
+                cr[r] = make_float2(h, __double2float_rn(v - (double)h));
+            }
+        }
+        const float2 gq = GAUSS && q < P ? src.gw2[d.y + q] : make_float2(1.0f, 0.0f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            float2 v = tm.crow[t] >= 0 ? pick4(cr, tm.crow[t]) : make_float2(tm.shi[t], tm.slo[t]);
+            if (GAUSS) {
+                const float ph = v.x * gq.x;
+                v = make_float2(ph, fmaf(v.x, gq.x, -ph) + fmaf(v.x, gq.y, v.y * gq.x));
+            }
+            if (q >= P) v = make_float2(0.0f, 0.0f);
+            M[t][q] = v;
+            cmax[t] = fmaxf(cmax[t], fabsf(v.x));
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) cmax[t] = tc_warp_max(cmax[t]);
+    if (lane < nt) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+            if (t == lane) {
+                const int vc = GAUSS ? tm.sc[t] : tm.wc[t];
+                sTerm[wib][t][0] = vc;
+                sTerm[wib][t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * 256;
+                sTerm[wib][t][2] = src.fexp[(int64_t)d2.z * nc + tm.tc[t]] + 8;
+            }
+    }
+    __syncwarp();
+
+    // row exponents: 2^E >= max_t vmax[row][v_t] cmax_t 2^f_t
+    int E[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int a = a0 + g + 8 * rr;
+        float bound = 0.0f;
+        if (a < m) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+                if (t < nt)
+                    bound = fmaxf(bound, src.vmax[(int64_t)(d2.x + a) * nv + sTerm[wib][t][0]] * cmax[t] *
+                                             exp2i(sTerm[wib][t][2] - 8));
+        }
+        int ex = 0;
+        if (bound > 0.0f) frexpf(bound * (1.0f + 0x1p-20f), &ex);
+        E[rr] = ex;
+    }
+
+    float acc[4][2][4];
+    float H[8], L[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) H[x] = L[x] = 0.0f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
+
+    // fold the level sums into (H, L) and clear them
+    auto fold = [&]() {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int n = (x >> 1) & 1, j = (x >> 2) * 2 + (x & 1);
+            const float lo = ((acc[3][n][j] * 0x1p-8f + acc[2][n][j]) * 0x1p-8f + acc[1][n][j]) * 0x1p-8f;
+            float s, e;
+            tc_two_sum(H[x], acc[0][n][j], s, e);
+            H[x] = s;
+            L[x] += lo + e;
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
+    };
+
+    const float2* __restrict__ V = src.vsrc;
+    const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 8;
+    const int nhalf = nt * hpt;
+    int seg = 0;
+    int t_cur = 0, hh_cur = 0;   // term and half-chunk of the next half
+    for (int h0 = 0; h0 < nhalf; h0 += 2) {
+        uint32_t A[4][4];
+        uint32_t Bw[2][8];
+#pragma unroll
+        for (int hs = 0; hs < 2; ++hs) {
+            if (h0 + hs < nhalf) {
+                const int t = t_cur, hh = hh_cur;
+                if (++hh_cur == hpt) hh_cur = 0, ++t_cur;
+                const int vc = sTerm[wib][t][0];
+                const uint4* bp = reinterpret_cast<const uint4*>(bsl + sTerm[wib][t][1] + hh * 256);
+                const uint4 w0 = __ldg(bp), w1 = __ldg(bp + 1);
+                Bw[hs][0] = w0.x, Bw[hs][1] = w0.y, Bw[hs][2] = w0.z, Bw[hs][3] = w0.w;
+                Bw[hs][4] = w1.x, Bw[hs][5] = w1.y, Bw[hs][6] = w1.z, Bw[hs][7] = w1.w;
+                const int q = hh * 8 + 2 * t4;
+                const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr) {
+                    const int a = a0 + g + 8 * rr;
+                    const float sg = exp2i(sTerm[wib][t][2] - E[rr]);
+                    float ks[2][4];
+#pragma unroll
+                    for (int pp = 0; pp < 2; ++pp) {
+                        float2 v = make_float2(0.0f, 0.0f);
+                        if (a < m && q + pp < P) {
+                            const int64_t off = GAUSS ? (int64_t)d.x + ((int64_t)(q + pp) * nc + vc) * m + a
+                                                      : ((int64_t)d.w + (int64_t)(q + pp) * m + a) * nv + vc;
+                            v = __ldg(V + off);
+                        }
+                        const float2 mu = pp ? mu1 : mu0;
+                        const float ph = v.x * mu.x;
+                        const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
+                        slice4(ph * sg, pl * sg, ks[pp]);
+                    }
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) A[s][hs * 2 + rr] = pack_bf16x2(ks[0][s], ks[1][s]);
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) A[s][hs * 2] = A[s][hs * 2 + 1] = 0u;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) Bw[hs][w] = 0u;
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+                for (int lb = 0; lb < 4 - ka; ++lb) mma_bf16(acc[ka + lb][n], A[ka], Bw[0][n * 4 + lb], Bw[1][n * 4 + lb]);
+        if (++seg == TC_SEG) {
+            fold();
+            seg = 0;
+        }
+    }
+    fold();
+    float2* __restrict__ kscr = src.kscr;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        const float sc = exp2i(E[x >> 2] - 16);
+        if (slot[x] >= 0) kscr[slot[x]] = make_float2(H[x] * sc, L[x] * sc);
+    }
+}
+
+cudaError_t launch_elem_tc(const TcItems& it, const TcSrc& src, const Terms& tm, int gauss, const double* coef,
+                           float* vals, cudaStream_t st, cudaEvent_t* evs) {
+    if (evs) cudaEventRecord(evs[0], st);
+    cudaError_t e = cudaSuccess;
+    if (src.nnz > 0 && it.n > 0) {
+        const int ntk = tm.nt <= 4 ? tm.nt : 8;
+        const TermsF tf = make_terms_f(tm, ntk);
+        const unsigned eb = (unsigned)((it.n + TC_NWARP - 1) / TC_NWARP);
+#define WQ_TC_CASE(N)                                                                                    \
+    do {                                                                                                 \
+        if (gauss)                                                                                       \
+            k_elem_tc<N, true><<<eb, TC_NWARP * 32, 0, st>>>(it, src, coef, tf);                         \
+        else                                                                                             \
+            k_elem_tc<N, false><<<eb, TC_NWARP * 32, 0, st>>>(it, src, coef, tf);                        \
+    } while (0)
+        switch (ntk) {
+            case 1: WQ_TC_CASE(1); break;
+            case 2: WQ_TC_CASE(2); break;
+            case 3: WQ_TC_CASE(3); break;
+            case 4: WQ_TC_CASE(4); break;
+            default: WQ_TC_CASE(8); break;
+        }
+#undef WQ_TC_CASE
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (evs) cudaEventRecord(evs[1], st);
+        ElemSrc gs{};
+        gs.ep = ElemPlan{src.scat, src.gptr, src.kscr};
+        gs.nnz = src.nnz;
+        e = launch_gather_f32(gs, vals, true, st);
+    } else if (evs) {
+        cudaEventRecord(evs[1], st);
+    }
+    if (evs) cudaEventRecord(evs[2], st);
+    return e;
+}
+
+// ------------------------------------------------------------------ set-up
+// One block per element: exponents f_c of the table components, the trial-side
+// slices in fragment order, and the test-side bounds (weights for WQ, table for Gauss).
+__global__ void __launch_bounds__(128) k_tc_prep(int nc, int nwc, const int32_t* __restrict__ m_arr,
+                                                 const double* __restrict__ table, const double* __restrict__ We,
+                                                 TcPrep pr) {
+    __shared__ double smax[4][8];
+    __shared__ int sf[8];
+    const int64_t e = blockIdx.x;
+    const int4 el = pr.el[e];
+    const int m = m_arr[e], P = el.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double* tb = table + el.x;
+    double mx[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) mx[c] = 0.0;
+    for (int x = threadIdx.x; x < P * m; x += blockDim.x) {
+        const int q = x / m, b = x - q * m;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < nc) mx[c] = fmax(mx[c], fabs(tb[((int64_t)q * nc + c) * m + b]));
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        double v = mx[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) smax[w][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        const int c = threadIdx.x;
+        const double v = fmax(fmax(smax[0][c], smax[1][c]), fmax(smax[2][c], smax[3][c]));
+        int f = 0;
+        if (v > 0.0) frexp(v, &f);   // 2^f > v
+        sf[c] = f;
+        pr.fexp[e * nc + c] = f;
+    }
+    __syncthreads();
+    // trial-side slices
+    const int ncb = (m + 15) >> 4, hpt = (P + 7) >> 3;
+    const int nitem = nc * ncb * hpt * 32;
+    uint32_t* out = pr.bs + pr.bs_ptr[e];
+    for (int x = threadIdx.x; x < nitem; x += blockDim.x) {
+        const int ln = x & 31;
+        int r = x >> 5;
+        const int hh = r % hpt;
+        r /= hpt;
+        const int cb = r % ncb, c = r / ncb;
+        const int g = ln >> 2, t4 = ln & 3;
+        uint32_t wd[8];
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            const int b = cb * 16 + n * 8 + g;
+            float kk[2][4];
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int q = hh * 8 + 2 * t4 + pp;
+                double y = (q < P && b < m) ? ldexp(tb[((int64_t)q * nc + c) * m + b], 8 - sf[c]) : 0.0;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const double v = rint(y);
+                    kk[pp][l] = (float)v;
+                    y = (y - v) * 256.0;
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l) wd[n * 4 + l] = pack_bf16x2(kk[0][l], kk[1][l]);
+        }
+        uint4* o4 = reinterpret_cast<uint4*>(out + ((int64_t)(c * ncb + cb) * hpt + hh) * 256 + ln * 8);
+        o4[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        o4[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+    }
+    // test-side bounds per (function, column)
+    const int nv = We ? nwc : nc;
+    for (int x = threadIdx.x; x < m * nv; x += blockDim.x) {
+        const int a = x / nv, v = x - a * nv;
+        double mv = 0.0;
+        for (int q = 0; q < P; ++q)
+            mv = fmax(mv, fabs(We ? We[((int64_t)el.z + (int64_t)q * m + a) * nwc + v]
+                                  : tb[((int64_t)q * nc + v) * m + a]));
+        pr.vmax[((int64_t)el.w + a) * nv + v] = __double2float_ru(mv);
+    }
+}
+
+cudaError_t launch_tc_prep(int64_t E, int nc, int nwc, const int32_t* m, const double* table, const double* We,
+                           const TcPrep& pr, cudaStream_t st) {
+    if (E == 0) return cudaSuccess;
+    if (nc > 8) return cudaErrorInvalidValue;
+    k_tc_prep<<<(unsigned)E, 128, 0, st>>>(nc, nwc, m, table, We, pr);
+    return cudaGetLastError();
+}
+
+}  // namespace wqd

@@ -27,8 +27,26 @@ struct TermsF {
     double scale[WQ_MAX_TERMS];
     float shi[WQ_MAX_TERMS], slo[WQ_MAX_TERMS];
     int ncrow;         // coefficient rows read (max crow + 1)
+    int nt;            // real terms (the rest are zero padding)
     int64_t cstride;
 };
+inline TermsF make_terms_f(const Terms& tm, int ntk) {
+    TermsF tf{};
+    tf.cstride = tm.cstride;
+    tf.nt = tm.nt;
+    for (int t = 0; t < ntk; ++t) {
+        const bool real = t < tm.nt;
+        tf.wc[t] = real ? tm.t[t].wc : 0;
+        tf.tc[t] = real ? tm.t[t].tc : 0;
+        tf.sc[t] = real ? tm.t[t].sc : 0;
+        tf.crow[t] = real ? tm.t[t].crow : -1;
+        tf.scale[t] = real ? tm.t[t].scale : 0.0;   // padding terms contribute zero
+        tf.shi[t] = (float)tf.scale[t];
+        tf.slo[t] = (float)(tf.scale[t] - (double)tf.shi[t]);
+        tf.ncrow = tf.ncrow > tf.crow[t] + 1 ? tf.ncrow : tf.crow[t] + 1;
+    }
+    return tf;
+}
 
 // Placement + basis evaluation at WQ (gauss = 0) or Gauss (gauss = 1) points:
 // table [pts][nc][m_e] per element, coordinates xout [pts][3], Gauss weights
@@ -52,6 +70,19 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemSrc& src, const Terms
 // the rules share their weight components and dimension, so one TermsF serves all).
 cudaError_t launch_elem_batch(const BatchPlan& bp, const double* const* coefs, float* const* vals, int k,
                               const Terms& tm, bool compensated, cudaStream_t st);
+
+// Per-entry sums of the slot buffer (FP32 pairs, TwoSum) as a programmatic dependent
+// of the element kernel just launched on st.
+cudaError_t launch_gather_f32(const ElemSrc& src, float* vals, bool compensated, cudaStream_t st);
+
+// Tensor-core element contraction (bf16 slices, exact FP32 integer sums; 1..8 terms),
+// then the per-entry sums; float CSR values.  Trial-side slices from launch_tc_prep.
+cudaError_t launch_elem_tc(const TcItems& it, const TcSrc& src, const Terms& tm, int gauss, const double* coef,
+                           float* vals, cudaStream_t st, cudaEvent_t* evs = nullptr);
+// Trial-side slices, exponents and test-side bounds of every element (rule set-up):
+// table [E blocks][P][nc][m]; We element-major FP64 weights (WQ) or null (Gauss).
+cudaError_t launch_tc_prep(int64_t E, int nc, int nwc, const int32_t* m, const double* table, const double* We,
+                           const TcPrep& pr, cudaStream_t st);
 
 // FP64 element-major assembly (same tiles and slot map; FMA sums; double CSR values).
 cudaError_t launch_elem_f64(const ElemItems& it, const ElemSrc64& src, const Terms& tm, int gauss,

@@ -61,6 +61,18 @@ struct wq_rule {
     wqd::ElemSrc src_wq{}, src_gq{};
     wqd::ElemSrc64 src64_wq{}, src64_gq{};
     double* d_We = nullptr;                // element-major FP64 weights [wbase_e + q m_e + a][nwc]
+    // tensor-core contraction (WQ_PREC_TC): per-element layout, trial-side slices,
+    // exponents, test-side bounds, per-tile extras, split Gauss weights
+    bool tc_ok = false;                    // every element has at most 64 points
+    int4 *d_tcel_wq = nullptr, *d_tcel_gq = nullptr, *d_it2_wq = nullptr, *d_it2_gq = nullptr;
+    int64_t *d_bsp_wq = nullptr, *d_bsp_gq = nullptr;
+    int64_t bs_words_wq = 0, bs_words_gq = 0;
+    uint32_t *d_bs_wq = nullptr, *d_bs_gq = nullptr;
+    int32_t *d_fexp_wq = nullptr, *d_fexp_gq = nullptr;
+    float *d_vmax_wq = nullptr, *d_vmax_gq = nullptr;
+    float2* d_gw2 = nullptr;
+    wqd::TcItems tit_wq{}, tit_gq{};
+    wqd::TcSrc tc_wq{}, tc_gq{};
     std::vector<int4> h_it_wq;          // host copies of the WQ tiles (batched assembly)
     std::vector<int32_t> h_kb_wq;
     int n_sm = 1;

@@ -20,7 +20,7 @@ WQ_OK, WQ_ERR_ARG, WQ_ERR_MESH, WQ_ERR_ILLPOSED, WQ_ERR_NOT_CONVERGED, WQ_ERR_NO
     WQ_ERR_OOM, WQ_ERR_NO_DEVICE = range(9)
 OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S, OP_HEAT_J = range(5)
 COMP_N, COMP_X, COMP_Y, COMP_Z, COMP_LAP = range(5)
-PREC_F64, PREC_F32, PREC_F32_FAST = 0, 1, 2
+PREC_F64, PREC_F32, PREC_F32_FAST, PREC_TC = 0, 1, 2, 3
 TYPE_NAMES = ["passive", "boundary", "irregular", "enriched_transition", "transition", "enriched_regular", "regular"]
 
 
