@@ -26,13 +26,15 @@
 // fraction of its instructions: the SIMT work is per (row, point, term) -- split
 // product and 4 slices, ~25 instructions -- instead of per (row, column, point, term).
 //
-// One warp per 16 x 16 tile (the FP32 path's tiles and slot map).  Lane (g, t4) =
-// (lane / 4, lane % 4) builds the m16n8k16 A fragments of its rows g, g + 8 at the
-// points 2 t4, 2 t4 + 1 of each half-chunk of 8 points (one term per half-chunk; each
-// term's points padded to a multiple of 8), loads the trial fragments precomputed in
-// that order (two 16-byte loads per half-chunk), and runs 10 slice pairs x 2 n-tiles
-// of mma.sync per chunk of 16 into 4 level accumulators.  Every 10 chunks the
-// levels are folded into a running (hi, lo) pair (TwoSum), so any K is exact.
+// One warp per 16 x 16 tile (the FP32 path's tiles and slot map).  The K range is
+// walked in half-chunks of 8 points of one term (each term's points padded to a
+// multiple of 8).  Lane (g, t4) = (lane / 4, lane % 4) builds the m16n8k8 A fragments
+// of its rows g, g + 8 at the points 2 t4, 2 t4 + 1, loads the trial fragments
+// precomputed in that order (two 16-byte loads), and runs 10 slice pairs x 2 n-tiles
+// of mma.sync into 4 level accumulators; the next half-chunk's loads are in flight
+// meanwhile.  Slicing uses FMA-pipe rounding (add and subtract 1.5 2^23) and a byte
+// permute for the bf16 packing.  Every 20 half-chunks (K = 160) the levels are added
+// to the tile's slots (a TwoSum against the earlier segments), so any K is exact.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -66,23 +68,35 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Four 8-bit slices of y = yh + yl (|y| <= 256): k_s = rint of the remainder, the
+// Round to the nearest integer (ties to even) for |x| < 2^22 with two FP32 adds:
+// adding 1.5 2^23 leaves no fraction bits (stays on the FMA pipe; rintf and the
+// conversions run on the slower conversion pipe).
+__device__ __forceinline__ float round_int(float x) {
+    return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
+// Four 8-bit slices of y = yh + yl (|y| <= 256): k_s = the rounded remainder, the
 // remainder kept as an unevaluated sum (yh - k_s is exact) and scaled by 2^8.
 __device__ __forceinline__ void slice4(float yh, float yl, float (&k)[4]) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-        const float v = rintf(yh + yl);
+        const float v = round_int(yh + yl);
         k[s] = v;
         yh = (yh - v) * 256.0f;
         yl = yl * 256.0f;
     }
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
+// Two integers |k| <= 256 as a bf16x2 word (low = first): their FP32 encodings have
+// zero low halves, so the bf16 encodings are the high halves (one byte permute).
+__device__ __forceinline__ uint32_t pack_int_bf16x2(float lo, float hi) {
+    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+__device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        : "r"(a0), "r"(a1), "r"(b0));
 }
 
 __device__ __forceinline__ float2 pick4(const float2 (&c)[4], int i) {
@@ -93,11 +107,43 @@ __device__ __forceinline__ float2 pick4(const float2 (&c)[4], int i) {
     return v;
 }
 
+__device__ __forceinline__ void cp_async_wait_all_tc() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tc_cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+
+// Operands of one half-chunk (8 points of one term): this lane's test-side values
+// (rows g, g + 8 at points 2 t4, 2 t4 + 1) and its trial-side fragment words.
+struct Half {
+    float2 v[4];     // [row][point]
+    uint4 b0, b1;    // n-tile 0 slices 0..3, n-tile 1 slices 0..3
+};
+
+template <bool GAUSS>
+__device__ __forceinline__ void load_half(Half& H, int t, int hh, const int (*sT)[3], const float2* __restrict__ Vb,
+                                          const uint32_t* __restrict__ bsl, int m, int P, int nc, int nv, int ra,
+                                          int t4) {
+    const int vc = sT[t][0];
+    const uint4* bp = reinterpret_cast<const uint4*>(bsl + sT[t][1] + hh * 256);
+    H.b0 = __ldg(bp);
+    H.b1 = __ldg(bp + 1);
+    const int q = hh * 8 + 2 * t4;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int a = ra + 8 * (x >> 1), qq = q + (x & 1);
+        H.v[x] = make_float2(0.0f, 0.0f);
+        if (a < m && qq < P) H.v[x] = __ldg(Vb + (GAUSS ? (qq * nc + vc) * m + a : (qq * m + a) * nv + vc));
+    }
+}
+
 template <int NT, bool GAUSS>
-__global__ void __launch_bounds__(TC_NWARP * 32, 4)
+__global__ void __launch_bounds__(TC_NWARP * 32, 5)
     k_elem_tc(TcItems it, TcSrc src, const double* __restrict__ coef, TermsF tm) {
     __shared__ __align__(16) float2 sMul[TC_NWARP][NT][TC_PMAX];   // per-term multipliers at the points
     __shared__ int sTerm[TC_NWARP][NT][3];                          // test column, slice block, f_t + 8
+    __shared__ int sSlot[TC_NWARP][8][32];                          // destination slots per (entry, lane)
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * TC_NWARP + wib;
@@ -107,18 +153,44 @@ __global__ void __launch_bounds__(TC_NWARP * 32, 4)
     const int kb = it.kb[k];
     const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
     const int hpt = d2.w >> 3, ncb = (m + 15) >> 4;
-    const int g = lane >> 2, t4 = lane & 3;
+    const int g = lane >> 2, t4 = lane & 3, ra = a0 + g;
     const int nt = tm.nt, nc = src.nc, nv = GAUSS ? src.nc : src.nwc;
-
-    // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1
-    // of both n-tiles): issued first, used at the end
-    int slot[8];
+    int(*sT)[3] = sTerm[wib];
+    if (lane < nt) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+            if (t == lane) {
+                sT[t][0] = GAUSS ? tm.sc[t] : tm.wc[t];
+                sT[t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * 256;
+            }
+    }
+    // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1 of
+    // both n-tiles), copied to shared memory in the background
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
-        const int a = a0 + g + 8 * (x >> 2), b = b0 + 8 * ((x >> 1) & 1) + 2 * t4 + (x & 1);
-        slot[x] = (a < m && b < m) ? __ldg(src.scat + kb + a * m + b) : -1;
+        const int a = ra + 8 * (x >> 2), b = b0 + 8 * ((x >> 1) & 1) + 2 * t4 + (x & 1);
+        if (a < m && b < m) tc_cp_async4(&sSlot[wib][x][lane], src.scat + kb + a * m + b);
+        else sSlot[wib][x][lane] = -1;
     }
-
+    __syncwarp();
+    const float2* __restrict__ Vb = GAUSS ? src.vsrc + d.x : src.vsrc + (int64_t)d.w * nv;
+    const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 8;
+    // first half-chunk's operands in flight while the scales are set up
+    Half cur;
+    load_half<GAUSS>(cur, 0, 0, sT, Vb, bsl, m, P, nc, nv, ra, t4);
+    if (lane < nt) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+            if (t == lane) sT[t][2] = src.fexp[(int64_t)d2.z * nc + tm.tc[t]] + 8;
+    }
+    float vm[2][NT];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int a = ra + 8 * rr;
+            vm[rr][t] = (a < m && t < nt) ? src.vmax[(int64_t)(d2.x + a) * nv + (GAUSS ? tm.sc[t] : tm.wc[t])] : 0.0f;
+        }
     // per-term multipliers (split pairs) at the element's points, zero up to P8
     float2(*M)[TC_PMAX] = sMul[wib];
     float cmax[NT];
@@ -150,57 +222,48 @@ __global__ void __launch_bounds__(TC_NWARP * 32, 4)
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t) cmax[t] = tc_warp_max(cmax[t]);
-    if (lane < nt) {
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-            if (t == lane) {
-                const int vc = GAUSS ? tm.sc[t] : tm.wc[t];
-                sTerm[wib][t][0] = vc;
-                sTerm[wib][t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * 256;
-                sTerm[wib][t][2] = src.fexp[(int64_t)d2.z * nc + tm.tc[t]] + 8;
-            }
-    }
     __syncwarp();
-
     // row exponents: 2^E >= max_t vmax[row][v_t] cmax_t 2^f_t
     int E[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-        const int a = a0 + g + 8 * rr;
         float bound = 0.0f;
-        if (a < m) {
 #pragma unroll
-            for (int t = 0; t < NT; ++t)
-                if (t < nt)
-                    bound = fmaxf(bound, src.vmax[(int64_t)(d2.x + a) * nv + sTerm[wib][t][0]] * cmax[t] *
-                                             exp2i(sTerm[wib][t][2] - 8));
-        }
+        for (int t = 0; t < NT; ++t)
+            if (t < nt) bound = fmaxf(bound, vm[rr][t] * cmax[t] * exp2i(sT[t][2] - 8));
         int ex = 0;
         if (bound > 0.0f) frexpf(bound * (1.0f + 0x1p-20f), &ex);
         E[rr] = ex;
     }
 
     float acc[4][2][4];
-    float H[8], L[8];
-#pragma unroll
-    for (int x = 0; x < 8; ++x) H[x] = L[x] = 0.0f;
 #pragma unroll
     for (int l = 0; l < 4; ++l)
 #pragma unroll
         for (int n = 0; n < 2; ++n)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
-
-    // fold the level sums into (H, L) and clear them
-    auto fold = [&]() {
+    // write the level sums of this segment to the slots (adding to the earlier
+    // segments' values, which only this lane writes) and clear them
+    auto flush = [&](bool first) {
+        cp_async_wait_all_tc();
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
             const int n = (x >> 1) & 1, j = (x >> 2) * 2 + (x & 1);
-            const float lo = ((acc[3][n][j] * 0x1p-8f + acc[2][n][j]) * 0x1p-8f + acc[1][n][j]) * 0x1p-8f;
-            float s, e;
-            tc_two_sum(H[x], acc[0][n][j], s, e);
-            H[x] = s;
-            L[x] += lo + e;
+            const int sl = sSlot[wib][x][lane];
+            const float sc = exp2i(E[x >> 2] - 16);
+            float hi = acc[0][n][j];
+            float lo = ((acc[3][n][j] * 0x1p-8f + acc[2][n][j]) * 0x1p-8f + acc[1][n][j]) * 0x1p-8f;
+            if (sl >= 0) {
+                if (!first) {
+                    const float2 o = src.kscr[sl];
+                    float s, e;
+                    tc_two_sum(o.x, hi * sc, s, e);
+                    src.kscr[sl] = make_float2(s, o.y + lo * sc + e);
+                } else {
+                    src.kscr[sl] = make_float2(hi * sc, lo * sc);
+                }
+            }
         }
 #pragma unroll
         for (int l = 0; l < 4; ++l)
@@ -210,72 +273,49 @@ __global__ void __launch_bounds__(TC_NWARP * 32, 4)
                 for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
     };
 
-    const float2* __restrict__ V = src.vsrc;
-    const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 8;
     const int nhalf = nt * hpt;
-    int seg = 0;
-    int t_cur = 0, hh_cur = 0;   // term and half-chunk of the next half
-    for (int h0 = 0; h0 < nhalf; h0 += 2) {
-        uint32_t A[4][4];
-        uint32_t Bw[2][8];
+    int t = 0, hh = 0, seg = 0;
+    bool first = true;
+    for (int h = 0; h < nhalf; ++h) {
+        // next half-chunk's operands in flight during this one's slicing and MMAs
+        int tn = t, hn = hh + 1;
+        if (hn == hpt) hn = 0, ++tn;
+        Half nxt;
+        if (h + 1 < nhalf) load_half<GAUSS>(nxt, tn, hn, sT, Vb, bsl, m, P, nc, nv, ra, t4);
+        const int q = hh * 8 + 2 * t4;
+        const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
+        uint32_t A[4][2];
 #pragma unroll
-        for (int hs = 0; hs < 2; ++hs) {
-            if (h0 + hs < nhalf) {
-                const int t = t_cur, hh = hh_cur;
-                if (++hh_cur == hpt) hh_cur = 0, ++t_cur;
-                const int vc = sTerm[wib][t][0];
-                const uint4* bp = reinterpret_cast<const uint4*>(bsl + sTerm[wib][t][1] + hh * 256);
-                const uint4 w0 = __ldg(bp), w1 = __ldg(bp + 1);
-                Bw[hs][0] = w0.x, Bw[hs][1] = w0.y, Bw[hs][2] = w0.z, Bw[hs][3] = w0.w;
-                Bw[hs][4] = w1.x, Bw[hs][5] = w1.y, Bw[hs][6] = w1.z, Bw[hs][7] = w1.w;
-                const int q = hh * 8 + 2 * t4;
-                const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
+        for (int rr = 0; rr < 2; ++rr) {
+            const float sg = exp2i(sT[t][2] - E[rr]);
+            float ks[2][4];
 #pragma unroll
-                for (int rr = 0; rr < 2; ++rr) {
-                    const int a = a0 + g + 8 * rr;
-                    const float sg = exp2i(sTerm[wib][t][2] - E[rr]);
-                    float ks[2][4];
-#pragma unroll
-                    for (int pp = 0; pp < 2; ++pp) {
-                        float2 v = make_float2(0.0f, 0.0f);
-                        if (a < m && q + pp < P) {
-                            const int64_t off = GAUSS ? (int64_t)d.x + ((int64_t)(q + pp) * nc + vc) * m + a
-                                                      : ((int64_t)d.w + (int64_t)(q + pp) * m + a) * nv + vc;
-                            v = __ldg(V + off);
-                        }
-                        const float2 mu = pp ? mu1 : mu0;
-                        const float ph = v.x * mu.x;
-                        const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
-                        slice4(ph * sg, pl * sg, ks[pp]);
-                    }
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) A[s][hs * 2 + rr] = pack_bf16x2(ks[0][s], ks[1][s]);
-                }
-            } else {
-#pragma unroll
-                for (int s = 0; s < 4; ++s) A[s][hs * 2] = A[s][hs * 2 + 1] = 0u;
-#pragma unroll
-                for (int w = 0; w < 8; ++w) Bw[hs][w] = 0u;
+            for (int pp = 0; pp < 2; ++pp) {
+                const float2 v = cur.v[rr * 2 + pp];
+                const float2 mu = pp ? mu1 : mu0;
+                const float ph = v.x * mu.x;
+                const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
+                slice4(ph * sg, pl * sg, ks[pp]);
             }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) A[s][rr] = pack_int_bf16x2(ks[0][s], ks[1][s]);
         }
+        const uint32_t bw[8] = {cur.b0.x, cur.b0.y, cur.b0.z, cur.b0.w, cur.b1.x, cur.b1.y, cur.b1.z, cur.b1.w};
 #pragma unroll
         for (int n = 0; n < 2; ++n)
 #pragma unroll
             for (int ka = 0; ka < 4; ++ka)
 #pragma unroll
-                for (int lb = 0; lb < 4 - ka; ++lb) mma_bf16(acc[ka + lb][n], A[ka], Bw[0][n * 4 + lb], Bw[1][n * 4 + lb]);
-        if (++seg == TC_SEG) {
-            fold();
+                for (int lb = 0; lb < 4 - ka; ++lb) mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], bw[n * 4 + lb]);
+        if (++seg == 2 * TC_SEG && h + 1 < nhalf) {
+            flush(first);
+            first = false;
             seg = 0;
         }
+        t = tn, hh = hn;
+        if (h + 1 < nhalf) cur = nxt;
     }
-    fold();
-    float2* __restrict__ kscr = src.kscr;
-#pragma unroll
-    for (int x = 0; x < 8; ++x) {
-        const float sc = exp2i(E[x >> 2] - 16);
-        if (slot[x] >= 0) kscr[slot[x]] = make_float2(H[x] * sc, L[x] * sc);
-    }
+    flush(first);
 }
 
 cudaError_t launch_elem_tc(const TcItems& it, const TcSrc& src, const Terms& tm, int gauss, const double* coef,
