@@ -68,23 +68,21 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Round to the nearest integer (ties to even) for |x| < 2^22 with two FP32 adds:
-// adding 1.5 2^23 leaves no fraction bits (stays on the FMA pipe; rintf and the
-// conversions run on the slower conversion pipe).
-__device__ __forceinline__ float round_int(float x) {
-    return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
-}
-
-// Four 8-bit slices of y = yh + yl (|y| <= 256): k_s = the rounded remainder, the
-// remainder kept as an unevaluated sum (yh - k_s is exact) and scaled by 2^8.
+// Four 8-bit slices of y = yh + yl (|y| <= 256, |yl| <= ulp(yh) / 2): integers k_s with
+// y = k0 + 2^-8 k1 + 2^-16 k2 + 2^-24 k3 to 2^-25.  Rounding to an integer adds and
+// subtracts 1.5 2^23 (FMA pipe; rintf runs on the slower conversion pipe).  Every
+// remainder yh - k0, r 2^8 - k1, t - k2 is exact; yl enters at the third slice
+// (|k2| <= 129), so 14 FP32 instructions.
 __device__ __forceinline__ void slice4(float yh, float yl, float (&k)[4]) {
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const float v = round_int(yh + yl);
-        k[s] = v;
-        yh = (yh - v) * 256.0f;
-        yl = yl * 256.0f;
-    }
+    const float M = 12582912.0f;
+    k[0] = __fsub_rn(__fadd_rn(yh, M), M);
+    float r = yh - k[0];
+    k[1] = __fsub_rn(__fmaf_rn(r, 256.0f, M), M);
+    r = __fmaf_rn(r, 256.0f, -k[1]);
+    const float t = __fmaf_rn(r, 256.0f, yl * 65536.0f);
+    k[2] = __fsub_rn(__fadd_rn(t, M), M);
+    r = t - k[2];
+    k[3] = __fsub_rn(__fmaf_rn(r, 256.0f, M), M);
 }
 
 // Two integers |k| <= 256 as a bf16x2 word (low = first): their FP32 encodings have
@@ -99,50 +97,56 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
         : "r"(a0), "r"(a1), "r"(b0));
 }
 
-__device__ __forceinline__ float2 pick4(const float2 (&c)[4], int i) {
-    float2 v = c[0];
-    v = i == 1 ? c[1] : v;
-    v = i == 2 ? c[2] : v;
-    v = i == 3 ? c[3] : v;
-    return v;
+// Smallest E with 2^E > x (x > 0, finite): the frexp exponent, from the encoding for
+// normal x.
+__device__ __forceinline__ int exp_above(float x) {
+    const unsigned e = (__float_as_uint(x) >> 23) & 255u;
+    if (e != 0u) return (int)e - 126;
+    int ex;
+    frexpf(x, &ex);
+    return ex;
 }
 
-__device__ __forceinline__ void cp_async_wait_all_tc() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
+// Operands of one half-chunk (8 points of one term): this lane's test-side values
+// (rows g, g + 8 at points 2 t4, 2 t4 + 1) and its trial-side fragment words.
 __device__ __forceinline__ void tc_cp_async4(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
 
-// Operands of one half-chunk (8 points of one term): this lane's test-side values
-// (rows g, g + 8 at points 2 t4, 2 t4 + 1) and its trial-side fragment words.
 struct Half {
     float2 v[4];     // [row][point]
     uint4 b0, b1;    // n-tile 0 slices 0..3, n-tile 1 slices 0..3
 };
 
-template <bool GAUSS>
-__device__ __forceinline__ void load_half(Half& H, int t, int hh, const int (*sT)[3], const float2* __restrict__ Vb,
-                                          const uint32_t* __restrict__ bsl, int m, int P, int nc, int nv, int ra,
-                                          int t4) {
-    const int vc = sT[t][0];
-    const uint4* bp = reinterpret_cast<const uint4*>(bsl + sT[t][1] + hh * 256);
+// Per-tile constants of the test-side loads: element base, row strides, validity.
+struct TileV {
+    const float2* base;
+    int r0, r1;          // offsets of rows g, g + 8 (-1: beyond m)
+    int qs, cs;          // stride of a point, of a column / component
+};
+
+__device__ __forceinline__ void load_half(Half& H, const TileV& tv, int vc, int boff, int hh, int P, int t4,
+                                          const uint32_t* __restrict__ bsl) {
+    const uint4* bp = reinterpret_cast<const uint4*>(bsl + boff + hh * 256);
     H.b0 = __ldg(bp);
     H.b1 = __ldg(bp + 1);
     const int q = hh * 8 + 2 * t4;
-#pragma unroll
-    for (int x = 0; x < 4; ++x) {
-        const int a = ra + 8 * (x >> 1), qq = q + (x & 1);
-        H.v[x] = make_float2(0.0f, 0.0f);
-        if (a < m && qq < P) H.v[x] = __ldg(Vb + (GAUSS ? (qq * nc + vc) * m + a : (qq * m + a) * nv + vc));
-    }
+    const float2* vb = tv.base + q * tv.qs + vc * tv.cs;
+    const bool q0 = q < P, q1 = q + 1 < P;
+    const float2 z = make_float2(0.0f, 0.0f);
+    H.v[0] = (tv.r0 >= 0 && q0) ? __ldg(vb + tv.r0) : z;
+    H.v[1] = (tv.r0 >= 0 && q1) ? __ldg(vb + tv.qs + tv.r0) : z;
+    H.v[2] = (tv.r1 >= 0 && q0) ? __ldg(vb + tv.r1) : z;
+    H.v[3] = (tv.r1 >= 0 && q1) ? __ldg(vb + tv.qs + tv.r1) : z;
 }
 
 template <int NT, bool GAUSS>
 __global__ void __launch_bounds__(TC_NWARP * 32, 5)
     k_elem_tc(TcItems it, TcSrc src, const double* __restrict__ coef, TermsF tm) {
     __shared__ __align__(16) float2 sMul[TC_NWARP][NT][TC_PMAX];   // per-term multipliers at the points
-    __shared__ int sTerm[TC_NWARP][NT][3];                          // test column, slice block, f_t + 8
+    __shared__ int sTerm[TC_NWARP][NT][2];                          // test column, slice block
+    __shared__ float sSg[TC_NWARP][NT][2][32];                      // per (term, row, lane) slice scale
     __shared__ int sSlot[TC_NWARP][8][32];                          // destination slots per (entry, lane)
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -155,7 +159,8 @@ __global__ void __launch_bounds__(TC_NWARP * 32, 5)
     const int hpt = d2.w >> 3, ncb = (m + 15) >> 4;
     const int g = lane >> 2, t4 = lane & 3, ra = a0 + g;
     const int nt = tm.nt, nc = src.nc, nv = GAUSS ? src.nc : src.nwc;
-    int(*sT)[3] = sTerm[wib];
+    int(*sT)[2] = sTerm[wib];
+    int f8[NT];   // f_t + 8 per term (uniform)
     if (lane < nt) {
 #pragma unroll
         for (int t = 0; t < NT; ++t)
@@ -164,77 +169,87 @@ __global__ void __launch_bounds__(TC_NWARP * 32, 5)
                 sT[t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * 256;
             }
     }
-    // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1 of
-    // both n-tiles), copied to shared memory in the background
-#pragma unroll
-    for (int x = 0; x < 8; ++x) {
-        const int a = ra + 8 * (x >> 2), b = b0 + 8 * ((x >> 1) & 1) + 2 * t4 + (x & 1);
-        if (a < m && b < m) tc_cp_async4(&sSlot[wib][x][lane], src.scat + kb + a * m + b);
-        else sSlot[wib][x][lane] = -1;
-    }
     __syncwarp();
-    const float2* __restrict__ Vb = GAUSS ? src.vsrc + d.x : src.vsrc + (int64_t)d.w * nv;
+    TileV tv;
+    tv.base = GAUSS ? src.vsrc + d.x : src.vsrc + (int64_t)d.w * nv;
+    tv.r0 = ra < m ? (GAUSS ? ra : ra * nv) : -1;
+    tv.r1 = ra + 8 < m ? (GAUSS ? ra + 8 : (ra + 8) * nv) : -1;
+    tv.qs = GAUSS ? nc * m : m * nv;
+    tv.cs = GAUSS ? m : 1;
     const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 8;
     // first half-chunk's operands in flight while the scales are set up
-    Half cur;
-    load_half<GAUSS>(cur, 0, 0, sT, Vb, bsl, m, P, nc, nv, ra, t4);
-    if (lane < nt) {
+    Half h0;
+    load_half(h0, tv, sT[0][0], sT[0][1], 0, P, t4, bsl);
+    // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1
+    // of both n-tiles), copied to shared memory in the background
+    {
+        const int32_t* sp = src.scat + kb + ra * m + b0 + 2 * t4;
+        const int bc = b0 + 2 * t4;
 #pragma unroll
-        for (int t = 0; t < NT; ++t)
-            if (t == lane) sT[t][2] = src.fexp[(int64_t)d2.z * nc + tm.tc[t]] + 8;
+        for (int x = 0; x < 8; ++x) {
+            const int dr = 8 * (x >> 2), dc = 8 * ((x >> 1) & 1) + (x & 1);
+            if (ra + dr < m && bc + dc < m) tc_cp_async4(&sSlot[wib][x][lane], sp + dr * m + dc);
+            else sSlot[wib][x][lane] = -1;
+        }
     }
     float vm[2][NT];
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int a = ra + 8 * rr;
-            vm[rr][t] = (a < m && t < nt) ? src.vmax[(int64_t)(d2.x + a) * nv + (GAUSS ? tm.sc[t] : tm.wc[t])] : 0.0f;
-        }
+    for (int t = 0; t < NT; ++t) {
+        f8[t] = t < nt ? __ldg(src.fexp + (int64_t)d2.z * nc + tm.tc[t]) + 8 : 0;
+        const int vc = GAUSS ? tm.sc[t] : tm.wc[t];
+        const float* vr = src.vmax + (int64_t)(d2.x + ra) * nv + vc;
+        vm[0][t] = (t < nt && ra < m) ? __ldg(vr) : 0.0f;
+        vm[1][t] = (t < nt && ra + 8 < m) ? __ldg(vr + 8 * nv) : 0.0f;
+    }
     // per-term multipliers (split pairs) at the element's points, zero up to P8
     float2(*M)[TC_PMAX] = sMul[wib];
     float cmax[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) cmax[t] = 0.0f;
     for (int q = lane; q < 8 * hpt; q += 32) {
+        const bool in = q < P;
         float2 cr[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             cr[r] = make_float2(0.0f, 0.0f);
-            if (r < tm.ncrow && q < P) {
+            if (r < tm.ncrow && in) {
                 const double v = coef ? coef[r * tm.cstride + d.y + q] : 1.0;
                 const float h = __double2float_rn(v);
                 cr[r] = make_float2(h, __double2float_rn(v - (double)h));
             }
         }
-        const float2 gq = GAUSS && q < P ? src.gw2[d.y + q] : make_float2(1.0f, 0.0f);
+        const float2 gq = GAUSS && in ? src.gw2[d.y + q] : make_float2(1.0f, 0.0f);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            float2 v = tm.crow[t] >= 0 ? pick4(cr, tm.crow[t]) : make_float2(tm.shi[t], tm.slo[t]);
+            const int c = tm.crow[t];
+            float2 v = c == 0 ? cr[0] : (c == 1 ? cr[1] : (c == 2 ? cr[2] : (c == 3 ? cr[3] :
+                       make_float2(tm.shi[t], tm.slo[t]))));
             if (GAUSS) {
                 const float ph = v.x * gq.x;
                 v = make_float2(ph, fmaf(v.x, gq.x, -ph) + fmaf(v.x, gq.y, v.y * gq.x));
             }
-            if (q >= P) v = make_float2(0.0f, 0.0f);
+            if (!in) v = make_float2(0.0f, 0.0f);
             M[t][q] = v;
             cmax[t] = fmaxf(cmax[t], fabsf(v.x));
         }
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t) cmax[t] = tc_warp_max(cmax[t]);
-    __syncwarp();
-    // row exponents: 2^E >= max_t vmax[row][v_t] cmax_t 2^f_t
-    int E[2];
+    // row exponents 2^E > max_t vmax[row][v_t] cmax_t 2^f_t, the slice scales
+    // 2^(f_t + 8 - E) per (term, row) and the entries' scales 2^(E - 16)
+    float esc[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
         float bound = 0.0f;
 #pragma unroll
         for (int t = 0; t < NT; ++t)
-            if (t < nt) bound = fmaxf(bound, vm[rr][t] * cmax[t] * exp2i(sT[t][2] - 8));
-        int ex = 0;
-        if (bound > 0.0f) frexpf(bound * (1.0f + 0x1p-20f), &ex);
-        E[rr] = ex;
+            if (t < nt) bound = fmaxf(bound, vm[rr][t] * cmax[t] * exp2i(f8[t] - 8));
+        const int E = bound > 0.0f ? exp_above(bound * (1.0f + 0x1p-20f)) : 0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) sSg[wib][t][rr][lane] = exp2i(f8[t] - E);
+        esc[rr] = exp2i(E - 16);
     }
+    __syncwarp();
 
     float acc[4][2][4];
 #pragma unroll
@@ -243,25 +258,54 @@ __global__ void __launch_bounds__(TC_NWARP * 32, 5)
         for (int n = 0; n < 2; ++n)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
+
+    // slices of one half-chunk's test side into A fragments, then the 20 MMAs
+    auto step = [&](const Half& H, int t, int hh) {
+        const int q = hh * 8 + 2 * t4;
+        const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
+        uint32_t A[4][2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const float sg = sSg[wib][t][rr][lane];
+            float ks[2][4];
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const float2 v = H.v[rr * 2 + pp];
+                const float2 mu = pp ? mu1 : mu0;
+                const float ph = v.x * mu.x;
+                const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
+                slice4(ph * sg, pl * sg, ks[pp]);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) A[s][rr] = pack_int_bf16x2(ks[0][s], ks[1][s]);
+        }
+        const uint32_t bw[8] = {H.b0.x, H.b0.y, H.b0.z, H.b0.w, H.b1.x, H.b1.y, H.b1.z, H.b1.w};
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+                for (int lb = 0; lb < 4 - ka; ++lb) mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], bw[n * 4 + lb]);
+    };
     // write the level sums of this segment to the slots (adding to the earlier
     // segments' values, which only this lane writes) and clear them
     auto flush = [&](bool first) {
-        cp_async_wait_all_tc();
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
-            const int n = (x >> 1) & 1, j = (x >> 2) * 2 + (x & 1);
             const int sl = sSlot[wib][x][lane];
-            const float sc = exp2i(E[x >> 2] - 16);
-            float hi = acc[0][n][j];
-            float lo = ((acc[3][n][j] * 0x1p-8f + acc[2][n][j]) * 0x1p-8f + acc[1][n][j]) * 0x1p-8f;
+            const int n = (x >> 1) & 1, j = (x >> 2) * 2 + (x & 1);
+            const float sc = esc[x >> 2];
+            const float hi = acc[0][n][j] * sc;
+            const float lo = ((acc[3][n][j] * 0x1p-8f + acc[2][n][j]) * 0x1p-8f + acc[1][n][j]) * (0x1p-8f * sc);
             if (sl >= 0) {
                 if (!first) {
                     const float2 o = src.kscr[sl];
-                    float s, e;
-                    tc_two_sum(o.x, hi * sc, s, e);
-                    src.kscr[sl] = make_float2(s, o.y + lo * sc + e);
+                    float s2, e2;
+                    tc_two_sum(o.x, hi, s2, e2);
+                    src.kscr[sl] = make_float2(s2, o.y + lo + e2);
                 } else {
-                    src.kscr[sl] = make_float2(hi * sc, lo * sc);
+                    src.kscr[sl] = make_float2(hi, lo);
                 }
             }
         }
@@ -273,47 +317,27 @@ __global__ void __launch_bounds__(TC_NWARP * 32, 5)
                 for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
     };
 
+    // walk the half-chunks two at a time, the next one's operands in flight
     const int nhalf = nt * hpt;
     int t = 0, hh = 0, seg = 0;
     bool first = true;
-    for (int h = 0; h < nhalf; ++h) {
-        // next half-chunk's operands in flight during this one's slicing and MMAs
-        int tn = t, hn = hh + 1;
-        if (hn == hpt) hn = 0, ++tn;
-        Half nxt;
-        if (h + 1 < nhalf) load_half<GAUSS>(nxt, tn, hn, sT, Vb, bsl, m, P, nc, nv, ra, t4);
-        const int q = hh * 8 + 2 * t4;
-        const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
-        uint32_t A[4][2];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const float sg = exp2i(sT[t][2] - E[rr]);
-            float ks[2][4];
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                const float2 v = cur.v[rr * 2 + pp];
-                const float2 mu = pp ? mu1 : mu0;
-                const float ph = v.x * mu.x;
-                const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
-                slice4(ph * sg, pl * sg, ks[pp]);
-            }
-#pragma unroll
-            for (int s = 0; s < 4; ++s) A[s][rr] = pack_int_bf16x2(ks[0][s], ks[1][s]);
-        }
-        const uint32_t bw[8] = {cur.b0.x, cur.b0.y, cur.b0.z, cur.b0.w, cur.b1.x, cur.b1.y, cur.b1.z, cur.b1.w};
-#pragma unroll
-        for (int n = 0; n < 2; ++n)
-#pragma unroll
-            for (int ka = 0; ka < 4; ++ka)
-#pragma unroll
-                for (int lb = 0; lb < 4 - ka; ++lb) mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], bw[n * 4 + lb]);
-        if (++seg == 2 * TC_SEG && h + 1 < nhalf) {
+    Half h1;
+    for (int h = 0; h < nhalf; h += 2) {
+        int t1 = t, hh1 = hh + 1;
+        if (hh1 == hpt) hh1 = 0, ++t1;
+        if (h + 1 < nhalf) load_half(h1, tv, sT[t1][0], sT[t1][1], hh1, P, t4, bsl);
+        step(h0, t, hh);
+        int t2 = t1, hh2 = hh1 + 1;
+        if (hh2 == hpt) hh2 = 0, ++t2;
+        if (h + 2 < nhalf) load_half(h0, tv, sT[t2][0], sT[t2][1], hh2, P, t4, bsl);
+        if (h + 1 < nhalf) step(h1, t1, hh1);
+        t = t2, hh = hh2;
+        seg += 2;
+        if (seg == 2 * TC_SEG && h + 2 < nhalf) {
             flush(first);
             first = false;
             seg = 0;
         }
-        t = tn, hh = hn;
-        if (h + 1 < nhalf) cur = nxt;
     }
     flush(first);
 }
