@@ -111,6 +111,10 @@ struct TcSrc {
     const uint32_t* bs;     // trial-side slices
     const int32_t* fexp;    // [E][nc]
     const float* vmax;      // [sum_e m_e][nv]
+    const int64_t* pptr;    // [E+1] first point of every element (WQ or Gauss points)
+    float2* cp2;            // per call: split coefficient rows [4][npts]
+    float* cmx;             // per call: their per-element maxima [E][5] (5th: Gauss weights)
+    int64_t npts, E;
     int64_t nnz;
     int nc, nwc;
 };
