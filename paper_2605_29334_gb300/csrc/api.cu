@@ -509,9 +509,7 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         (!dalloc(R, R->d_bs_wq, (size_t)bsp_wq[E], sst) || !dalloc(R, R->d_bs_gq, (size_t)bsp_gq[E], sst) ||
          !dalloc(R, R->d_fexp_wq, (size_t)E * nc, sst) || !dalloc(R, R->d_fexp_gq, (size_t)E * nc, sst) ||
          !dalloc(R, R->d_vmax_wq, (size_t)B.fn_ptr[E] * R->nwc, sst) ||
-         !dalloc(R, R->d_vmax_gq, (size_t)B.fn_ptr[E] * nc, sst) || !dalloc(R, R->d_gw2, (size_t)R->G, sst) ||
-         !dalloc(R, R->d_cp2_wq, (size_t)R->Q * 4, sst) || !dalloc(R, R->d_cp2_gq, (size_t)R->G * 4, sst) ||
-         !dalloc(R, R->d_cmx_wq, (size_t)E * 5, sst) || !dalloc(R, R->d_cmx_gq, (size_t)E * 5, sst)))
+         !dalloc(R, R->d_vmax_gq, (size_t)B.fn_ptr[E] * nc, sst) || !dalloc(R, R->d_gw2, (size_t)R->G, sst)))
         return bail(sst);
     if (!dalloc(R, R->d_table, (size_t)bt_ptr[E], sst) || !dalloc(R, R->d_gtable, (size_t)gbt_ptr[E], sst) ||
         !dalloc(R, R->d_x, (size_t)R->Q * 3, sst) || !dalloc(R, R->d_gx, (size_t)R->G * 3, sst) ||
@@ -574,11 +572,11 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     R->src64_gq = {R->d_scat, R->d_gptr, reinterpret_cast<double*>(R->d_kscr), R->d_gtable, nullptr, R->d_gw, R->nnz,
                    nc, R->nwc};
     R->tc_wq = {R->d_scat, R->d_kscr, R->d_gptr, R->d_W2, nullptr, R->d_bs_wq, R->d_fexp_wq, R->d_vmax_wq,
-                R->d_pt_ptr, R->d_cp2_wq, R->d_cmx_wq, R->Q, E, R->nnz, nc, R->nwc};
+                R->nnz, nc, R->nwc};
     R->tc_gq = {R->d_scat, R->d_kscr, R->d_gptr, R->d_gtable2, R->d_gw2, R->d_bs_gq, R->d_fexp_gq, R->d_vmax_gq,
-                R->d_gp_ptr, R->d_cp2_gq, R->d_cmx_gq, R->G, E, R->nnz, nc, R->nwc};
-    R->tit_wq = {(int64_t)it_wq.size(), R->d_it_wq, R->d_kb_wq, R->d_it2_wq};
-    R->tit_gq = {(int64_t)it_gq.size(), R->d_it_gq, R->d_kb_gq, R->d_it2_gq};
+                R->nnz, nc, R->nwc};
+    R->tit_wq = {(int64_t)it_wq.size(), R->d_it_wq, R->d_kb_wq, R->d_it2_wq, R->n_sm};
+    R->tit_gq = {(int64_t)it_gq.size(), R->d_it_gq, R->d_kb_gq, R->d_it2_gq, R->n_sm};
     R->h_it_wq = it_wq;
     R->h_kb_wq = kb_wq;
 

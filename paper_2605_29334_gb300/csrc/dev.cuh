@@ -101,6 +101,7 @@ struct TcItems {
     const int4* item;
     const int32_t* kb;
     const int4* it2;
+    int n_sm;               // multiprocessors (persistent grid size)
 };
 struct TcSrc {
     const int32_t* scat;
@@ -111,10 +112,6 @@ struct TcSrc {
     const uint32_t* bs;     // trial-side slices
     const int32_t* fexp;    // [E][nc]
     const float* vmax;      // [sum_e m_e][nv]
-    const int64_t* pptr;    // [E+1] first point of every element (WQ or Gauss points)
-    float2* cp2;            // per call: split coefficient rows [4][npts]
-    float* cmx;             // per call: their per-element maxima [E][5] (5th: Gauss weights)
-    int64_t npts, E;
     int64_t nnz;
     int nc, nwc;
 };

@@ -46,7 +46,7 @@ namespace wqd {
 constexpr int TC_NWARP = 4;     // warps per block
 constexpr int TC_PMAX = 64;     // points per element (WQ side^2, Gauss 16 nsub)
 constexpr int TC_SEG = 10;      // chunks per exact segment: K <= 160
-constexpr int TC_BLOCKS_PER_SM = 5;
+constexpr int TC_BLOCKS_PER_SM = 4;   // resident blocks at the register budget (no spills)
 
 __device__ __forceinline__ float tc_warp_max(float v) {
 #pragma unroll
@@ -110,275 +110,255 @@ __device__ __forceinline__ int exp_above(float x) {
     return ex;
 }
 
+// Operands of one half-chunk (8 points of one term): this lane's test-side values
+// (rows g, g + 8 at points 2 t4, 2 t4 + 1) and its trial-side fragment words.
 __device__ __forceinline__ void tc_cp_async4(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
 
-// Operands of one half-chunk (8 points of one term) for one n-tile: this lane's
-// test-side values (rows g, g + 8 at points 2 t4, 2 t4 + 1), the term's multipliers at
-// those points, and the trial-side fragment words (slices 0..3).
 struct Half {
     float2 v[4];     // [row][point]
-    float2 mu[2];    // [point]
-    uint4 b;
+    uint4 b0, b1;    // n-tile 0 slices 0..3, n-tile 1 slices 0..3
 };
 
-// Per-tile constants of the loads.
+// Per-tile constants of the test-side loads: element base, row strides, validity.
 struct TileV {
-    const float2* base;  // test side of the element
+    const float2* base;
     int r0, r1;          // offsets of rows g, g + 8 (-1: beyond m)
     int qs, cs;          // stride of a point, of a column / component
-    int p0, P;           // first point, points
 };
 
-// Per-term constants (warp-uniform, in shared memory).
-struct TermC {
-    int vc;              // test-side column (weight column, or table component)
-    int boff;            // trial slices of (component, column block), words
-    int mrow;            // multiplier row in cp2 (-1: constant)
-    float shi, slo;      // constant multiplier (split)
-};
-
-template <bool GAUSS>
-__device__ __forceinline__ void load_half(Half& H, const TileV& tv, const TermC& tc, int hh, int n, int t4,
-                                          const uint32_t* __restrict__ bsl, const float2* __restrict__ cp2,
-                                          int64_t npts, const float2* __restrict__ gw2) {
-    H.b = __ldg(reinterpret_cast<const uint4*>(bsl + tc.boff + hh * 256) + n);
+__device__ __forceinline__ void load_half(Half& H, const TileV& tv, int vc, int boff, int hh, int P, int t4,
+                                          const uint32_t* __restrict__ bsl) {
+    const uint4* bp = reinterpret_cast<const uint4*>(bsl + boff + hh * 256);
+    H.b0 = __ldg(bp);
+    H.b1 = __ldg(bp + 1);
     const int q = hh * 8 + 2 * t4;
-    const float2* vb = tv.base + q * tv.qs + tc.vc * tv.cs;
-    const bool q0 = q < tv.P, q1 = q + 1 < tv.P;
+    const float2* vb = tv.base + q * tv.qs + vc * tv.cs;
+    const bool q0 = q < P, q1 = q + 1 < P;
     const float2 z = make_float2(0.0f, 0.0f);
     H.v[0] = (tv.r0 >= 0 && q0) ? __ldg(vb + tv.r0) : z;
     H.v[1] = (tv.r0 >= 0 && q1) ? __ldg(vb + tv.qs + tv.r0) : z;
     H.v[2] = (tv.r1 >= 0 && q0) ? __ldg(vb + tv.r1) : z;
     H.v[3] = (tv.r1 >= 0 && q1) ? __ldg(vb + tv.qs + tv.r1) : z;
-    if (tc.mrow >= 0) {
-        const float2* mp = cp2 + tc.mrow * npts + tv.p0 + q;
-        H.mu[0] = q0 ? __ldg(mp) : z;
-        H.mu[1] = q1 ? __ldg(mp + 1) : z;
-    } else if (GAUSS) {   // Gauss weight times the constant
-        const float2 c = make_float2(tc.shi, tc.slo);
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-            const float2 g = (pp ? q1 : q0) ? __ldg(gw2 + tv.p0 + q + pp) : z;
-            const float ph = g.x * c.x;
-            H.mu[pp] = make_float2(ph, fmaf(g.x, c.x, -ph) + fmaf(g.x, c.y, g.y * c.x));
-        }
-    } else {
-        H.mu[0] = H.mu[1] = make_float2(tc.shi, tc.slo);
-    }
 }
 
 template <int NT, bool GAUSS>
 __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
-    k_elem_tc(TcItems it, TcSrc src, TermsF tm) {
-    __shared__ TermC sTerm[TC_NWARP][NT];
-    __shared__ float sSg[TC_NWARP][NT][2][32];     // per (term, row, lane) slice scale
-    __shared__ int sSlot[TC_NWARP][8][32];         // destination slots per (entry, lane)
+    k_elem_tc(TcItems it, TcSrc src, const double* __restrict__ coef, TermsF tm) {
+    __shared__ __align__(16) float2 sMul[TC_NWARP][NT][TC_PMAX];   // per-term multipliers at the points
+    __shared__ int sTerm[TC_NWARP][NT][2];                          // test column, slice block
+    __shared__ float sSg[TC_NWARP][NT][2][32];                      // per (term, row, lane) slice scale
+    __shared__ int sSlot[TC_NWARP][8][32];                          // destination slots per (entry, lane)
+    __shared__ int sItem[TC_NWARP][2][12];                          // tile descriptors, double-buffered
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t k = (int64_t)blockIdx.x * TC_NWARP + wib;
+    const int64_t nw = (int64_t)gridDim.x * TC_NWARP;
+    int64_t k = (int64_t)blockIdx.x * TC_NWARP + wib;
     if (k >= it.n) return;
-    const int4 d = it.item[k];
-    const int4 d2 = it.it2[k];
-    const int kb = it.kb[k];
-    const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
-    const int hpt = d2.w >> 3, ncb = (m + 15) >> 4;
-    const int g = lane >> 2, t4 = lane & 3, ra = a0 + g;
-    const int nt = tm.nt, nc = src.nc, nv = GAUSS ? src.nc : src.nwc;
-    TermC* sT = sTerm[wib];
-    if (lane < nt) {
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-            if (t == lane) {
-                TermC c;
-                c.vc = GAUSS ? tm.sc[t] : tm.wc[t];
-                c.boff = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * 256;
-                c.mrow = tm.crow[t];
-                c.shi = tm.shi[t];
-                c.slo = tm.slo[t];
-                sT[t] = c;
-            }
-    }
-    // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1
-    // of both n-tiles), copied to shared memory in the background
-    {
-        const int32_t* sp = src.scat + kb + ra * m + b0 + 2 * t4;
-        const int bc = b0 + 2 * t4;
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const int dr = 8 * (x >> 2), dc = 8 * ((x >> 1) & 1) + (x & 1);
-            if (ra + dr < m && bc + dc < m) tc_cp_async4(&sSlot[wib][x][lane], sp + dr * m + dc);
-            else sSlot[wib][x][lane] = -1;
-        }
-    }
-    __syncwarp();
-    TileV tv;
-    tv.base = GAUSS ? src.vsrc + d.x : src.vsrc + (int64_t)d.w * nv;
-    tv.r0 = ra < m ? (GAUSS ? ra : ra * nv) : -1;
-    tv.r1 = ra + 8 < m ? (GAUSS ? ra + 8 : (ra + 8) * nv) : -1;
-    tv.qs = GAUSS ? nc * m : m * nv;
-    tv.cs = GAUSS ? m : 1;
-    tv.p0 = d.y;
-    tv.P = P;
-    const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 8;
-    // exponents and bounds (independent of the coefficients)
-    float vm[2][NT], fsc[NT];
-    int f8[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        f8[t] = t < nt ? __ldg(src.fexp + (int64_t)d2.z * nc + tm.tc[t]) + 8 : 0;
-        const int vc = GAUSS ? tm.sc[t] : tm.wc[t];
-        const float* vr = src.vmax + (int64_t)(d2.x + ra) * nv + vc;
-        vm[0][t] = (t < nt && ra < m) ? __ldg(vr) : 0.0f;
-        vm[1][t] = (t < nt && ra + 8 < m) ? __ldg(vr + 8 * nv) : 0.0f;
-    }
-    // the split coefficients and their per-element maxima come from the preceding kernel
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    const float* cm = src.cmx + (int64_t)d2.z * 5;
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const int c = tm.crow[t];
-        const float sabs = fabsf(tm.shi[t]) * (1.0f + 0x1p-22f);
-        fsc[t] = t >= nt ? 0.0f : (c >= 0 ? __ldg(cm + c) : (GAUSS ? __ldg(cm + 4) * sabs : sabs));
-    }
-    // row exponents 2^E > max_t vmax[row][v_t] cmax_t 2^f_t, the slice scales
-    // 2^(f_t + 8 - E) per (term, row) and the entries' scales 2^(E - 16)
-    float esc[2];
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        float bound = 0.0f;
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-            if (t < nt) bound = fmaxf(bound, vm[rr][t] * fsc[t] * exp2i(f8[t] - 8));
-        const int E = bound > 0.0f ? exp_above(bound * (1.0f + 0x1p-20f)) : 0;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) sSg[wib][t][rr][lane] = exp2i(f8[t] - E);
-        esc[rr] = exp2i(E - 16);
-    }
-
-    // slices of one half-chunk's test side into A fragments, then 10 MMAs
-    float acc[4][4];
-    auto step = [&](const Half& H, int t) {
-        uint32_t A[4][2];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const float sg = sSg[wib][t][rr][lane];
-            float ks[2][4];
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                const float2 v = H.v[rr * 2 + pp];
-                const float2 mu = H.mu[pp];
-                const float ph = v.x * mu.x;
-                const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
-                slice4(ph * sg, pl * sg, ks[pp]);
-            }
-#pragma unroll
-            for (int s = 0; s < 4; ++s) A[s][rr] = pack_int_bf16x2(ks[0][s], ks[1][s]);
-        }
-        const uint32_t bw[4] = {H.b.x, H.b.y, H.b.z, H.b.w};
-#pragma unroll
-        for (int ka = 0; ka < 4; ++ka)
-#pragma unroll
-            for (int lb = 0; lb < 4 - ka; ++lb) mma_k8(acc[ka + lb], A[ka][0], A[ka][1], bw[lb]);
+    // persistent warps: tiles k, k + nw, ...; the next tile's descriptors are copied in
+    // the background while this one is processed
+    auto fetch_item = [&](int64_t kk, int b) {
+        if (lane < 4) tc_cp_async4(&sItem[wib][b][lane], reinterpret_cast<const int*>(it.item + kk) + lane);
+        else if (lane < 8) tc_cp_async4(&sItem[wib][b][lane], reinterpret_cast<const int*>(it.it2 + kk) + lane - 4);
+        else if (lane == 8) tc_cp_async4(&sItem[wib][b][8], it.kb + kk);
     };
-    // write the level sums of n-tile n to the slots (adding to the earlier segments'
-    // values, which only this lane writes) and clear them
-    auto flush = [&](int n, bool first) {
+    fetch_item(k, 0);
+    for (int buf = 0; k < it.n; k += nw, buf ^= 1) {
         asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncwarp();
+        const int* si = sItem[wib][buf];
+        const int4 d = make_int4(si[0], si[1], si[2], si[3]);
+        const int4 d2 = make_int4(si[4], si[5], si[6], si[7]);
+        const int kb = si[8];
+        if (k + nw < it.n) fetch_item(k + nw, buf ^ 1);
+        const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
+        const int hpt = d2.w >> 3, ncb = (m + 15) >> 4;
+        const int g = lane >> 2, t4 = lane & 3, ra = a0 + g;
+        const int nt = tm.nt, nc = src.nc, nv = GAUSS ? src.nc : src.nwc;
+        int(*sT)[2] = sTerm[wib];
+        int f8[NT];   // f_t + 8 per term (uniform)
+        if (lane < nt) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int sl = sSlot[wib][(j >> 1) * 4 + n * 2 + (j & 1)][lane];
-            const float sc = esc[j >> 1];
-            const float hi = acc[0][j] * sc;
-            const float lo = ((acc[3][j] * 0x1p-8f + acc[2][j]) * 0x1p-8f + acc[1][j]) * (0x1p-8f * sc);
-            if (sl >= 0) {
-                if (!first) {
-                    const float2 o = src.kscr[sl];
-                    float s2, e2;
-                    tc_two_sum(o.x, hi, s2, e2);
-                    src.kscr[sl] = make_float2(s2, o.y + lo + e2);
-                } else {
-                    src.kscr[sl] = make_float2(hi, lo);
+            for (int t = 0; t < NT; ++t)
+                if (t == lane) {
+                    sT[t][0] = GAUSS ? tm.sc[t] : tm.wc[t];
+                    sT[t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * 256;
+                }
+        }
+        __syncwarp();
+        TileV tv;
+        tv.base = GAUSS ? src.vsrc + d.x : src.vsrc + (int64_t)d.w * nv;
+        tv.r0 = ra < m ? (GAUSS ? ra : ra * nv) : -1;
+        tv.r1 = ra + 8 < m ? (GAUSS ? ra + 8 : (ra + 8) * nv) : -1;
+        tv.qs = GAUSS ? nc * m : m * nv;
+        tv.cs = GAUSS ? m : 1;
+        const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 8;
+        // first half-chunk's operands in flight while the scales are set up
+        Half h0;
+        load_half(h0, tv, sT[0][0], sT[0][1], 0, P, t4, bsl);
+        // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1
+        // of both n-tiles), copied to shared memory in the background
+        {
+            const int32_t* sp = src.scat + kb + ra * m + b0 + 2 * t4;
+            const int bc = b0 + 2 * t4;
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int dr = 8 * (x >> 2), dc = 8 * ((x >> 1) & 1) + (x & 1);
+                if (ra + dr < m && bc + dc < m) tc_cp_async4(&sSlot[wib][x][lane], sp + dr * m + dc);
+                else sSlot[wib][x][lane] = -1;
+            }
+        }
+        float vm[2][NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            f8[t] = t < nt ? __ldg(src.fexp + (int64_t)d2.z * nc + tm.tc[t]) + 8 : 0;
+            const int vc = GAUSS ? tm.sc[t] : tm.wc[t];
+            const float* vr = src.vmax + (int64_t)(d2.x + ra) * nv + vc;
+            vm[0][t] = (t < nt && ra < m) ? __ldg(vr) : 0.0f;
+            vm[1][t] = (t < nt && ra + 8 < m) ? __ldg(vr + 8 * nv) : 0.0f;
+        }
+        // per-term multipliers (split pairs) at the element's points, zero up to P8
+        float2(*M)[TC_PMAX] = sMul[wib];
+        float cmax[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) cmax[t] = 0.0f;
+        for (int q = lane; q < 8 * hpt; q += 32) {
+            const bool in = q < P;
+            float2 cr[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                cr[r] = make_float2(0.0f, 0.0f);
+                if (r < tm.ncrow && in) {
+                    const double v = coef ? coef[r * tm.cstride + d.y + q] : 1.0;
+                    const float h = __double2float_rn(v);
+                    cr[r] = make_float2(h, __double2float_rn(v - (double)h));
                 }
             }
+            const float2 gq = GAUSS && in ? src.gw2[d.y + q] : make_float2(1.0f, 0.0f);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const int c = tm.crow[t];
+                float2 v = c == 0 ? cr[0] : (c == 1 ? cr[1] : (c == 2 ? cr[2] : (c == 3 ? cr[3] :
+                           make_float2(tm.shi[t], tm.slo[t]))));
+                if (GAUSS) {
+                    const float ph = v.x * gq.x;
+                    v = make_float2(ph, fmaf(v.x, gq.x, -ph) + fmaf(v.x, gq.y, v.y * gq.x));
+                }
+                if (!in) v = make_float2(0.0f, 0.0f);
+                M[t][q] = v;
+                cmax[t] = fmaxf(cmax[t], fabsf(v.x));
+            }
         }
-    };
+#pragma unroll
+        for (int t = 0; t < NT; ++t) cmax[t] = tc_warp_max(cmax[t]);
+        // row exponents 2^E > max_t vmax[row][v_t] cmax_t 2^f_t, the slice scales
+        // 2^(f_t + 8 - E) per (term, row) and the entries' scales 2^(E - 16)
+        float esc[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            float bound = 0.0f;
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+                if (t < nt) bound = fmaxf(bound, vm[rr][t] * cmax[t] * exp2i(f8[t] - 8));
+            const int E = bound > 0.0f ? exp_above(bound * (1.0f + 0x1p-20f)) : 0;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) sSg[wib][t][rr][lane] = exp2i(f8[t] - E);
+            esc[rr] = exp2i(E - 16);
+        }
+        __syncwarp();
 
-    // the two n-tiles one after the other (the second is empty for m <= b0 + 8); the
-    // half-chunks two per trip, the next one's operands in flight
-    const int nhalf = nt * hpt;
-    for (int n = 0; n < 2; ++n) {
-        if (b0 + 8 * n >= m) break;
+        float acc[4][2][4];
 #pragma unroll
         for (int l = 0; l < 4; ++l)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[l][j] = 0.0f;
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
+
+        // slices of one half-chunk's test side into A fragments, then the 20 MMAs
+        auto step = [&](const Half& H, int t, int hh) {
+            const int q = hh * 8 + 2 * t4;
+            const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
+            uint32_t A[4][2];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const float sg = sSg[wib][t][rr][lane];
+                float ks[2][4];
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                    const float2 v = H.v[rr * 2 + pp];
+                    const float2 mu = pp ? mu1 : mu0;
+                    const float ph = v.x * mu.x;
+                    const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
+                    slice4(ph * sg, pl * sg, ks[pp]);
+                }
+#pragma unroll
+                for (int s = 0; s < 4; ++s) A[s][rr] = pack_int_bf16x2(ks[0][s], ks[1][s]);
+            }
+            const uint32_t bw[8] = {H.b0.x, H.b0.y, H.b0.z, H.b0.w, H.b1.x, H.b1.y, H.b1.z, H.b1.w};
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+                for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+                    for (int lb = 0; lb < 4 - ka; ++lb) mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], bw[n * 4 + lb]);
+        };
+        // write the level sums of this segment to the slots (adding to the earlier
+        // segments' values, which only this lane writes) and clear them
+        auto flush = [&](bool first) {
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int sl = sSlot[wib][x][lane];
+                const int n = (x >> 1) & 1, j = (x >> 2) * 2 + (x & 1);
+                const float sc = esc[x >> 2];
+                const float hi = acc[0][n][j] * sc;
+                const float lo = ((acc[3][n][j] * 0x1p-8f + acc[2][n][j]) * 0x1p-8f + acc[1][n][j]) * (0x1p-8f * sc);
+                if (sl >= 0) {
+                    if (!first) {
+                        const float2 o = src.kscr[sl];
+                        float s2, e2;
+                        tc_two_sum(o.x, hi, s2, e2);
+                        src.kscr[sl] = make_float2(s2, o.y + lo + e2);
+                    } else {
+                        src.kscr[sl] = make_float2(hi, lo);
+                    }
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+#pragma unroll
+                for (int n = 0; n < 2; ++n)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
+        };
+
+        // walk the half-chunks two at a time, the next one's operands in flight
+        const int nhalf = nt * hpt;
         int t = 0, hh = 0, seg = 0;
         bool first = true;
-        Half h0, h1;
-        load_half<GAUSS>(h0, tv, sT[0], 0, n, t4, bsl, src.cp2, src.npts, src.gw2);
+        Half h1;
         for (int h = 0; h < nhalf; h += 2) {
             int t1 = t, hh1 = hh + 1;
             if (hh1 == hpt) hh1 = 0, ++t1;
-            if (h + 1 < nhalf) load_half<GAUSS>(h1, tv, sT[t1], hh1, n, t4, bsl, src.cp2, src.npts, src.gw2);
-            step(h0, t);
+            if (h + 1 < nhalf) load_half(h1, tv, sT[t1][0], sT[t1][1], hh1, P, t4, bsl);
+            step(h0, t, hh);
             int t2 = t1, hh2 = hh1 + 1;
             if (hh2 == hpt) hh2 = 0, ++t2;
-            if (h + 2 < nhalf) load_half<GAUSS>(h0, tv, sT[t2], hh2, n, t4, bsl, src.cp2, src.npts, src.gw2);
-            if (h + 1 < nhalf) step(h1, t1);
+            if (h + 2 < nhalf) load_half(h0, tv, sT[t2][0], sT[t2][1], hh2, P, t4, bsl);
+            if (h + 1 < nhalf) step(h1, t1, hh1);
             t = t2, hh = hh2;
             seg += 2;
             if (seg == 2 * TC_SEG && h + 2 < nhalf) {
-                flush(n, first);
-#pragma unroll
-                for (int l = 0; l < 4; ++l)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[l][j] = 0.0f;
+                flush(first);
                 first = false;
                 seg = 0;
             }
         }
-        flush(n, first);
-    }
-}
-
-// Split coefficients at the points (one warp per element): cp2[r][p] = (hi, lo) of
-// coefficient row r (times the Gauss weight for Gauss points), cmx[e][r] = the
-// element's largest |hi|; cmx[e][4] = the largest Gauss weight (Gauss points).
-__global__ void __launch_bounds__(256) k_tc_coef(int64_t E, const int64_t* __restrict__ pptr,
-                                                 const double* __restrict__ coef, int ncrow, int64_t cstride,
-                                                 const float2* __restrict__ gw2, float2* __restrict__ cp2,
-                                                 float* __restrict__ cmx, int64_t npts) {
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    const int lane = threadIdx.x & 31;
-    const int64_t e = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (e >= E) return;
-    const int64_t p0 = pptr[e];
-    const int P = (int)(pptr[e + 1] - p0);
-    for (int r = 0; r < ncrow; ++r) {
-        float mx = 0.0f;
-        for (int q = lane; q < P; q += 32) {
-            const double v = coef ? coef[r * cstride + p0 + q] : 1.0;
-            const float h = __double2float_rn(v);
-            float2 c = make_float2(h, __double2float_rn(v - (double)h));
-            if (gw2) {
-                const float2 gq = gw2[p0 + q];
-                const float ph = c.x * gq.x;
-                c = make_float2(ph, fmaf(c.x, gq.x, -ph) + fmaf(c.x, gq.y, c.y * gq.x));
-            }
-            cp2[r * npts + p0 + q] = c;
-            mx = fmaxf(mx, fabsf(c.x));
-        }
-        mx = tc_warp_max(mx);
-        if (lane == 0) cmx[e * 5 + r] = mx * (1.0f + 0x1p-22f);
-    }
-    if (gw2) {
-        float mx = 0.0f;
-        for (int q = lane; q < P; q += 32) mx = fmaxf(mx, fabsf(gw2[p0 + q].x));
-        mx = tc_warp_max(mx);
-        if (lane == 0) cmx[e * 5 + 4] = mx * (1.0f + 0x1p-22f);
+        flush(first);
+        __syncwarp();   // the per-warp shared arrays are rewritten by the next tile
     }
 }
 
@@ -389,28 +369,15 @@ cudaError_t launch_elem_tc(const TcItems& it, const TcSrc& src, const Terms& tm,
     if (src.nnz > 0 && it.n > 0) {
         const int ntk = tm.nt <= 4 ? tm.nt : 8;
         const TermsF tf = make_terms_f(tm, ntk);
-        if (tf.ncrow > 4) return cudaErrorInvalidValue;
-        k_tc_coef<<<(unsigned)((src.E + 7) / 8), 256, 0, st>>>(src.E, src.pptr, coef, tf.ncrow, tm.cstride,
-                                                                gauss ? src.gw2 : nullptr, src.cp2, src.cmx,
-                                                                src.npts);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)((it.n + TC_NWARP - 1) / TC_NWARP));
-        cfg.blockDim = dim3(TC_NWARP * 32);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        // persistent grid: the resident blocks
+        const unsigned eb = (unsigned)std::min<int64_t>((it.n + TC_NWARP - 1) / TC_NWARP,
+                                                        (int64_t)std::max(it.n_sm, 1) * TC_BLOCKS_PER_SM);
 #define WQ_TC_CASE(N)                                                                                    \
     do {                                                                                                 \
         if (gauss)                                                                                       \
-            e = cudaLaunchKernelEx(&cfg, k_elem_tc<N, true>, it, src, tf);                               \
+            k_elem_tc<N, true><<<eb, TC_NWARP * 32, 0, st>>>(it, src, coef, tf);                         \
         else                                                                                             \
-            e = cudaLaunchKernelEx(&cfg, k_elem_tc<N, false>, it, src, tf);                              \
+            k_elem_tc<N, false><<<eb, TC_NWARP * 32, 0, st>>>(it, src, coef, tf);                        \
     } while (0)
         switch (ntk) {
             case 1: WQ_TC_CASE(1); break;
@@ -420,6 +387,7 @@ cudaError_t launch_elem_tc(const TcItems& it, const TcSrc& src, const Terms& tm,
             default: WQ_TC_CASE(8); break;
         }
 #undef WQ_TC_CASE
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (evs) cudaEventRecord(evs[1], st);
         ElemSrc gs{};

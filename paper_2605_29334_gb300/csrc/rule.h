@@ -71,8 +71,6 @@ struct wq_rule {
     int32_t *d_fexp_wq = nullptr, *d_fexp_gq = nullptr;
     float *d_vmax_wq = nullptr, *d_vmax_gq = nullptr;
     float2* d_gw2 = nullptr;
-    float2 *d_cp2_wq = nullptr, *d_cp2_gq = nullptr;   // per call: split coefficients [4][points]
-    float *d_cmx_wq = nullptr, *d_cmx_gq = nullptr;    // per call: their per-element maxima [E][5]
     wqd::TcItems tit_wq{}, tit_gq{};
     wqd::TcSrc tc_wq{}, tc_gq{};
     std::vector<int4> h_it_wq;          // host copies of the WQ tiles (batched assembly)
