@@ -21,12 +21,13 @@
 //    accumulation of the MMA is exact (integers below 2^24);
 //  * K_e[a][b] = 2^(E_a - 16) sum_{d <= 3} 2^(-8 d) D_d, the pairs with k + l > 3
 //    dropped (below 2^-32 of the tile's product scale).
-// On the 10,240-element Poisson workload this gives ~1e-8 normwise against FP64 (the
-// level-3 cut and the final FP32 rounding), the compensated SIMT path's accuracy at a
-// fraction of its instructions: the SIMT work is per (row, point, term) -- split
-// product and 4 slices, ~25 instructions -- instead of per (row, column, point, term).
+// On the 10,240-element Poisson workload this gives 4e-8 normwise against FP64 (the
+// level-3 cut and the final FP32 rounding), the compensated SIMT path's accuracy; the
+// SIMT work is per (row, point, term) -- split product and 4 slices, ~20 instructions --
+// instead of per (row, column, point, term).
 //
-// One warp per 16 x 16 tile (the FP32 path's tiles and slot map).  The K range is
+// Persistent warps, one 16 x 16 tile at a time (the FP32 path's tiles and slot map; the
+// next tile's descriptors are prefetched).  The K range is
 // walked in half-chunks of 8 points of one term (each term's points padded to a
 // multiple of 8).  Lane (g, t4) = (lane / 4, lane % 4) builds the m16n8k8 A fragments
 // of its rows g, g + 8 at the points 2 t4, 2 t4 + 1, loads the trial fragments
