@@ -456,10 +456,10 @@ def assembly_work(rule, basis, n_terms):
     n_tiles = int(np.sum(((m + 15) // 16) ** 2))
     f32 = weights + tables + coef + int(np.sum(m * m)) * 4 + (rule.nnz + 1) * 4 + n_tiles * 20 + rule.nnz * 4
     # tensor-core element kernel: split weights (8 B per used value), trial slices (per tile,
-    # term and 8 points: 32 lanes x 32 B), coefficients, slot map, tile descriptors
-    # (2 x int4 + kb) and the slot writes (float pairs)
+    # term and 8 points: 5 slices x 32 lanes x 8 B), coefficients, slot map, tile
+    # descriptors (2 x int4 + kb) and the slot writes (float pairs)
     P8 = (P + 7) // 8 * 8
-    tc_elem = (weights + int(np.sum(((m + 15) // 16) ** 2 * P8)) * n_terms * 128 + coef
+    tc_elem = (weights + int(np.sum(((m + 15) // 16) ** 2 * P8)) * n_terms * 160 + coef
                + int(np.sum(m * m)) * 4 + n_tiles * 36 + int(np.sum(m * m)) * 8)
     return {"products": products, "hbm_bytes_f64": int(f64), "hbm_bytes_f32": int(f32),
             "tc_elem_bytes": int(tc_elem)}

@@ -65,10 +65,10 @@ typedef enum {
     WQ_PREC_F32_FAST = 2, /* FP32 split products, plain FP32 sums (operators with <= 2 terms); float
                              values; its error depends on the cancellation in the rows -- measure it */
     WQ_PREC_TC = 3        /* element blocks on the tensor cores: both operands scaled per row /
-                             element and split into four 8-bit bf16 slices, slice pairs up to level 3
+                             element and split into five 8-bit bf16 slices, slice pairs up to level 4
                              summed exactly in FP32 (integers below 2^24; error-free transformation
                              of Ozaki et al.), per-entry sums as WQ_PREC_F32; float values, error
-                             ~2^-32 of each tile's product scale; needs <= 64 points per element */
+                             ~2^-40 of each tile's largest |s| |T| K; needs <= 64 points per element */
 } wq_prec;
 
 /* Point-count rule (Sec. 4.2). */

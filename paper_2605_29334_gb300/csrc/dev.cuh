@@ -90,10 +90,10 @@ struct ElemSrc64 {
 // of the element in the per-function arrays, offset of the element's trial-side slices
 // in bs (words), element, P rounded up to 8}.  The trial side of element e (table
 // component c, column block cb of 16 functions, half-chunk hh of 8 points) is stored
-// in mma fragment order: 32 lanes x 8 words, word nt * 4 + l of lane (g, t4) holding
-// slice l of T[q][n] for q = 8 hh + 2 t4 (low half) and q + 1 (high half), column
-// n = 16 cb + 8 nt + g, as bf16 integers of T 2^(8 - f_ec) (f_ec = fexp[e nc + c],
-// 2^f_ec >= max |T| over the element).  vmax[(fn + a) nv + v] bounds the test-side
+// in mma fragment order: per slice l, 32 lanes x 2 words, word nt of lane (g, t4)
+// holding slice l of T[q][n] for q = 8 hh + 2 t4 (low half) and q + 1 (high half),
+// column n = 16 cb + 8 nt + g, as bf16 integers of T 2^(8 - f_ec) (f_ec = fexp[e nc + c],
+// 2^f_ec > max |T| over the element).  vmax[(fn + a) nv + v] bounds the test-side
 // values of local function a over the element's points (v: weight column, or
 // table component for Gauss items).
 struct TcItems {

@@ -8,34 +8,35 @@
 // error-free splitting of the operands (the idea of Ozaki, Ogita, Oishi and Rump,
 // "Error-free transformations of matrix multiplication by using fast routines of
 // matrix multiplication and its applications", Numer. Algorithms 59, 2012):
-//  * the trial side of element e, component c, is scaled by 2^(8 - f), 2^f >= max|T|
-//    over the element, and rounded into 4 slices of 8 bits, T 2^(8-f) =
+//  * the trial side of element e, component c, is scaled by 2^(8 - f), 2^f > max|T|
+//    over the element, and rounded into 5 slices of 8 bits, T 2^(8-f) =
 //    sum_l b_l 2^(-8 l) with integers |b_0| <= 256, |b_l| <= 128 (exact bf16), to
-//    2^-25 of 256 (set-up, from the FP64 table);
-//  * the test side of row a is scaled by 2^(f_t + 8 - E_a), 2^E_a >= max_{t,q} |s^t_aq|
+//    2^-33 of 256 (set-up, from the FP64 table);
+//  * the test side of row a is scaled by 2^(f_t + 8 - E_a), 2^E_a > max_{t,q} |s^t_aq|
 //    2^(f_t) (the bound from per-function maxima of the weights and the largest
 //    coefficient of the element), and sliced the same way at run time from the split
 //    (hi, lo) products;
 //  * every product a_k b_l of bf16 integers is exact, and a level sum
-//    D_d = sum_{k + l = d} sum_K a_k b_l has |D_d| < 2^24 for K <= 160, so the FP32
-//    accumulation of the MMA is exact (integers below 2^24);
-//  * K_e[a][b] = 2^(E_a - 16) sum_{d <= 3} 2^(-8 d) D_d, the pairs with k + l > 3
-//    dropped (below 2^-32 of the tile's product scale).
-// On the 10,240-element Poisson workload this gives 4e-8 normwise against FP64 (the
-// level-3 cut and the final FP32 rounding), the compensated SIMT path's accuracy; the
-// SIMT work is per (row, point, term) -- split product and 4 slices, ~20 instructions --
-// instead of per (row, column, point, term).
+//    D_d = sum_{k + l = d} sum_K a_k b_l has |D_d| <= 114,816 K < 2^24 for K <= 128, so
+//    the FP32 accumulation of the MMA adds integers exactly;
+//  * K_e[a][b] = 2^(E_a - 16) sum_{d <= 4} 2^(-8 d) D_d, the pairs with k + l > 4
+//    dropped (below 2^-40 of the tile's product scale).
+// The error is relative to the tile's largest |s| |T| K, not to each entry: the weights
+// of ill-conditioned rows span several decades with cancelling signs, and with four
+// slices (2^-32) the 24,576-element sphere bilaplacian reached 1e-5 normwise; five
+// slices put that case below the FP32 rounding of the values.  The SIMT work is per
+// (row, point, term) -- split product and 5 slices, ~24 instructions -- instead of per
+// (row, column, point, term).
 //
 // Persistent warps, one 16 x 16 tile at a time (the FP32 path's tiles and slot map; the
-// next tile's descriptors are prefetched).  The K range is
-// walked in half-chunks of 8 points of one term (each term's points padded to a
-// multiple of 8).  Lane (g, t4) = (lane / 4, lane % 4) builds the m16n8k8 A fragments
-// of its rows g, g + 8 at the points 2 t4, 2 t4 + 1, loads the trial fragments
-// precomputed in that order (two 16-byte loads), and runs 10 slice pairs x 2 n-tiles
-// of mma.sync into 4 level accumulators; the next half-chunk's loads are in flight
-// meanwhile.  Slicing uses FMA-pipe rounding (add and subtract 1.5 2^23) and a byte
-// permute for the bf16 packing.  Every 20 half-chunks (K = 160) the levels are added
-// to the tile's slots (a TwoSum against the earlier segments), so any K is exact.
+// next tile's descriptors are prefetched).  The K range is walked in half-chunks of 8
+// points of one term (each term's points padded to a multiple of 8).  Lane (g, t4) =
+// (lane / 4, lane % 4) builds the m16n8k8 A fragments of its rows g, g + 8 at the points
+// 2 t4, 2 t4 + 1, loads the trial fragments precomputed in that order (one 8-byte load
+// per slice), and runs 15 slice pairs x 2 n-tiles of mma.sync into 5 level
+// accumulators; the next half-chunk's loads are in flight meanwhile.  Every 16
+// half-chunks (K = 128) the levels are added to the tile's slots (a TwoSum against the
+// earlier segments), so any K is exact.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -46,7 +47,9 @@ namespace wqd {
 
 constexpr int TC_NWARP = 4;     // warps per block
 constexpr int TC_PMAX = 64;     // points per element (WQ side^2, Gauss 16 nsub)
-constexpr int TC_SEG = 10;      // chunks per exact segment: K <= 160
+constexpr int TC_NS = WQ_TC_SLICES;        // slices per operand
+constexpr int TC_HW = WQ_TC_HALF_WORDS;    // trial-slice words per (half-chunk, column block)
+constexpr int TC_SEGH = 16;                // half-chunks per exact segment: K <= 128
 constexpr int TC_BLOCKS_PER_SM = 4;   // resident blocks at the register budget (no spills)
 
 __device__ __forceinline__ float tc_warp_max(float v) {
@@ -72,21 +75,23 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Four 8-bit slices of y = yh + yl (|y| <= 256, |yl| <= ulp(yh) / 2): integers k_s with
-// y = k0 + 2^-8 k1 + 2^-16 k2 + 2^-24 k3 to 2^-25.  Rounding to an integer adds and
-// subtracts 1.5 2^23 (FMA pipe; rintf runs on the slower conversion pipe).  Every
-// remainder yh - k0, r 2^8 - k1, t - k2 is exact; yl enters at the third slice
-// (|k2| <= 129), so 14 FP32 instructions.
-__device__ __forceinline__ void slice4(float yh, float yl, float (&k)[4]) {
+// Five 8-bit slices of y = yh + yl (|y| <= 256, |yl| <= ulp(yh) / 2): integers k_s with
+// y = k0 + 2^-8 k1 + ... + 2^-32 k4 to 2^-33.  Rounding to an integer adds and subtracts
+// 1.5 2^23 (FMA pipe; rintf runs on the slower conversion pipe).  The remainders
+// yh - k0 and r 2^8 - k1 are exact; yl enters at the third slice (|k2| <= 129) and the
+// remainder after it, (t - k2) + yl, is kept to 2^-24 of itself, far below k4's unit.
+__device__ __forceinline__ void slice5(float yh, float yl, float (&k)[TC_NS]) {
     const float M = 12582912.0f;
     k[0] = __fsub_rn(__fadd_rn(yh, M), M);
     float r = yh - k[0];
     k[1] = __fsub_rn(__fmaf_rn(r, 256.0f, M), M);
     r = __fmaf_rn(r, 256.0f, -k[1]);
-    const float t = __fmaf_rn(r, 256.0f, yl * 65536.0f);
-    k[2] = __fsub_rn(__fadd_rn(t, M), M);
-    r = t - k[2];
+    const float t = r * 256.0f, yl2 = yl * 65536.0f;
+    k[2] = __fsub_rn(__fadd_rn(t + yl2, M), M);
+    r = (t - k[2]) + yl2;
     k[3] = __fsub_rn(__fmaf_rn(r, 256.0f, M), M);
+    r = __fmaf_rn(r, 256.0f, -k[3]);
+    k[4] = __fsub_rn(__fmaf_rn(r, 256.0f, M), M);
 }
 
 // Two integers |k| <= 256 as a bf16x2 word (low = first): their FP32 encodings have
@@ -120,7 +125,7 @@ __device__ __forceinline__ void tc_cp_async4(void* smem, const void* gmem) {
 
 struct Half {
     float2 v[4];     // [row][point]
-    uint4 b0, b1;    // n-tile 0 slices 0..3, n-tile 1 slices 0..3
+    uint2 b[TC_NS];  // per slice: the words of n-tiles 0 and 1
 };
 
 // Per-tile constants of the test-side loads: element base, row strides, validity.
@@ -132,9 +137,9 @@ struct TileV {
 
 __device__ __forceinline__ void load_half(Half& H, const TileV& tv, int vc, int boff, int hh, int P, int t4,
                                           const uint32_t* __restrict__ bsl) {
-    const uint4* bp = reinterpret_cast<const uint4*>(bsl + boff + hh * 256);
-    H.b0 = __ldg(bp);
-    H.b1 = __ldg(bp + 1);
+    const uint32_t* bp = bsl + boff + hh * TC_HW;
+#pragma unroll
+    for (int l = 0; l < TC_NS; ++l) H.b[l] = __ldg(reinterpret_cast<const uint2*>(bp + l * 64));
     const int q = hh * 8 + 2 * t4;
     const float2* vb = tv.base + q * tv.qs + vc * tv.cs;
     const bool q0 = q < P, q1 = q + 1 < P;
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
             for (int t = 0; t < NT; ++t)
                 if (t == lane) {
                     sT[t][0] = GAUSS ? tm.sc[t] : tm.wc[t];
-                    sT[t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * 256;
+                    sT[t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * TC_HW;
                 }
         }
         __syncwarp();
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         tv.r1 = ra + 8 < m ? (GAUSS ? ra + 8 : (ra + 8) * nv) : -1;
         tv.qs = GAUSS ? nc * m : m * nv;
         tv.cs = GAUSS ? m : 1;
-        const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 8;
+        const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 2;
         // first half-chunk's operands in flight while the scales are set up
         Half h0;
         load_half(h0, tv, sT[0][0], sT[0][1], 0, P, t4, bsl);
@@ -270,9 +275,9 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         }
         __syncwarp();
 
-        float acc[4][2][4];
+        float acc[TC_NS][2][4];
 #pragma unroll
-        for (int l = 0; l < 4; ++l)
+        for (int l = 0; l < TC_NS; ++l)
 #pragma unroll
             for (int n = 0; n < 2; ++n)
 #pragma unroll
@@ -282,29 +287,29 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         auto step = [&](const Half& H, int t, int hh) {
             const int q = hh * 8 + 2 * t4;
             const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
-            uint32_t A[4][2];
+            uint32_t A[TC_NS][2];
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
                 const float sg = sSg[wib][t][rr][lane];
-                float ks[2][4];
+                float ks[2][TC_NS];
 #pragma unroll
                 for (int pp = 0; pp < 2; ++pp) {
                     const float2 v = H.v[rr * 2 + pp];
                     const float2 mu = pp ? mu1 : mu0;
                     const float ph = v.x * mu.x;
                     const float pl = fmaf(v.x, mu.x, -ph) + fmaf(v.x, mu.y, v.y * mu.x);
-                    slice4(ph * sg, pl * sg, ks[pp]);
+                    slice5(ph * sg, pl * sg, ks[pp]);
                 }
 #pragma unroll
-                for (int s = 0; s < 4; ++s) A[s][rr] = pack_int_bf16x2(ks[0][s], ks[1][s]);
+                for (int s = 0; s < TC_NS; ++s) A[s][rr] = pack_int_bf16x2(ks[0][s], ks[1][s]);
             }
-            const uint32_t bw[8] = {H.b0.x, H.b0.y, H.b0.z, H.b0.w, H.b1.x, H.b1.y, H.b1.z, H.b1.w};
 #pragma unroll
             for (int n = 0; n < 2; ++n)
 #pragma unroll
-                for (int ka = 0; ka < 4; ++ka)
+                for (int ka = 0; ka < TC_NS; ++ka)
 #pragma unroll
-                    for (int lb = 0; lb < 4 - ka; ++lb) mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], bw[n * 4 + lb]);
+                    for (int lb = 0; lb < TC_NS - ka; ++lb)
+                        mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], n ? H.b[lb].y : H.b[lb].x);
         };
         // write the level sums of this segment to the slots (adding to the earlier
         // segments' values, which only this lane writes) and clear them
@@ -316,7 +321,10 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
                 const int n = (x >> 1) & 1, j = (x >> 2) * 2 + (x & 1);
                 const float sc = esc[x >> 2];
                 const float hi = acc[0][n][j] * sc;
-                const float lo = ((acc[3][n][j] * 0x1p-8f + acc[2][n][j]) * 0x1p-8f + acc[1][n][j]) * (0x1p-8f * sc);
+                float lo = acc[TC_NS - 1][n][j];
+#pragma unroll
+                for (int l = TC_NS - 2; l >= 1; --l) lo = lo * 0x1p-8f + acc[l][n][j];
+                lo *= 0x1p-8f * sc;
                 if (sl >= 0) {
                     if (!first) {
                         const float2 o = src.kscr[sl];
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
                 }
             }
 #pragma unroll
-            for (int l = 0; l < 4; ++l)
+            for (int l = 0; l < TC_NS; ++l)
 #pragma unroll
                 for (int n = 0; n < 2; ++n)
 #pragma unroll
@@ -352,7 +360,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
             if (h + 1 < nhalf) step(h1, t1, hh1);
             t = t2, hh = hh2;
             seg += 2;
-            if (seg == 2 * TC_SEG && h + 2 < nhalf) {
+            if (seg == TC_SEGH && h + 2 < nhalf) {
                 flush(first);
                 first = false;
                 seg = 0;
@@ -452,28 +460,27 @@ __global__ void __launch_bounds__(128) k_tc_prep(int nc, int nwc, const int32_t*
         r /= hpt;
         const int cb = r % ncb, c = r / ncb;
         const int g = ln >> 2, t4 = ln & 3;
-        uint32_t wd[8];
+        float kk[2][2][TC_NS];   // [n-tile][point][slice]
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
             const int b = cb * 16 + n * 8 + g;
-            float kk[2][4];
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp) {
                 const int q = hh * 8 + 2 * t4 + pp;
                 double y = (q < P && b < m) ? ldexp(tb[((int64_t)q * nc + c) * m + b], 8 - sf[c]) : 0.0;
 #pragma unroll
-                for (int l = 0; l < 4; ++l) {
+                for (int l = 0; l < TC_NS; ++l) {
                     const double v = rint(y);
-                    kk[pp][l] = (float)v;
+                    kk[n][pp][l] = (float)v;
                     y = (y - v) * 256.0;
                 }
             }
-#pragma unroll
-            for (int l = 0; l < 4; ++l) wd[n * 4 + l] = pack_bf16x2(kk[0][l], kk[1][l]);
         }
-        uint4* o4 = reinterpret_cast<uint4*>(out + ((int64_t)(c * ncb + cb) * hpt + hh) * 256 + ln * 8);
-        o4[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-        o4[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        uint32_t* o = out + ((int64_t)(c * ncb + cb) * hpt + hh) * TC_HW + ln * 2;
+#pragma unroll
+        for (int l = 0; l < TC_NS; ++l)
+            *reinterpret_cast<uint2*>(o + l * 64) =
+                make_uint2(pack_bf16x2(kk[0][0][l], kk[0][1][l]), pack_bf16x2(kk[1][0][l], kk[1][1][l]));
     }
     // test-side bounds per (function, column)
     const int nv = We ? nwc : nc;
