@@ -320,11 +320,16 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
                 const int sl = sSlot[wib][x][lane];
                 const int n = (x >> 1) & 1, j = (x >> 2) * 2 + (x & 1);
                 const float sc = esc[x >> 2];
-                const float hi = acc[0][n][j] * sc;
-                float lo = acc[TC_NS - 1][n][j];
+                // D0 and 2^-8 D1 are exact floats (integers below 2^24); their TwoSum plus
+                // the lower levels (rounded at 2^-24 of a 2^-16 part) keep the pair to
+                // ~2^-40 of the tile scale
+                float rest = acc[TC_NS - 1][n][j];
 #pragma unroll
-                for (int l = TC_NS - 2; l >= 1; --l) lo = lo * 0x1p-8f + acc[l][n][j];
-                lo *= 0x1p-8f * sc;
+                for (int l = TC_NS - 2; l >= 2; --l) rest = rest * 0x1p-8f + acc[l][n][j];
+                float hs, he;
+                tc_two_sum(acc[0][n][j], acc[1][n][j] * 0x1p-8f, hs, he);
+                const float hi = hs * sc;
+                const float lo = (he + rest * 0x1p-16f) * sc;
                 if (sl >= 0) {
                     if (!first) {
                         const float2 o = src.kscr[sl];
