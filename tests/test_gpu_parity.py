@@ -225,7 +225,7 @@ def test_assemble_host_roundtrip(case, W):
     torch.cuda.synchronize()
     host = r.assemble_host(1, kap)
     assert np.array_equal(dev, host)
-    # page-locked output: written directly by the per-entry sums
+    # page-locked output buffers, both precisions
     for prec, dt in ((W.PREC_F32, torch.float32), (W.PREC_F64, torch.float64)):
         pinned = torch.full((r.nnz,), float("nan"), dtype=dt).pin_memory()
         r.assemble_host(1, kap, prec=prec, out=pinned.numpy())
