@@ -116,13 +116,13 @@ __device__ __forceinline__ int exp_above(float x) {
     return ex;
 }
 
-// Operands of one half-chunk (8 points of one term): this lane's test-side values
-// (rows g, g + 8 at points 2 t4, 2 t4 + 1) and its trial-side fragment words.
 __device__ __forceinline__ void tc_cp_async4(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
 
+// Operands of one half-chunk (8 points of one term): this lane's test-side values
+// (rows g, g + 8 at points 2 t4, 2 t4 + 1) and its trial-side fragment words.
 struct Half {
     float2 v[4];     // [row][point]
     uint2 b[TC_NS];  // per slice: the words of n-tiles 0 and 1
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
     __shared__ float sSg[TC_NWARP][NT][2][32];                      // per (term, row, lane) slice scale
     __shared__ int sSlot[TC_NWARP][8][32];                          // destination slots per (entry, lane)
     __shared__ int sItem[TC_NWARP][2][12];                          // tile descriptors, double-buffered
+    __shared__ __align__(16) float2 sCr[TC_NWARP][4][TC_PMAX];      // split coefficient rows at the points
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * TC_NWARP;
@@ -230,24 +231,28 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         float cmax[NT];
 #pragma unroll
         for (int t = 0; t < NT; ++t) cmax[t] = 0.0f;
-        for (int q = lane; q < 8 * hpt; q += 32) {
-            const bool in = q < P;
-            float2 cr[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                cr[r] = make_float2(0.0f, 0.0f);
-                if (r < tm.ncrow && in) {
+        // the coefficient rows split once per point (a runtime loop over the rows used:
+        // the FP64 conversions are on the slow FP64 pipe)
+        float2(*CR)[TC_PMAX] = sCr[wib];
+#pragma unroll 1
+        for (int r = 0; r < tm.ncrow; ++r)
+            for (int q = lane; q < 8 * hpt; q += 32) {
+                float2 c = make_float2(0.0f, 0.0f);
+                if (q < P) {
                     const double v = coef ? coef[r * tm.cstride + d.y + q] : 1.0;
                     const float h = __double2float_rn(v);
-                    cr[r] = make_float2(h, __double2float_rn(v - (double)h));
+                    c = make_float2(h, __double2float_rn(v - (double)h));
                 }
+                CR[r][q] = c;
             }
+        __syncwarp();
+        for (int q = lane; q < 8 * hpt; q += 32) {
+            const bool in = q < P;
             const float2 gq = GAUSS && in ? src.gw2[d.y + q] : make_float2(1.0f, 0.0f);
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 const int c = tm.crow[t];
-                float2 v = c == 0 ? cr[0] : (c == 1 ? cr[1] : (c == 2 ? cr[2] : (c == 3 ? cr[3] :
-                           make_float2(tm.shi[t], tm.slo[t]))));
+                float2 v = c >= 0 ? CR[c][q] : make_float2(tm.shi[t], tm.slo[t]);
                 if (GAUSS) {
                     const float ph = v.x * gq.x;
                     v = make_float2(ph, fmaf(v.x, gq.x, -ph) + fmaf(v.x, gq.y, v.y * gq.x));
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
 
-        // slices of one half-chunk's test side into A fragments, then the 20 MMAs
+        // slices of one half-chunk's test side into A fragments, then the 30 MMAs
         auto step = [&](const Half& H, int t, int hh) {
             const int q = hh * 8 + 2 * t4;
             const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
