@@ -430,8 +430,8 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     make_items(true, it_gq, kb_gq, ie_gq);
     // tensor-core contraction: per element {table offset, points, weight row, first
     // function} and the offsets of its trial-side slices (nc components x column
-    // blocks x half-chunks x WQ_TC_HALF_WORDS words); per tile {first function, slice
-    // offset, element, points rounded up to 8}
+    // blocks x quarter-chunks x WQ_TC_QUARTER_WORDS words); per tile {first function,
+    // slice offset, element, points rounded up to 4}
     std::vector<int4> tcel_wq(E), tcel_gq(E), it2_wq(it_wq.size()), it2_gq(it_gq.size());
     std::vector<int64_t> bsp_wq(E + 1, 0), bsp_gq(E + 1, 0);
     R->tc_ok = true;
@@ -440,17 +440,17 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         if (pw > 64 || pg > 64) R->tc_ok = false;
         tcel_wq[e] = make_int4((int)bt_ptr[e], pw, (int)wbase[e], (int)B.fn_ptr[e]);
         tcel_gq[e] = make_int4((int)gbt_ptr[e], pg, (int)wbase[e], (int)B.fn_ptr[e]);
-        bsp_wq[e + 1] = bsp_wq[e] + (int64_t)nc * ncb * ((pw + 7) / 8) * wqd::WQ_TC_HALF_WORDS;
-        bsp_gq[e + 1] = bsp_gq[e] + (int64_t)nc * ncb * ((pg + 7) / 8) * wqd::WQ_TC_HALF_WORDS;
+        bsp_wq[e + 1] = bsp_wq[e] + (int64_t)nc * ncb * ((pw + 3) / 4) * wqd::WQ_TC_QUARTER_WORDS;
+        bsp_gq[e + 1] = bsp_gq[e] + (int64_t)nc * ncb * ((pg + 3) / 4) * wqd::WQ_TC_QUARTER_WORDS;
     }
     if (bsp_wq[E] > INT32_MAX || bsp_gq[E] > INT32_MAX || B.fn_ptr[E] > INT32_MAX) R->tc_ok = false;
     for (size_t x = 0; x < it_wq.size(); ++x) {
         const int32_t e = ie_wq[x];
-        it2_wq[x] = make_int4((int)B.fn_ptr[e], (int)bsp_wq[e], e, (side[e] * side[e] + 7) / 8 * 8);
+        it2_wq[x] = make_int4((int)B.fn_ptr[e], (int)bsp_wq[e], e, (side[e] * side[e] + 3) / 4 * 4);
     }
     for (size_t x = 0; x < it_gq.size(); ++x) {
         const int32_t e = ie_gq[x];
-        it2_gq[x] = make_int4((int)B.fn_ptr[e], (int)bsp_gq[e], e, (16 * nsub[e] + 7) / 8 * 8);
+        it2_gq[x] = make_int4((int)B.fn_ptr[e], (int)bsp_gq[e], e, (16 * nsub[e] + 3) / 4 * 4);
     }
     R->bs_words_wq = bsp_wq[E];
     R->bs_words_gq = bsp_gq[E];

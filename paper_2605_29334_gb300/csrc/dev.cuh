@@ -88,12 +88,13 @@ struct ElemSrc64 {
 
 // Tensor-core element contraction (WQ_PREC_TC).  Per tile, it2[k] = {first function
 // of the element in the per-function arrays, offset of the element's trial-side slices
-// in bs (words), element, P rounded up to 8}.  The trial side of element e (table
-// component c, column block cb of 16 functions, half-chunk hh of 8 points) is stored
-// in mma fragment order: per slice l, 32 lanes x 2 words, word nt of lane (g, t4)
-// holding slice l of T[q][n] for q = 8 hh + 2 t4 (low half) and q + 1 (high half),
-// column n = 16 cb + 8 nt + g, as bf16 integers of T 2^(8 - f_ec) (f_ec = fexp[e nc + c],
-// 2^f_ec > max |T| over the element).  vmax[(fn + a) nv + v] bounds the test-side
+// in bs (words), element, P rounded up to 4}.  The trial side of element e (table
+// component c, column block cb of 16 functions, quarter-chunk qq of 4 points) is stored
+// in mma fragment order: per slice l, 2 x 8 x 2 words, word (p, g, nt) holding slice l
+// of T[q][n] for q = 4 qq + 2 p (low half) and q + 1 (high half), column
+// n = 16 cb + 8 nt + g, as bf16 integers of T 2^(8 - f_ec) (f_ec = fexp[e nc + c],
+// 2^f_ec > max |T| over the element); lane (g, t4) of a half-chunk reads p = t4 % 2 of
+// the quarter its t4 / 2 selects.  vmax[(fn + a) nv + v] bounds the test-side
 // values of local function a over the element's points (v: weight column, or
 // table component for Gauss items).
 struct TcItems {

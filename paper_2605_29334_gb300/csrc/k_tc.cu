@@ -48,7 +48,7 @@ namespace wqd {
 constexpr int TC_NWARP = 4;     // warps per block
 constexpr int TC_PMAX = 64;     // points per element (WQ side^2, Gauss 16 nsub)
 constexpr int TC_NS = WQ_TC_SLICES;        // slices per operand
-constexpr int TC_HW = WQ_TC_HALF_WORDS;    // trial-slice words per (half-chunk, column block)
+constexpr int TC_QW = WQ_TC_QUARTER_WORDS; // trial-slice words per (quarter-chunk, column block)
 constexpr int TC_SEGH = 16;                // half-chunks per exact segment: K <= 128
 constexpr int TC_BLOCKS_PER_SM = 4;   // resident blocks at the register budget (no spills)
 
@@ -126,6 +126,7 @@ __device__ __forceinline__ void tc_cp_async4(void* smem, const void* gmem) {
 struct Half {
     float2 v[4];     // [row][point]
     uint2 b[TC_NS];  // per slice: the words of n-tiles 0 and 1
+    int t, q;        // this lane's term and first point (t < 0: beyond the last quarter)
 };
 
 // Per-tile constants of the test-side loads: element base, row strides, validity.
@@ -135,15 +136,26 @@ struct TileV {
     int qs, cs;          // stride of a point, of a column / component
 };
 
-__device__ __forceinline__ void load_half(Half& H, const TileV& tv, int vc, int boff, int hh, int P, int t4,
-                                          const uint32_t* __restrict__ bsl) {
-    const uint32_t* bp = bsl + boff + hh * TC_HW;
-#pragma unroll
-    for (int l = 0; l < TC_NS; ++l) H.b[l] = __ldg(reinterpret_cast<const uint2*>(bp + l * 64));
-    const int q = hh * 8 + 2 * t4;
-    const float2* vb = tv.base + q * tv.qs + vc * tv.cs;
-    const bool q0 = q < P, q1 = q + 1 < P;
+// This lane's quarter-chunk (term t, quarter qq) of a half-chunk: its trial fragment
+// words and test-side values.
+__device__ __forceinline__ void load_half(Half& H, const TileV& tv, const int (*sT)[2], int t, int qq, int P,
+                                          int t4, const uint32_t* __restrict__ bsl) {
+    H.t = t;
+    H.q = 4 * qq + 2 * (t4 & 1);
     const float2 z = make_float2(0.0f, 0.0f);
+    if (t < 0) {
+#pragma unroll
+        for (int l = 0; l < TC_NS; ++l) H.b[l] = make_uint2(0u, 0u);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) H.v[x] = z;
+        return;
+    }
+    const uint32_t* bp = bsl + sT[t][1] + qq * TC_QW;
+#pragma unroll
+    for (int l = 0; l < TC_NS; ++l) H.b[l] = __ldg(reinterpret_cast<const uint2*>(bp + l * 32));
+    const int q = H.q;
+    const float2* vb = tv.base + q * tv.qs + sT[t][0] * tv.cs;
+    const bool q0 = q < P, q1 = q + 1 < P;
     H.v[0] = (tv.r0 >= 0 && q0) ? __ldg(vb + tv.r0) : z;
     H.v[1] = (tv.r0 >= 0 && q1) ? __ldg(vb + tv.qs + tv.r0) : z;
     H.v[2] = (tv.r1 >= 0 && q0) ? __ldg(vb + tv.r1) : z;
@@ -181,7 +193,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         const int kb = si[8];
         if (k + nw < it.n) fetch_item(k + nw, buf ^ 1);
         const int m = d.z & 255, P = (d.z >> 8) & 255, a0 = ((d.z >> 16) & 15) * 16, b0 = ((d.z >> 20) & 15) * 16;
-        const int hpt = d2.w >> 3, ncb = (m + 15) >> 4;
+        const int qpt = d2.w >> 2, ncb = (m + 15) >> 4;   // quarter-chunks per term
         const int g = lane >> 2, t4 = lane & 3, ra = a0 + g;
         const int nt = tm.nt, nc = src.nc, nv = GAUSS ? src.nc : src.nwc;
         int(*sT)[2] = sTerm[wib];
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
             for (int t = 0; t < NT; ++t)
                 if (t == lane) {
                     sT[t][0] = GAUSS ? tm.sc[t] : tm.wc[t];
-                    sT[t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * hpt * TC_HW;
+                    sT[t][1] = (tm.tc[t] * ncb + (b0 >> 4)) * qpt * TC_QW;
                 }
         }
         __syncwarp();
@@ -201,10 +213,19 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         tv.r1 = ra + 8 < m ? (GAUSS ? ra + 8 : (ra + 8) * nv) : -1;
         tv.qs = GAUSS ? nc * m : m * nv;
         tv.cs = GAUSS ? m : 1;
-        const uint32_t* __restrict__ bsl = src.bs + d2.y + lane * 2;
+        const uint32_t* __restrict__ bsl = src.bs + d2.y + ((t4 & 1) * 8 + g) * 2;
+        // quarter-chunks: lanes t4 < 2 take the even quarter of a half-chunk, t4 >= 2 the
+        // odd one; (tq, qq) = this lane's quarter, advanced by two per half-chunk
+        const int nq = nt * qpt;
+        int tq = 0, qq = t4 >> 1;
+        auto advance = [&]() {
+            qq += 2;
+            while (qq >= qpt && tq < nt) qq -= qpt, ++tq;
+        };
+        if (qq >= qpt) qq -= qpt, ++tq;
         // first half-chunk's operands in flight while the scales are set up
         Half h0;
-        load_half(h0, tv, sT[0][0], sT[0][1], 0, P, t4, bsl);
+        load_half(h0, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
         // destination slots of this lane's 8 entries (rows g, g + 8; columns 2 t4, 2 t4 + 1
         // of both n-tiles), copied to shared memory in the background
         {
@@ -226,7 +247,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
             vm[0][t] = (t < nt && ra < m) ? __ldg(vr) : 0.0f;
             vm[1][t] = (t < nt && ra + 8 < m) ? __ldg(vr + 8 * nv) : 0.0f;
         }
-        // per-term multipliers (split pairs) at the element's points, zero up to P8
+        // per-term multipliers (split pairs) at the element's points, zero up to P4
         float2(*M)[TC_PMAX] = sMul[wib];
         float cmax[NT];
 #pragma unroll
@@ -236,7 +257,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         float2(*CR)[TC_PMAX] = sCr[wib];
 #pragma unroll 1
         for (int r = 0; r < tm.ncrow; ++r)
-            for (int q = lane; q < 8 * hpt; q += 32) {
+            for (int q = lane; q < 4 * qpt; q += 32) {
                 float2 c = make_float2(0.0f, 0.0f);
                 if (q < P) {
                     const double v = coef ? coef[r * tm.cstride + d.y + q] : 1.0;
@@ -246,7 +267,7 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
                 CR[r][q] = c;
             }
         __syncwarp();
-        for (int q = lane; q < 8 * hpt; q += 32) {
+        for (int q = lane; q < 4 * qpt; q += 32) {
             const bool in = q < P;
             const float2 gq = GAUSS && in ? src.gw2[d.y + q] : make_float2(1.0f, 0.0f);
 #pragma unroll
@@ -289,8 +310,8 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
                 for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
 
         // slices of one half-chunk's test side into A fragments, then the 30 MMAs
-        auto step = [&](const Half& H, int t, int hh) {
-            const int q = hh * 8 + 2 * t4;
+        auto step = [&](const Half& H) {
+            const int t = H.t < 0 ? 0 : H.t, q = H.t < 0 ? 0 : H.q;   // zero operands beyond the last quarter
             const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
             uint32_t A[TC_NS][2];
 #pragma unroll
@@ -355,20 +376,17 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         };
 
         // walk the half-chunks two at a time, the next one's operands in flight
-        const int nhalf = nt * hpt;
-        int t = 0, hh = 0, seg = 0;
+        const int nhalf = (nq + 1) >> 1;
+        int seg = 0;
         bool first = true;
         Half h1;
         for (int h = 0; h < nhalf; h += 2) {
-            int t1 = t, hh1 = hh + 1;
-            if (hh1 == hpt) hh1 = 0, ++t1;
-            if (h + 1 < nhalf) load_half(h1, tv, sT[t1][0], sT[t1][1], hh1, P, t4, bsl);
-            step(h0, t, hh);
-            int t2 = t1, hh2 = hh1 + 1;
-            if (hh2 == hpt) hh2 = 0, ++t2;
-            if (h + 2 < nhalf) load_half(h0, tv, sT[t2][0], sT[t2][1], hh2, P, t4, bsl);
-            if (h + 1 < nhalf) step(h1, t1, hh1);
-            t = t2, hh = hh2;
+            advance();
+            if (h + 1 < nhalf) load_half(h1, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
+            step(h0);
+            advance();
+            if (h + 2 < nhalf) load_half(h0, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
+            if (h + 1 < nhalf) step(h1);
             seg += 2;
             if (seg == TC_SEGH && h + 2 < nhalf) {
                 flush(first);
@@ -459,24 +477,23 @@ __global__ void __launch_bounds__(128) k_tc_prep(int nc, int nwc, const int32_t*
         pr.fexp[e * nc + c] = f;
     }
     __syncthreads();
-    // trial-side slices
-    const int ncb = (m + 15) >> 4, hpt = (P + 7) >> 3;
-    const int nitem = nc * ncb * hpt * 32;
+    // trial-side slices, per (component, column block, quarter-chunk, point pair p, column g)
+    const int ncb = (m + 15) >> 4, qpt = (P + 3) >> 2;
+    const int nitem = nc * ncb * qpt * 16;
     uint32_t* out = pr.bs + pr.bs_ptr[e];
     for (int x = threadIdx.x; x < nitem; x += blockDim.x) {
-        const int ln = x & 31;
-        int r = x >> 5;
-        const int hh = r % hpt;
-        r /= hpt;
+        const int pg = x & 15, p = pg >> 3, g = pg & 7;
+        int r = x >> 4;
+        const int qq = r % qpt;
+        r /= qpt;
         const int cb = r % ncb, c = r / ncb;
-        const int g = ln >> 2, t4 = ln & 3;
         float kk[2][2][TC_NS];   // [n-tile][point][slice]
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
             const int b = cb * 16 + n * 8 + g;
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp) {
-                const int q = hh * 8 + 2 * t4 + pp;
+                const int q = qq * 4 + 2 * p + pp;
                 double y = (q < P && b < m) ? ldexp(tb[((int64_t)q * nc + c) * m + b], 8 - sf[c]) : 0.0;
 #pragma unroll
                 for (int l = 0; l < TC_NS; ++l) {
@@ -486,10 +503,10 @@ __global__ void __launch_bounds__(128) k_tc_prep(int nc, int nwc, const int32_t*
                 }
             }
         }
-        uint32_t* o = out + ((int64_t)(c * ncb + cb) * hpt + hh) * TC_HW + ln * 2;
+        uint32_t* o = out + ((int64_t)(c * ncb + cb) * qpt + qq) * TC_QW + pg * 2;
 #pragma unroll
         for (int l = 0; l < TC_NS; ++l)
-            *reinterpret_cast<uint2*>(o + l * 64) =
+            *reinterpret_cast<uint2*>(o + l * 32) =
                 make_uint2(pack_bf16x2(kk[0][0][l], kk[0][1][l]), pack_bf16x2(kk[1][0][l], kk[1][1][l]));
     }
     // test-side bounds per (function, column)

@@ -71,10 +71,11 @@ cudaError_t launch_elem_f32(const ElemItems& it, const ElemSrc& src, const Terms
 cudaError_t launch_elem_batch(const BatchPlan& bp, const double* const* coefs, float* const* vals, int k,
                               const Terms& tm, bool compensated, cudaStream_t st);
 
-// Tensor-core contraction: slices per operand, and trial-slice words per (half-chunk of 8
-// points, 16-column block): 32 lanes x 2 n-tiles per slice.
+// Tensor-core contraction: slices per operand, and trial-slice words per (quarter-chunk
+// of 4 points of one component, 16-column block): per slice, 2 point pairs x 8
+// columns x 2 n-tiles.
 constexpr int WQ_TC_SLICES = 5;
-constexpr int WQ_TC_HALF_WORDS = 64 * WQ_TC_SLICES;
+constexpr int WQ_TC_QUARTER_WORDS = 32 * WQ_TC_SLICES;
 
 // Per-entry sums of the slot buffer (FP32 pairs, TwoSum) as a programmatic dependent
 // of the element kernel just launched on st.
