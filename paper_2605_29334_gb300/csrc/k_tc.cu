@@ -38,7 +38,6 @@
 // half-chunks (K = 128) the levels are added to the tile's slots (a TwoSum against the
 // earlier segments), so any K is exact.
 #include <algorithm>
-#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -105,13 +104,6 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
     asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a0), "r"(a1), "r"(b0));
-}
-// The same with a zero accumulator input (the first product of a segment).
-__device__ __forceinline__ void mma_k8_first(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
-    const float z = 0.0f;
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%7,%7,%7};\n"
-        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-        : "r"(a0), "r"(a1), "r"(b0), "f"(z));
 }
 
 // Smallest E with 2^E > x (x > 0, finite): the frexp exponent, from the encoding for
@@ -309,10 +301,16 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         }
         __syncwarp();
 
-        float acc[TC_NS][2][4];   // written first by the segment's first half-chunk
+        float acc[TC_NS][2][4];
+#pragma unroll
+        for (int l = 0; l < TC_NS; ++l)
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
 
         // slices of one half-chunk's test side into A fragments, then the 30 MMAs
-        auto step = [&](const Half& H, auto first_half) {   // first_half: std::true_type / false_type
+        auto step = [&](const Half& H) {
             const int t = H.t < 0 ? 0 : H.t, q = H.t < 0 ? 0 : H.q;   // zero operands beyond the last quarter
             const float2 mu0 = M[t][q], mu1 = M[t][q + 1];
             uint32_t A[TC_NS][2];
@@ -336,14 +334,11 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
 #pragma unroll
                 for (int ka = 0; ka < TC_NS; ++ka)
 #pragma unroll
-                    for (int lb = 0; lb < TC_NS - ka; ++lb) {
-                        const uint32_t bw = n ? H.b[lb].y : H.b[lb].x;
-                        if (decltype(first_half)::value && ka == 0) mma_k8_first(acc[lb][n], A[0][0], A[0][1], bw);
-                        else mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], bw);
-                    }
+                    for (int lb = 0; lb < TC_NS - ka; ++lb)
+                        mma_k8(acc[ka + lb][n], A[ka][0], A[ka][1], n ? H.b[lb].y : H.b[lb].x);
         };
         // write the level sums of this segment to the slots (adding to the earlier
-        // segments' values, which only this lane writes)
+        // segments' values, which only this lane writes) and clear them
         auto flush = [&](bool first) {
             asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
@@ -372,40 +367,32 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
                     }
                 }
             }
+#pragma unroll
+            for (int l = 0; l < TC_NS; ++l)
+#pragma unroll
+                for (int n = 0; n < 2; ++n)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
         };
 
-        // walk the half-chunks two at a time, the next one's operands in flight; the
-        // first one writes the accumulators (zero input), later segments start from
-        // cleared ones
+        // walk the half-chunks two at a time, the next one's operands in flight
         const int nhalf = (nq + 1) >> 1;
+        int seg = 0;
         bool first = true;
         Half h1;
-        advance();
-        if (1 < nhalf) load_half(h1, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
-        step(h0, std::true_type{});
-        advance();
-        if (2 < nhalf) load_half(h0, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
-        if (1 < nhalf) step(h1, std::false_type{});
-        int seg = 2;
-        for (int h = 2; h < nhalf; h += 2) {
-            if (seg == TC_SEGH) {
+        for (int h = 0; h < nhalf; h += 2) {
+            advance();
+            if (h + 1 < nhalf) load_half(h1, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
+            step(h0);
+            advance();
+            if (h + 2 < nhalf) load_half(h0, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
+            if (h + 1 < nhalf) step(h1);
+            seg += 2;
+            if (seg == TC_SEGH && h + 2 < nhalf) {
                 flush(first);
                 first = false;
                 seg = 0;
-#pragma unroll
-                for (int l = 0; l < TC_NS; ++l)
-#pragma unroll
-                    for (int n = 0; n < 2; ++n)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[l][n][j] = 0.0f;
             }
-            advance();
-            if (h + 1 < nhalf) load_half(h1, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
-            step(h0, std::false_type{});
-            advance();
-            if (h + 2 < nhalf) load_half(h0, tv, sT, tq < nt ? tq : -1, qq, P, t4, bsl);
-            if (h + 1 < nhalf) step(h1, std::false_type{});
-            seg += 2;
         }
         flush(first);
         __syncwarp();   // the per-warp shared arrays are rewritten by the next tile
