@@ -126,6 +126,28 @@ struct TcPrep {
     float* vmax;
 };
 
+// (hi, lo) float pair of a double v with hi + lo = v to 2^-47 |v|: hi is v cut to 24
+// significant bits, lo the next 24 bits of the remainder (cut as well).  Built from the
+// encoding with integer instructions for 2^-60 < |v| < 2^100 (the FP64 conversions run on
+// the slow FP64 pipe of this GPU); outside that range, and for 0, by conversions.
+__device__ __forceinline__ float2 split_double(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (ex <= -60 || ex >= 100) {
+        const float h = __double2float_rn(v);
+        return make_float2(h, __double2float_rn(v - (double)h));
+    }
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;                  // 52 bits
+    const float hi = __uint_as_float(sign | ((unsigned)(ex + 127) << 23) | (unsigned)(mant >> 29));
+    const unsigned r = (unsigned)(mant & 0x1FFFFFFFu);                      // the other 29 bits
+    if (r == 0u) return make_float2(hi, 0.0f);
+    const int msb = 31 - __clz(r);                                          // 0..28
+    const unsigned m24 = msb >= 23 ? (r >> (msb - 23)) : (r << (23 - msb));  // leading one at bit 23
+    const float lo = __uint_as_float(sign | ((unsigned)(ex - 52 + msb + 127) << 23) | (m24 & 0x7FFFFFu));
+    return make_float2(hi, lo);
+}
+
 // Per-call device pointers, passed as a kernel parameter (N = 1 for one rule).
 constexpr int WQ_BATCH_MAX = 256;
 template <int N>

@@ -239,14 +239,10 @@ __global__ void __launch_bounds__(EL_NWARP * 32, 6)
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     const int cr = tm.crow[t];
-                    const double v = g * (cr < 0 ? tm.scale[t] : (coef ? D_[cr * QC + lane] : 1.0));
-                    const float vh = (float)v;
-                    C_[lane * NT + t] = make_float2(vh, (float)(v - (double)vh));
+                    C_[lane * NT + t] = split_double(g * (cr < 0 ? tm.scale[t] : (coef ? D_[cr * QC + lane] : 1.0)));
                 }
             } else if (tm.ncrow <= 1) {
-                const double cq = coef ? D_[lane] : 1.0;
-                const float ch = (float)cq;
-                const float2 cs = make_float2(ch, (float)(cq - (double)ch));   // split once per point
+                const float2 cs = coef ? split_double(D_[lane]) : make_float2(1.0f, 0.0f);   // once per point
 #pragma unroll
                 for (int t = 0; t < NT; ++t)
                     C_[lane * NT + t] = tm.crow[t] >= 0 ? cs : make_float2(tm.shi[t], tm.slo[t]);
@@ -254,13 +250,10 @@ __global__ void __launch_bounds__(EL_NWARP * 32, 6)
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     const int cr = tm.crow[t];
-                    if (cr < 0) {
+                    if (cr < 0)
                         C_[lane * NT + t] = make_float2(tm.shi[t], tm.slo[t]);
-                    } else {
-                        const double cq = coef ? D_[cr * QC + lane] : 1.0;
-                        const float ch = (float)cq;
-                        C_[lane * NT + t] = make_float2(ch, (float)(cq - (double)ch));
-                    }
+                    else
+                        C_[lane * NT + t] = coef ? split_double(D_[cr * QC + lane]) : make_float2(1.0f, 0.0f);
                 }
             }
         }

@@ -252,18 +252,13 @@ __global__ void __launch_bounds__(TC_NWARP * 32, TC_BLOCKS_PER_SM)
         float cmax[NT];
 #pragma unroll
         for (int t = 0; t < NT; ++t) cmax[t] = 0.0f;
-        // the coefficient rows split once per point (a runtime loop over the rows used:
-        // the FP64 conversions are on the slow FP64 pipe)
+        // the coefficient rows split once per point (a runtime loop over the rows used)
         float2(*CR)[TC_PMAX] = sCr[wib];
 #pragma unroll 1
         for (int r = 0; r < tm.ncrow; ++r)
             for (int q = lane; q < 4 * qpt; q += 32) {
                 float2 c = make_float2(0.0f, 0.0f);
-                if (q < P) {
-                    const double v = coef ? coef[r * tm.cstride + d.y + q] : 1.0;
-                    const float h = __double2float_rn(v);
-                    c = make_float2(h, __double2float_rn(v - (double)h));
-                }
+                if (q < P) c = coef ? split_double(coef[r * tm.cstride + d.y + q]) : make_float2(1.0f, 0.0f);
                 CR[r][q] = c;
             }
         __syncwarp();
