@@ -428,7 +428,7 @@ def other_configs(ctx, flush, steps, warmup):
 # DRAM bytes (read + write) of one launch of the element-block kernel on this workload,
 # from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md), valid for the kernel
 # source it was taken on.
-ELEM_TRAFFIC = {"k_assemble.cu": "8568ae817d395ffb6aea7eafeb45bcede23bfd56", "k_elem_f32<2,1,0>": 60599296}
+ELEM_TRAFFIC = {"k_assemble.cu": "a98cd6ec97b61537dadabb952082956f467ef544", "k_elem_f32<2,1,0>": 60436992}
 
 
 def _kernel_source_sha1(name):
