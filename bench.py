@@ -158,22 +158,13 @@ def bench_ours(args, rank, world):
     out64 = torch.empty(nnz, dtype=torch.float64, device="cuda")
     out32 = torch.empty(nnz, dtype=torch.float32, device="cuda")
     outg = torch.empty(nnz, dtype=torch.float64, device="cuda")
-    # accuracy of the FP32 paths against the FP64 path (same weights), per mode
-    rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F64, out=out64)
-    torch.cuda.synchronize()
-    a64 = out64.cpu().numpy()
-    rel = {}
     modes = {"f64": wq.PREC_F64, "f32": wq.PREC_F32, "f32_fast": wq.PREC_F32_FAST, "tc": wq.PREC_TC}
-    for name in ("tc", "f32", "f32_fast"):
-        rule.assemble(wq.OP_STIFF, coef, prec=modes[name], out=out32)
-        torch.cuda.synchronize()
-        rel[name] = float(np.max(np.abs(out32.cpu().numpy().astype(np.float64) - a64)) / np.max(np.abs(a64)))
+    # the library's autotuner: each float mode's error against FP64 on this workload, and
+    # the fastest mode within the 1e-6 bar (else FP64)
+    tune = rule.autotune(wq.OP_STIFF, coef, tol=1e-6, reps=50)
+    rel = dict(zip(("tc", "f32", "f32_fast"), tune["err"]))
     if args.prec == "auto":
-        # the fastest mode within the 1e-6 bar (short flushed trial of each), else FP64
-        trial = {name: float(np.median(time_steps(
-            lambda pm=modes[name]: rule.assemble(wq.OP_STIFF, coef, prec=pm, out=out32), 50, 5, flush)))
-            for name in ("tc", "f32", "f32_fast") if rel[name] <= 1e-6}
-        choice = min(trial, key=trial.get) if trial else "f64"
+        choice = {wq.PREC_TC: "tc", wq.PREC_F32: "f32", wq.PREC_F32_FAST: "f32_fast"}.get(tune["chosen"], "f64")
     else:
         choice = args.prec
     prec = modes[choice]
@@ -291,6 +282,7 @@ def bench_ours(args, rank, world):
                    "n_points": rule.Q, "n_gauss": rule.G, "op": "stiffness", "l2": "flushed (256 MB write) before "
                    "every timed step; timed = the assembly call only", "parallelism": "independent instance per GPU"},
         "rel_err_vs_f64": rel,
+        "autotune_ms": dict(zip(("tc", "f32", "f32_fast"), tune["ms"])),
         "gpu_launches": args.steps * 2,
         "roofline": roof,
         "comparators": dict({k + "_ms": v for k, v in comp_ms.items()},

@@ -62,13 +62,15 @@ typedef enum { WQ_COMP_N = 0, WQ_COMP_X = 1, WQ_COMP_Y = 2, WQ_COMP_Z = 3, WQ_CO
 typedef enum {
     WQ_PREC_F64 = 0,      /* FP64 weights, tables and accumulation; CSR values double */
     WQ_PREC_F32 = 1,      /* FP32 split (hi/lo) products, error-free (TwoSum) accumulation; float values */
-    WQ_PREC_F32_FAST = 2, /* FP32 split products, plain FP32 sums (operators with <= 2 terms); float
-                             values; its error depends on the cancellation in the rows -- measure it */
-    WQ_PREC_TC = 3        /* element blocks on the tensor cores: both operands scaled per row /
+    WQ_PREC_F32_FAST = 2, /* FP32 split products, plain FP32 sums; float values; its error depends on
+                             the cancellation in the rows -- measure it (wq_rule_autotune does) */
+    WQ_PREC_TC = 3,       /* element blocks on the tensor cores: both operands scaled per row /
                              element and split into five 8-bit bf16 slices, slice pairs up to level 4
                              summed exactly in FP32 (integers below 2^24; error-free transformation
                              of Ozaki et al.), per-entry sums as WQ_PREC_F32; float values, error
                              ~2^-40 of each tile's largest |s| |T| K; needs <= 64 points per element */
+    WQ_PREC_AUTO = 4      /* the float mode wq_rule_autotune chose for this operator and quadrature
+                             (WQ_PREC_F32 until it has run); float values */
 } wq_prec;
 
 /* Point-count rule (Sec. 4.2). */
@@ -296,6 +298,22 @@ wq_status wq_rule_load(wq_basis* basis, const char* path, wq_rule** out);
  * frees the events.  Not for calls inside a stream capture.  Errors: WQ_ERR_ARG,
  * WQ_ERR_CUDA (event creation). */
 wq_status wq_rule_set_timing(wq_rule* rule, int32_t capacity);
+
+/* Kernel choice by measurement (autotuner; no counterpart in the paper).  For
+ * operator op on this rule (gauss = 0: WQ assembly, 1: Gauss assembly) and the
+ * coefficient d_coef (as for wq_assemble / wq_gq_assemble): assembles once in FP64
+ * and once in each float mode (WQ_PREC_TC, WQ_PREC_F32, WQ_PREC_F32_FAST),
+ * measures each mode's normwise error max|A - A_64| / max|A_64|, times the modes
+ * within tol on the device (CUDA events on stream; two warm-ups, then `reps`
+ * assemblies, no cache flush), and records the fastest of them as the rule's
+ * WQ_PREC_AUTO choice for (op, gauss).  *chosen = that mode, or -1 when no float
+ * mode is within tol (WQ_PREC_AUTO then stays WQ_PREC_F32).  h_err[3] and h_ms[3]
+ * (optional) receive the errors and the mean times in the order TC, F32, F32_FAST
+ * (a mode not available for this rule or operator: error -1; not timed: time -1).
+ * Allocates temporary device buffers and synchronises stream.  Errors: WQ_ERR_ARG,
+ * WQ_ERR_OOM, WQ_ERR_CUDA. */
+wq_status wq_rule_autotune(wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t gauss, double tol,
+                           int32_t reps, void* stream, int32_t* chosen, double* h_err, float* h_ms);
 
 /* Durations of the recorded calls in call order: h_ms[2k] and h_ms[2k + 1] are
  * the first and second kernel of call k (milliseconds); *n_calls = number of

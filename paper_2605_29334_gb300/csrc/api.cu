@@ -855,6 +855,7 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
         return fail(rule->ctx, WQ_ERR_ARG, "operator needs weight sets that this rule did not build");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
+    if (prec == WQ_PREC_AUTO) prec = rule->auto_prec[op][0];
     if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST && prec != WQ_PREC_TC)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     if (prec == WQ_PREC_TC && !rule->tc_ok)
@@ -878,6 +879,7 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
     if (!op_terms(rule, op, alpha, false, tm, rule->G)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
     cudaError_t e;
     cudaStream_t st = (cudaStream_t)stream;
+    if (prec == WQ_PREC_AUTO) prec = rule->auto_prec[op][1];
     if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST && prec != WQ_PREC_TC)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     if (prec == WQ_PREC_TC && !rule->tc_ok)
@@ -1006,6 +1008,10 @@ wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* con
     if (!batch || !h_vals) return WQ_ERR_ARG;
     const int k = (int)batch->rules.size();
     cudaStream_t st = (cudaStream_t)stream;
+    if (prec == WQ_PREC_AUTO) {   // the first rule's choice (the rules share their operators)
+        if (op < 0 || op > 4) return fail(batch->ctx, WQ_ERR_ARG, "unknown operator");
+        prec = batch->rules[0]->auto_prec[op][0];
+    }
     if (prec == WQ_PREC_F64 || prec == WQ_PREC_TC) {   // one launch pair per rule
         for (int r = 0; r < k; ++r) {
             wq_status s = wq_assemble(batch->rules[r], op, h_coefs ? h_coefs[r] : nullptr, alpha, prec, h_vals[r],
@@ -1030,6 +1036,88 @@ wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* con
     }
     cudaError_t e = wqd::launch_elem_batch(batch->plan, coefs, vals, k, tm, prec == WQ_PREC_F32, st);
     if (e != cudaSuccess) return fail(batch->ctx, WQ_ERR_CUDA, std::string("batched assembly: ") + cudaGetErrorString(e));
+    return WQ_OK;
+}
+
+wq_status wq_rule_autotune(wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t gauss, double tol,
+                           int32_t reps, void* stream, int32_t* chosen, double* h_err, float* h_ms) {
+    if (!rule || op < 0 || op > 4 || (gauss != 0 && gauss != 1) || reps < 1 || !(tol >= 0.0))
+        return fail(rule ? rule->ctx : nullptr, WQ_ERR_ARG, "autotune: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nnz = rule->nnz;
+    double* d64 = nullptr;
+    float* d32 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto release = [&]() {
+        if (d64) cudaFree(d64);
+        if (d32) cudaFree(d32);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&d64, std::max<int64_t>(nnz, 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&d32, std::max<int64_t>(nnz, 1) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(rule->ctx, WQ_ERR_OOM, "autotune: scratch allocation failed");
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        release();
+        return fail(rule->ctx, WQ_ERR_CUDA, "autotune: event creation failed");
+    }
+    auto run = [&](int32_t prec, void* out) {
+        return gauss ? wq_gq_assemble(rule, op, d_coef, alpha, prec, out, stream)
+                     : wq_assemble(rule, op, d_coef, alpha, prec, out, stream);
+    };
+    wq_status s = run(WQ_PREC_F64, d64);
+    std::vector<double> a64(nnz);
+    std::vector<float> a32(nnz);
+    if (s == WQ_OK && nnz > 0 &&
+        (cudaMemcpyAsync(a64.data(), d64, nnz * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+        s = fail(rule->ctx, WQ_ERR_CUDA, "autotune: copy failed");
+    if (s != WQ_OK) {
+        release();
+        return s;
+    }
+    double amax = 0.0;
+    for (double v : a64) amax = std::max(amax, std::fabs(v));
+    const int32_t modes[3] = {WQ_PREC_TC, WQ_PREC_F32, WQ_PREC_F32_FAST};
+    int32_t best = -1;
+    float best_ms = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        double err = -1.0;
+        float ms = -1.0f;
+        if (run(modes[k], d32) == WQ_OK) {   // a mode this rule or operator does not take is skipped
+            if (nnz > 0 && (cudaMemcpyAsync(a32.data(), d32, nnz * sizeof(float), cudaMemcpyDeviceToHost, st) !=
+                                cudaSuccess ||
+                            cudaStreamSynchronize(st) != cudaSuccess)) {
+                release();
+                return fail(rule->ctx, WQ_ERR_CUDA, "autotune: copy failed");
+            }
+            double dmax = 0.0;
+            for (int64_t x = 0; x < nnz; ++x) dmax = std::max(dmax, std::fabs((double)a32[x] - a64[x]));
+            err = amax > 0.0 ? dmax / amax : dmax;
+            if (err <= tol) {
+                for (int w = 0; w < 2; ++w) run(modes[k], d32);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < reps; ++r) run(modes[k], d32);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    release();
+                    return fail(rule->ctx, WQ_ERR_CUDA, "autotune: timing failed");
+                }
+                ms /= (float)reps;
+                if (best < 0 || ms < best_ms) best = modes[k], best_ms = ms;
+            }
+        } else {
+            rule->ctx->err.clear();
+        }
+        if (h_err) h_err[k] = err;
+        if (h_ms) h_ms[k] = ms;
+    }
+    release();
+    rule->auto_prec[op][gauss] = best >= 0 ? best : WQ_PREC_F32;
+    if (chosen) *chosen = best;
     return WQ_OK;
 }
 

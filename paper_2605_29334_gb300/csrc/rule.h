@@ -38,6 +38,7 @@ struct wq_rule {
     double tol = 1e-12;
     int max_sweeps = 40;
     int count_mode = 0;
+    int32_t auto_prec[5][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}};   // WQ_PREC_AUTO per (op, gauss)
     std::vector<wqi::DevBuf> bufs;
     // device arrays
     int32_t *d_m = nullptr, *d_nsub = nullptr, *d_side = nullptr, *d_pt_elem = nullptr, *d_gp_elem = nullptr;

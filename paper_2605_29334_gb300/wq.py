@@ -20,7 +20,7 @@ WQ_OK, WQ_ERR_ARG, WQ_ERR_MESH, WQ_ERR_ILLPOSED, WQ_ERR_NOT_CONVERGED, WQ_ERR_NO
     WQ_ERR_OOM, WQ_ERR_NO_DEVICE = range(9)
 OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S, OP_HEAT_J = range(5)
 COMP_N, COMP_X, COMP_Y, COMP_Z, COMP_LAP = range(5)
-PREC_F64, PREC_F32, PREC_F32_FAST, PREC_TC = 0, 1, 2, 3
+PREC_F64, PREC_F32, PREC_F32_FAST, PREC_TC, PREC_AUTO = 0, 1, 2, 3, 4
 TYPE_NAMES = ["passive", "boundary", "irregular", "enriched_transition", "transition", "enriched_regular", "regular"]
 
 
@@ -91,6 +91,8 @@ EXPORTS = {
     "wq_assemble_batched": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.c_double, C.c_int32,
                                       C.POINTER(C.c_void_p), C.c_void_p]),
     "wq_rule_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_void_p)]),
+    "wq_rule_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_double,
+                                   C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p]),
     "wq_rule_kernel_times": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
 }
 
@@ -363,6 +365,19 @@ class Rule:
         self.ctx.check(lib().wq_rule_weights_noalloc(self.h, int(comp), C.c_void_p(out.data_ptr()),
                                                      _stream_handle(stream)))
         return out
+
+    def autotune(self, op, coef, alpha=0.0, gauss=False, tol=1e-6, reps=20, stream=None):
+        """wq_rule_autotune: pick the fastest float mode within tol for (op, gauss) by
+        measurement; later calls with prec=PREC_AUTO use it.  Returns {"chosen": mode
+        or -1, "err": [TC, F32, F32_FAST], "ms": [...]} (-1: not available / not timed)."""
+        chosen = C.c_int32(0)
+        err = np.zeros(3, dtype=np.float64)
+        ms = np.zeros(3, dtype=np.float32)
+        cp = C.c_void_p(coef.data_ptr()) if coef is not None else C.c_void_p(0)
+        self.ctx.check(lib().wq_rule_autotune(self.h, int(op), cp, float(alpha), int(bool(gauss)),
+                                              float(tol), int(reps), _stream_handle(stream), C.byref(chosen),
+                                              _ptr(err), _ptr(ms)))
+        return {"chosen": chosen.value, "err": err.tolist(), "ms": ms.tolist()}
 
     def set_timing(self, capacity):
         """Record per-kernel CUDA events for the next `capacity` assembly calls (0: off)."""
