@@ -22,18 +22,19 @@
 //  * K_e[a][b] = 2^(E_a - 16) sum_{d <= 4} 2^(-8 d) D_d, the pairs with k + l > 4
 //    dropped (below 2^-40 of the tile's product scale).
 // The error is relative to the tile's largest |s| |T| K, not to each entry: the weights
-// of ill-conditioned rows span several decades with cancelling signs, and with four
-// slices (2^-32) the 24,576-element sphere bilaplacian reached 1e-5 normwise; five
-// slices put that case below the FP32 rounding of the values.  The SIMT work is per
-// (row, point, term) -- split product and 5 slices, ~24 instructions -- instead of per
-// (row, column, point, term).
+// of ill-conditioned rows span several decades with cancelling signs.  Five slices, and
+// a fold that keeps D_0 + 2^-8 D_1 as an exact TwoSum pair, put the 24,576-element
+// sphere bilaplacian at the FP32 rounding of the values (four slices with a plain FP32
+// fold: 1e-5 normwise).  The SIMT work is per (row, point, term) -- split product and 5
+// slices, ~24 instructions -- instead of per (row, column, point, term).
 //
 // Persistent warps, one 16 x 16 tile at a time (the FP32 path's tiles and slot map; the
-// next tile's descriptors are prefetched).  The K range is walked in half-chunks of 8
-// points of one term (each term's points padded to a multiple of 8).  Lane (g, t4) =
-// (lane / 4, lane % 4) builds the m16n8k8 A fragments of its rows g, g + 8 at the points
-// 2 t4, 2 t4 + 1, loads the trial fragments precomputed in that order (one 8-byte load
-// per slice), and runs 15 slice pairs x 2 n-tiles of mma.sync into 5 level
+// next tile's descriptors are prefetched).  K is walked in quarter-chunks of 4 points
+// of one term (each term's points padded to a multiple of 4), two quarters per
+// m16n8k8 step: lane (g, t4) = (lane / 4, lane % 4) takes the quarter t4 / 2 selects
+// and builds the A fragments of its rows g, g + 8 at that quarter's points
+// 2 (t4 % 2), 2 (t4 % 2) + 1, loads the trial fragments precomputed in that order (one
+// 8-byte load per slice), and runs 15 slice pairs x 2 n-tiles of mma.sync into 5 level
 // accumulators; the next half-chunk's loads are in flight meanwhile.  Every 16
 // half-chunks (K = 128) the levels are added to the tile's slots (a TwoSum against the
 // earlier segments), so any K is exact.
