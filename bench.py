@@ -291,7 +291,13 @@ def bench_ours(args, rank, world):
                             speedup_wq_over_gq_f32=comp_ms["gq_f32"] / comp_ms["wq_f32"],
                             speedup_wq_over_gq_tc=comp_ms["gq_tc"] / comp_ms["wq_tc"]),
         "setup": {"host_basis_ms": host_ms, "rule_build_wall_ms": build_ms, "rule_build_device_ms": rule.info.setup_ms,
-                  "n_truncated_x": rule.info.n_truncated[1], "n_z_identity_x": rule.info.n_z_identity[1]},
+                  "n_truncated_x": rule.info.n_truncated[1], "n_z_identity_x": rule.info.n_z_identity[1],
+                  # truncated-SVD weight solves (a5): FP64 operations counted by the kernel against
+                  # 152 SMs x 2 FP64 FMA per cycle x 2 x max SM clock
+                  "tsvd_ms": rule.info.tsvd_ms, "tsvd_gflop": rule.info.tsvd_gflop,
+                  "tsvd_fp64_tflops": rule.info.tsvd_gflop / max(rule.info.tsvd_ms, 1e-9),
+                  "tsvd_fp64_frac": rule.info.tsvd_gflop / max(rule.info.tsvd_ms, 1e-9)
+                  / (152 * 2 * 2 * sm_mhz * 1e6 / 1e12)},
         "e2e": {"value": nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(rule.Q * 8),
                 "d2h_bytes_per_step": int(nnz * (8 if prec == wq.PREC_F64 else 4))},
         "clocks": clocks,

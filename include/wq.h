@@ -128,6 +128,8 @@ typedef struct {
     int32_t n_truncated[5];   /* per component: systems with t < n_i (rank-deficient) */
     int32_t n_z_identity[5];  /* per component: systems that used Z = I (N_i vanishes on a sub-element) */
     double setup_ms;          /* device time of the rule build */
+    double tsvd_ms;           /* device time of the truncated-SVD weight solves (0 for a loaded rule) */
+    double tsvd_gflop;        /* their FP64 operations, counted by the kernel (1e9) */
 } wq_rule_info;
 
 /* --- context ------------------------------------------------------------ */

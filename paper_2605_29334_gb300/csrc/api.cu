@@ -525,7 +525,9 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         if (R->wcidx[c] >= 0 && !dalloc(R, R->d_mom[c], (size_t)R->nnz, sst)) return bail(sst);
     int32_t* d_rank = nullptr;
     uint8_t* d_zid = nullptr;
-    if (!dalloc(R, d_rank, (size_t)n, sst) || !dalloc(R, d_zid, (size_t)n, sst)) return bail(sst);
+    double* d_flops = nullptr;
+    if (!dalloc(R, d_rank, (size_t)n, sst) || !dalloc(R, d_zid, (size_t)n, sst) || !dalloc(R, d_flops, 1, sst))
+        return bail(sst);
     // TSVD scratch: one slice per resident CTA
     const int64_t mn = R->max_n_i, mr = R->max_r;
     const int64_t per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
@@ -614,13 +616,20 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         ce = wqd::launch_moments_f64(rw, R->d_desc_gq, table_comp(R, c), nc, R->d_gtable, R->d_gw, R->d_mom[c],
                                      R->max_n_i, st);
     }
-    // a5: truncated-SVD weights per component
+    // a5: truncated-SVD weights per component (timed, FP64 operations counted)
     std::vector<int32_t> rank(n);
     std::vector<uint8_t> zid(n);
+    cudaEvent_t evt0 = nullptr, evt1 = nullptr;
+    if (!saved && ce == cudaSuccess) {
+        ce = cudaMemsetAsync(d_flops, 0, sizeof(double), st);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&evt0);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&evt1);
+        if (ce == cudaSuccess) ce = cudaEventRecord(evt0, st);
+    }
     for (int c = 0; c < 5 && ce == cudaSuccess && !saved; ++c) {
         if (R->wcidx[c] < 0) continue;
         ce = wqd::launch_tsvd(el, rw, R->d_table, table_comp(R, c), R->d_mom[c], R->d_W, R->nwc, R->wcidx[c], tol,
-                              sweeps, d_scratch, per_cta, n_cta, d_rank, d_zid, R->d_status, st);
+                              sweeps, d_scratch, per_cta, n_cta, d_rank, d_zid, R->d_status, d_flops, st);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(rank.data(), d_rank, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(zid.data(), d_zid, n, cudaMemcpyDeviceToHost, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -634,6 +643,20 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
             R->info.n_z_identity[c] = zcount;
         }
     }
+    if (evt0 && evt1 && ce == cudaSuccess) {
+        // the per-component synchronisations above sit inside this interval; they wait on
+        // the device, which is what the interval measures
+        double fl = 0.0;
+        float tms = 0.0f;
+        ce = cudaEventRecord(evt1, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&fl, d_flops, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tms, evt0, evt1);
+        R->info.tsvd_ms = tms;
+        R->info.tsvd_gflop = fl * 1e-9;
+    }
+    if (evt0) cudaEventDestroy(evt0);
+    if (evt1) cudaEventDestroy(evt1);
     if (saved && ce == cudaSuccess) {
         // weights and moments from the file (host buffers live until the synchronisation below)
         ce = cudaMemcpyAsync(R->d_W, saved->W.data(), saved->W.size() * sizeof(double), cudaMemcpyHostToDevice, st);

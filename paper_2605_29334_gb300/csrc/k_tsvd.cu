@@ -29,9 +29,14 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
                                               const double* __restrict__ mom, double* __restrict__ W, int nwc,
                                               int wc, double tol, int max_sweeps, double* __restrict__ scratch,
                                               int64_t per_cta, int32_t* __restrict__ rank_out,
-                                              uint8_t* __restrict__ zid_out, unsigned* status) {
+                                              uint8_t* __restrict__ zid_out, unsigned* status,
+                                              double* __restrict__ flops) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5, bd = blockDim.x;
     __shared__ int sh_t;
+    __shared__ double sh_fl[4];
+    // FP64 operations of the Jacobi phase (6 r per pair check, 6 (r + n) + 20 per rotation)
+    // and of the QR and solves (~2 r t^2 + 8 r t), for the set-up roofline
+    double fl = 0.0;
     double* S = scratch + (int64_t)blockIdx.x * per_cta;
     const int nc = el.nc;
     for (int64_t i = blockIdx.x; i < rw.n; i += gridDim.x) {
@@ -85,6 +90,7 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
         const int per_pass = nwarp * (32 / JG);
         const int npairs = np / 2;
         int converged = (n < 2);
+        int nchk = 0, nrot = 0;   // pair checks and rotations of this lane group
         for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
             int rotated = 0;
             for (int rnd = 0; rnd < np - 1; ++rnd) {
@@ -115,7 +121,9 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
                         be += __shfl_xor_sync(0xffffffffu, be, o);
                         ga += __shfl_xor_sync(0xffffffffu, ga, o);
                     }
+                    nchk += valid && gl == 0;
                     if (valid && al > 0.0 && be > 0.0 && ga * ga > tol2 * (al * be)) {
+                        nrot += gl == 0;
                         const double z = (be - al) / (2.0 * ga);
                         double t;
                         if (fabs(z) < 1e30) {
@@ -149,6 +157,7 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
             converged = !__syncthreads_or(rotated);
         }
         if (!converged && tid == 0) atomicOr(status, ST_NOT_CONVERGED);
+        fl += 6.0 * r * nchk + (6.0 * (r + n) + 20.0) * nrot;
         // 3. singular values, kept set, g = S_t^-1 U_t^T b
         for (int a = warp; a < n; a += nwarp) {
             double s2 = 0.0;
@@ -168,6 +177,7 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
         }
         __syncthreads();
         const int t = sh_t;
+        if (tid == 0) fl += 2.0 * r * (double)t * t + 8.0 * r * t;
         for (int k = warp; k < t; k += nwarp) {
             const int a = keep[k];
             double d = 0.0;
@@ -259,14 +269,24 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
         }
         __syncthreads();
     }
+    if (flops) {
+        for (int o = 16; o >= 1; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
+        if (lane == 0) sh_fl[warp] = fl;
+        __syncthreads();
+        if (tid == 0) {
+            double f = 0.0;
+            for (int w = 0; w < nwarp; ++w) f += sh_fl[w];
+            atomicAdd(flops, f);
+        }
+    }
 }
 
 cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, int tc, const double* mom, double* W,
                         int nwc, int wc, double tol, int max_sweeps, double* scratch, int64_t per_cta, int n_cta,
-                        int32_t* rank, uint8_t* zid, unsigned* status, cudaStream_t st) {
+                        int32_t* rank, uint8_t* zid, unsigned* status, double* flops, cudaStream_t st) {
     if (rw.n == 0) return cudaSuccess;
     k_tsvd<<<n_cta, 128, 0, st>>>(el, rw, table, tc, mom, W, nwc, wc, tol, max_sweeps, scratch, per_cta, rank, zid,
-                                  status);
+                                  status, flops);
     return cudaGetLastError();
 }
 

@@ -104,11 +104,12 @@ cudaError_t launch_split_rows(const double* W, const int32_t* dst, float2* W2e, 
 // Truncated-SVD weights of every row for one component (Sec. 4.3):
 //   table comp tc gives A, table comp 0 gives Z, mom [nnz] gives b;
 //   writes W[(w_ptr[i] + q) * nwc + wc].  scratch holds `per_cta` doubles per CTA.
-//   Per-row rank written to rank[i], Z = I fallback flagged in zid[i].
+//   Per-row rank written to rank[i], Z = I fallback flagged in zid[i]; the FP64
+//   operation count is added to *flops (may be null).
 cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, int tc,
                         const double* mom, double* W, int nwc, int wc, double tol, int max_sweeps,
                         double* scratch, int64_t per_cta, int n_cta, int32_t* rank, uint8_t* zid,
-                        unsigned* status, cudaStream_t st);
+                        unsigned* status, double* flops, cudaStream_t st);
 
 // u_h and grad u_h at WQ points (Sec. 5 interpolation).
 cudaError_t launch_interp(const Elems& el, const int32_t* pt_elem, const int32_t* fns,

@@ -85,7 +85,7 @@ extern "C" wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, 
     if (e == cudaSuccess)
         e = wqd::launch_tsvd(rule->el, rule->rw, rule->d_table, comp == WQ_COMP_LAP ? rule->nc - 1 : comp,
                              rule->d_mom[comp], d_w, 1, 0, rule->tol, rule->max_sweeps, scratch, per_cta, (int)n_cta,
-                             nullptr, nullptr, status, st);
+                             nullptr, nullptr, status, nullptr, st);
     unsigned h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

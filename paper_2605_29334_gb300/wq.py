@@ -47,7 +47,8 @@ class RuleOpts(C.Structure):
 
 class RuleInfo(C.Structure):
     _fields_ = [("n_points", C.c_int64), ("n_gauss", C.c_int64), ("sum_r", C.c_int64), ("max_r", C.c_int32),
-                ("n_truncated", C.c_int32 * 5), ("n_z_identity", C.c_int32 * 5), ("setup_ms", C.c_double)]
+                ("n_truncated", C.c_int32 * 5), ("n_z_identity", C.c_int32 * 5), ("setup_ms", C.c_double),
+                ("tsvd_ms", C.c_double), ("tsvd_gflop", C.c_double)]
 
 
 EXPORTS = {
