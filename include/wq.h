@@ -22,6 +22,10 @@
  *     exactness set S_i (Eq. 10), numerically zero entries are kept.
  *   - Streams are passed as void* (a cudaStream_t; NULL = legacy default stream).
  *   - Handles are not thread-safe; use one context per host thread.
+ *   - Handles may be destroyed in any order (a rule or batch keeps its device id
+ *     and does not read its context when destroyed); calls on a handle whose
+ *     context was destroyed are not allowed.  A CUDA error left pending by other
+ *     code is cleared, not reported, by the next call that launches work.
  */
 #ifndef WQ_H
 #define WQ_H

@@ -118,6 +118,8 @@ bool op_terms(const wq_rule* R, int op, double alpha, bool need_weights, wqd::Te
 
 }  // namespace
 
+
+
 extern "C" {
 
 wq_status wq_create(int device, wq_ctx** out) {
@@ -271,6 +273,10 @@ uint64_t basis_fingerprint(const wqi::BasisHost& B) {
 }
 }  // namespace
 
+// A CUDA error left pending by another caller (or by a teardown) must not be reported
+// by this library's next launch check: entry points that launch work drop it first.
+static inline void drop_stale_error() { (void)cudaGetLastError(); }
+
 static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, const SavedRule* saved, wq_rule** out) {
     if (!basis || !opts || !out) return WQ_ERR_ARG;
     *out = nullptr;
@@ -284,10 +290,12 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     int sweeps = opts->max_sweeps > 0 ? opts->max_sweeps : 40;
     cudaStream_t st = (cudaStream_t)opts->stream;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    drop_stale_error();
 
     wq_rule* R = new (std::nothrow) wq_rule();
     if (!R) return fail(ctx, WQ_ERR_OOM, "host allocation failed");
     R->ctx = ctx;
+    R->device = ctx->device;
     R->basis = basis;
     R->dim = B.dim;
     R->nc = B.dim + 2;
@@ -809,8 +817,11 @@ wq_status wq_rule_load(wq_basis* basis, const char* path, wq_rule** out) {
 }
 
 void wq_rule_destroy(wq_rule* rule) {
-    if (rule && rule->ctx && rule->ctx->device >= 0) cudaSetDevice(rule->ctx->device);
+    // the rule keeps its device id: its context may already be gone (any destruction order)
+    if (!rule) return;
+    if (rule->device >= 0 && cudaSetDevice(rule->device) != cudaSuccess) cudaGetLastError();
     delete rule;
+    cudaGetLastError();   // nothing of a teardown is reported through a later call
 }
 
 wq_status wq_rule_info_get(const wq_rule* rule, wq_rule_info* info) {
@@ -863,6 +874,7 @@ wq_status wq_rule_table(const wq_rule* rule, int32_t gauss, const double** d_tab
 }
 
 wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* stream) {
+    drop_stale_error();
     if (!rule || !d_vals || comp < 0 || comp > 4 || !rule->d_mom[comp])
         return fail(rule ? rule->ctx : nullptr, WQ_ERR_ARG, "component not built");
     CUDA_TRY(rule->ctx, cudaMemcpyAsync(d_vals, rule->d_mom[comp], rule->nnz * sizeof(double),
@@ -872,6 +884,7 @@ wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* st
 
 wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t prec, void* d_vals,
                       void* stream) {
+    drop_stale_error();
     if (!rule || !d_vals) return WQ_ERR_ARG;
     wqd::Terms tm;
     if (!op_terms(rule, op, alpha, true, tm, rule->Q))
@@ -897,6 +910,7 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
 
 wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t prec,
                          void* d_vals, void* stream) {
+    drop_stale_error();
     if (!rule || !d_vals) return WQ_ERR_ARG;
     wqd::Terms tm;
     if (!op_terms(rule, op, alpha, false, tm, rule->G)) return fail(rule->ctx, WQ_ERR_ARG, "unknown operator");
@@ -920,6 +934,7 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
 }
 
 wq_status wq_interp(const wq_rule* rule, const double* d_u, double* d_uq, double* d_grad, void* stream) {
+    drop_stale_error();
     if (!rule || !d_u || !d_uq) return WQ_ERR_ARG;
     cudaError_t e = wqd::launch_interp(rule->el, rule->d_pt_elem, rule->d_fns, rule->d_fn_ptr, rule->Q,
                                        rule->d_table, d_u, d_uq, d_grad, (cudaStream_t)stream);
@@ -929,6 +944,7 @@ wq_status wq_interp(const wq_rule* rule, const double* d_u, double* d_uq, double
 
 wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps, const double* d_g, double* d_y,
                    void* stream) {
+    drop_stale_error();
     if (!rule || !h_comps || !d_g || !d_y || n_terms < 1 || n_terms > 4) return WQ_ERR_ARG;
     int wc[4] = {0, 0, 0, 0};
     for (int t = 0; t < n_terms; ++t) {
@@ -944,6 +960,7 @@ wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps,
 
 wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d_u_old, double dt, double k0, double k2,
                          double f, int32_t jacobian, double* d_kappa, double* d_g, void* stream) {
+    drop_stale_error();
     if (!rule || !d_u || !d_u_old || !d_kappa || !d_g || !(dt > 0)) return WQ_ERR_ARG;
     cudaError_t e = wqd::launch_heat_fields(rule->el, rule->d_pt_elem, rule->d_fns, rule->d_fn_ptr, rule->Q,
                                             rule->d_table, d_u, d_u_old, dt, k0, k2, f, jacobian != 0, d_kappa, d_g,
@@ -953,6 +970,7 @@ wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d
 }
 
 wq_status wq_batch_create(int32_t k, const wq_rule* const* rules, wq_batch** out) {
+    drop_stale_error();
     if (!rules || !out || k < 1 || k > wqd::WQ_BATCH_MAX || !rules[0]) return WQ_ERR_ARG;
     *out = nullptr;
     wq_ctx* ctx = rules[0]->ctx;
@@ -966,6 +984,7 @@ wq_status wq_batch_create(int32_t k, const wq_rule* const* rules, wq_batch** out
     wq_batch* Bt = new (std::nothrow) wq_batch();
     if (!Bt) return fail(ctx, WQ_ERR_OOM, "host allocation failed");
     Bt->ctx = ctx;
+    Bt->device = ctx->device;
     Bt->rules.assign(rules, rules + k);
     // all tiles, ordered by their number of point chunks (long ones first), then by rule
     struct T {
@@ -1022,12 +1041,15 @@ wq_status wq_batch_create(int32_t k, const wq_rule* const* rules, wq_batch** out
 }
 
 void wq_batch_destroy(wq_batch* batch) {
-    if (batch && batch->ctx && batch->ctx->device >= 0) cudaSetDevice(batch->ctx->device);
+    if (!batch) return;
+    if (batch->device >= 0 && cudaSetDevice(batch->device) != cudaSuccess) cudaGetLastError();
     delete batch;
+    cudaGetLastError();
 }
 
 wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* const* h_coefs, double alpha,
                               int32_t prec, void* const* h_vals, void* stream) {
+    drop_stale_error();
     if (!batch || !h_vals) return WQ_ERR_ARG;
     const int k = (int)batch->rules.size();
     cudaStream_t st = (cudaStream_t)stream;
@@ -1064,6 +1086,7 @@ wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* con
 
 wq_status wq_rule_autotune(wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t gauss, double tol,
                            int32_t reps, void* stream, int32_t* chosen, double* h_err, float* h_ms) {
+    drop_stale_error();
     if (!rule || op < 0 || op > 4 || (gauss != 0 && gauss != 1) || reps < 1 || !(tol >= 0.0))
         return fail(rule ? rule->ctx : nullptr, WQ_ERR_ARG, "autotune: bad argument");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1187,6 +1210,7 @@ wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids) {
 
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha, int32_t prec,
                            void* h_vals, void* stream) {
+    drop_stale_error();
     if (!rule || !h_coef || !h_vals) return WQ_ERR_ARG;
     if (op == WQ_OP_HEAT_J) return fail(rule->ctx, WQ_ERR_ARG, "wq_assemble_host takes one coefficient row");
     cudaStream_t st = (cudaStream_t)stream;

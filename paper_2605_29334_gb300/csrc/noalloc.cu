@@ -50,6 +50,7 @@ extern "C" wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, 
     if (dev < 0 || dev >= kMaxDevices) return set_err(ctx, WQ_ERR_NO_DEVICE, "context has no usable device");
     cudaError_t e = cudaSetDevice(dev);
     if (e != cudaSuccess) return set_err(ctx, WQ_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    (void)cudaGetLastError();   // an error pending from another caller is not this call's
     double* scratch = nullptr;
     unsigned* status = nullptr;
     {

@@ -28,6 +28,7 @@ struct DevBuf {
 
 struct wq_rule {
     wq_ctx* ctx = nullptr;
+    int device = -1;                       // the context's device, kept for destruction
     const wq_basis* basis = nullptr;
     int dim = 2, nc = 4;
     uint32_t comps = 0;
@@ -109,6 +110,7 @@ struct wq_rule {
 // Several rules assembled together (wq_batch_create / wq_assemble_batched).
 struct wq_batch {
     wq_ctx* ctx = nullptr;
+    int device = -1;
     std::vector<const wq_rule*> rules;
     std::vector<wqi::DevBuf> bufs;
     wqd::BatchPlan plan{};

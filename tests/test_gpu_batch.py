@@ -126,3 +126,29 @@ def test_rule_save_load_roundtrip(W, tmp_path):
         f.write(data[: len(data) // 2])
     with pytest.raises(W.WQError):
         W.Rule(b, path=cut)
+
+
+def test_handles_destroyed_in_any_order(W):
+    """A context destroyed before its rule (Python's cyclic collector finalises in any
+    order) leaves the rule's teardown and every later call working."""
+    import torch
+    L = W.lib()
+    ctx = W.Context(0)
+    b = W.Basis(ctx, meshes.disk(mu=5, n=4))
+    r = W.Rule(b, comps=[W.COMP_N, W.COMP_X, W.COMP_Y])
+    batch = W.Batch([r])
+    L.wq_destroy(ctx.h)
+    ctx.h = None
+    L.wq_batch_destroy(batch.h)
+    batch.h = None
+    L.wq_rule_destroy(r.h)
+    r.h = None
+    L.wq_basis_destroy(b.h)
+    b.h = None
+    ctx2 = W.Context(0)
+    b2 = W.Basis(ctx2, meshes.disk(mu=5, n=4))
+    r2 = W.Rule(b2, comps=[W.COMP_N, W.COMP_X, W.COMP_Y])
+    kap = torch.tensor(meshes.kappa_sines(r2.points().cpu().numpy()), device="cuda")
+    v = r2.assemble(W.OP_STIFF, kap, prec=W.PREC_F32)
+    torch.cuda.synchronize()
+    assert torch.isfinite(v).all()
