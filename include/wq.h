@@ -262,7 +262,7 @@ wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
                            int32_t prec, void* h_vals, void* stream);
 
-/* Batched assembly of several independent rules (SURVEY config 5: many mesh
+/* Batched assembly of several independent rules (many mesh
  * instances of uneven size).  wq_batch_create concatenates the element tiles of
  * k <= 256 rules (which must share the device, the weight components and the
  * dimension; the rules must outlive the batch) and uploads that plan once.
