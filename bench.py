@@ -423,16 +423,29 @@ def other_configs(ctx, flush, steps, warmup):
     return out
 
 
-# DRAM bytes (read + write) of one launch of the element-block kernel on this workload,
-# from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md), valid for the kernel
-# source it was taken on.
-ELEM_TRAFFIC = {"k_assemble.cu": "a98cd6ec97b61537dadabb952082956f467ef544", "k_elem_f32<2,1,0>": 60436992}
+# DRAM bytes (read + write) of one launch of the element-block kernels on this workload,
+# from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md and
+# profiles/k_elem_tc_poisson_rotated_L4.md), valid for the kernel source they were taken on.
+# The key is the SHA-1 of the kernel's own source text (the template up to the per-entry
+# sums that follow it), so that edits elsewhere in the file keep the measurement.
+ELEM_TRAFFIC = {"k_assemble.cu": "1a3e2518c10271d66a893af1613b3e0eb6afa02a", "k_elem_f32<2,1,0>": 60436992,
+                "k_tc.cu": "3c5ca0106f23d6257452c245b034a1ca7f2d45f6", "k_elem_tc<2,0>": 68657152}
+_KERNEL_TEXT = {"k_assemble.cu": ("template <int NT, bool COMP, bool GAUSS, bool BATCH, int NP>\n__global__ void "
+                                  "__launch_bounds__(EL_NWARP * 32, 6)",
+                                  "// Phase 2: one thread per two consecutive CSR entries."),
+                "k_tc.cu": ("template <int NT, bool GAUSS>\n__global__", "cudaError_t launch_elem_tc(")}
 
 
 def _kernel_source_sha1(name):
     import hashlib
-    with open(os.path.join(ROOT, "paper_2605_29334_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+    with open(os.path.join(ROOT, "paper_2605_29334_gb300", "csrc", name)) as f:
+        s = f.read()
+    begin, end = _KERNEL_TEXT[name]
+    try:
+        s = s[s.index(begin):s.index(end)]
+    except ValueError:
+        return None
+    return hashlib.sha1(s.encode()).hexdigest()
 
 
 def assembly_work(rule, basis, n_terms):

@@ -254,11 +254,13 @@ wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d
 wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
 
 /* Host-buffer round trip for end-to-end use: copies h_coef [Q] to the device,
- * assembles, copies the CSR values back to h_vals [nnz] (double or float by
- * prec), synchronising on stream.  Uses library-owned staging buffers (writing
- * page-locked output directly from the per-entry sums was measured slower: their
- * 4-byte stores use the host link poorly); operators with one coefficient row only
- * (not WQ_OP_HEAT_J). */
+ * assembles, and returns the CSR values in h_vals [nnz] (double or float by prec),
+ * synchronising on stream.  When h_vals is page-locked host memory mapped into the
+ * device's address space (cudaHostAlloc / cudaHostRegister under unified
+ * addressing), the per-entry sums write it directly over the host link, 8 or 16
+ * bytes per store where h_vals is so aligned; otherwise the values go through a
+ * library-owned device buffer and one copy.  Operators with one coefficient row
+ * only (not WQ_OP_HEAT_J). */
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
                            int32_t prec, void* h_vals, void* stream);
 

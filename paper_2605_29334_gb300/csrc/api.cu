@@ -1215,10 +1215,24 @@ wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef
     if (op == WQ_OP_HEAT_J) return fail(rule->ctx, WQ_ERR_ARG, "wq_assemble_host takes one coefficient row");
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(rule->ctx, cudaMemcpyAsync(rule->d_coef_stage, h_coef, rule->Q * sizeof(double), cudaMemcpyHostToDevice, st));
-    wq_status s = wq_assemble(rule, op, rule->d_coef_stage, alpha, prec, rule->d_vals_stage, stream);
+    // page-locked host memory mapped into the device's address space: the per-entry
+    // sums write it directly (the values cross the host link once, no staging copy)
+    void* out = rule->d_vals_stage;
+    bool direct = false;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, h_vals) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr) {
+        out = pa.devicePointer;
+        direct = true;
+    } else {
+        cudaGetLastError();
+    }
+    wq_status s = wq_assemble(rule, op, rule->d_coef_stage, alpha, prec, out, stream);
     if (s != WQ_OK) return s;
-    const size_t vb = rule->nnz * (prec == WQ_PREC_F64 ? sizeof(double) : sizeof(float));
-    CUDA_TRY(rule->ctx, cudaMemcpyAsync(h_vals, rule->d_vals_stage, vb, cudaMemcpyDeviceToHost, st));
+    if (!direct) {
+        const size_t vb = rule->nnz * (prec == WQ_PREC_F64 ? sizeof(double) : sizeof(float));
+        CUDA_TRY(rule->ctx, cudaMemcpyAsync(h_vals, rule->d_vals_stage, vb, cudaMemcpyDeviceToHost, st));
+    }
     CUDA_TRY(rule->ctx, cudaStreamSynchronize(st));
     return WQ_OK;
 }

@@ -394,8 +394,14 @@ __global__ void __launch_bounds__(256) k_gather_f32(ElemSrc one, BatchPlan bp, c
             else hi1 = h, lo1 = l;
         }
     }
-    vals[n] = hi0 + lo0;
-    if (n + 1 < nnz) vals[n + 1] = hi1 + lo1;
+    // n is even: one 8-byte store per pair where the output is 8-byte aligned (a warp
+    // then writes 256 contiguous bytes in one instruction, also to mapped host memory)
+    if (n + 1 < nnz && (reinterpret_cast<uintptr_t>(vals) & 7) == 0) {
+        *reinterpret_cast<float2*>(vals + n) = make_float2(hi0 + lo0, hi1 + lo1);
+    } else {
+        vals[n] = hi0 + lo0;
+        if (n + 1 < nnz) vals[n + 1] = hi1 + lo1;
+    }
 }
 
 // Element kernel, then the per-entry sums as a programmatic dependent launch (its
@@ -623,8 +629,12 @@ __global__ void __launch_bounds__(256) k_gather_f64(int64_t nnz, const int32_t* 
     double s0 = 0.0, s1 = 0.0;
     for (int c = c0; c < c1; ++c) s0 += kscr[c];
     for (int c = c1; c < c2; ++c) s1 += kscr[c];
-    vals[n] = s0;
-    if (n + 1 < nnz) vals[n + 1] = s1;
+    if (n + 1 < nnz && (reinterpret_cast<uintptr_t>(vals) & 15) == 0) {
+        *reinterpret_cast<double2*>(vals + n) = make_double2(s0, s1);
+    } else {
+        vals[n] = s0;
+        if (n + 1 < nnz) vals[n + 1] = s1;
+    }
 }
 
 cudaError_t launch_elem_f64(const ElemItems& it, const ElemSrc64& src, const Terms& tm, int gauss,
