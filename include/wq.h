@@ -95,7 +95,16 @@ typedef struct wq_batch wq_batch;
  *   level0_face  [n_faces] index of the initial-mesh face each face descends
  *                from (-1: none), or NULL when the mesh is itself the initial
  *                mesh.  Enriched elements = descendants of initial irregular
- *                faces (Sec. 3 terminology). */
+ *                faces (Sec. 3 terminology).
+ *   face_xyz     [n_face_xyz][3] positions of the face-based control points:
+ *                4 per enriched face (enriched faces in ascending face order,
+ *                one per corner in corner order), e.g. from wq_refine_apply;
+ *                n_face_xyz must be 4 x the number of enriched faces
+ *                (WQ_ERR_ARG otherwise).  NULL: each is placed at the B-spline
+ *                inner Bezier point of its face (the legs between the face's
+ *                vertices divided in the ratio of the knot spans), which makes
+ *                the geometry away from EPs the bicubic B-spline of the vertex
+ *                control points. */
 typedef struct {
     int32_t dim;
     int64_t n_vertices;
@@ -103,6 +112,8 @@ typedef struct {
     int64_t n_faces;
     const int32_t* quads;
     const int32_t* level0_face;
+    int64_t n_face_xyz;
+    const double* face_xyz;
 } wq_mesh_desc;
 
 typedef struct {

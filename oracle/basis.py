@@ -45,6 +45,14 @@ Table 1 for every entry (tests/test_oracle_basis.py).  The construction is a
 partition of unity and C1 across every edge except inside the sub-elements
 touching an EP (C0 there, with a common tangent plane at the EP).
 
+Positions of the control variables: vertex DOFs sit at the mesh vertices; the
+face DOFs of enriched faces are given by the mesh (``face_xyz`` [4 per enriched
+face, ascending face id, corner order], e.g. computed by a refinement, Sec. 3) or,
+when absent, placed at the B-spline inner Bezier points of the face's four
+vertices (the legs divided in the ratio of the knot spans, (4 near + 2 + 2 +
+1 far)/9 with unit spans; a generator choice for initial meshes, which makes
+the geometry away from EPs the bicubic B-spline of the vertex DOFs).
+
 Function numbering: raw id = vertex index for vertex DOFs, V + 4 * (rank of the
 enriched face) + corner for face DOFs; functions with no non-zero coefficient
 (|c| > 1e-12) on an active element are dropped and the rest renumbered in
@@ -164,18 +172,26 @@ class Basis:
             self.elem_coef.append(np.stack([coefs[k] for k in keys]) if keys else np.zeros((0, 1, 4, 4)))
         self.nsub = np.array([c.shape[1] for c in self.elem_coef], dtype=np.int64)
         self.etype = T.etype[self.elements]
+        # positions of every control variable: vertices, then the face-based points
+        # (given by the mesh, e.g. by a refinement, else the generator's choice below)
+        raw_xyz = np.zeros((self.n_raw, 3))
+        raw_xyz[:V] = xyz
+        fx = mesh.get("face_xyz")
+        if fx is not None:
+            fx = np.asarray(fx, dtype=np.float64).reshape(-1, 3)
+            if len(fx) != 4 * len(enr):
+                raise ValueError("face_xyz holds %d points, the mesh has %d enriched faces"
+                                 % (len(fx), len(enr)))
+            raw_xyz[V:] = fx
+        else:
+            for r, f in enumerate(enr):
+                for c in range(4):
+                    raw_xyz[V + 4 * r + c] = sum(w * xyz[k] for k, w in self.leg(int(f), c).items())
+        self.raw_xyz = raw_xyz
+        self.nets = nets            # active face -> 4 x 4 net (raw id -> weight)
+        self.split_nets = split     # irregular face -> 7 x 7 net after the D-patch treatment
         # control points of the functions
-        P = np.zeros((self.n, 3))
-        for i, k in enumerate(used):
-            if k < V:
-                P[i] = xyz[k]
-            else:
-                r = (k - V) // 4
-                c = (k - V) % 4
-                f = int(enr[r])
-                q = T.quads[f]
-                P[i] = (4 * xyz[q[c]] + 2 * xyz[q[(c + 1) % 4]] + 2 * xyz[q[(c + 3) % 4]]
-                        + xyz[q[(c + 2) % 4]]) / 9.0
+        P = raw_xyz[np.asarray(used, dtype=np.int64)] if used else np.zeros((0, 3))
         self.ctrl = P
         # geometry Bezier nets per element relative to a reference control point
         # (the element's first function): x = ref + sum_j c_j (P_j - ref), the same map
@@ -198,24 +214,28 @@ class Basis:
         if key in self._inner_cache:
             return self._inner_cache[key]
         T = self.topo
-        if T.enriched[f]:
-            out = {self.fdof(f, c): 1.0}
-        else:
-            du, dv = T.span[f]
-            dum, dup = T.cross_span(f, 3), T.cross_span(f, 1)
-            dvm, dvp = T.cross_span(f, 0), T.cross_span(f, 2)
-            su, sv = dum + du + dup, dvm + dv + dvp
-            if su <= 0 or sv <= 0:
-                raise ValueError("degenerate knot spans around face %d" % f)
-            cu, cv = CORNER_UV[c]
-            a = (dum + (du if cu else 0.0)) / su
-            b = (dvm + (dv if cv else 0.0)) / sv
-            q = T.quads[f]
-            out = {}
-            for cc, w in ((0, (1 - a) * (1 - b)), (1, a * (1 - b)), (2, a * b), (3, (1 - a) * b)):
-                if w != 0.0:
-                    out[int(q[cc])] = out.get(int(q[cc]), 0.0) + w
+        out = {self.fdof(f, c): 1.0} if T.enriched[f] else self.leg(f, c)
         self._inner_cache[key] = out
+        return out
+
+    def leg(self, f, c):
+        """B-spline inner Bezier point of face f next to corner c, as weights of its
+        four vertex DOFs: each leg divided in the ratio of the knot spans around it."""
+        T = self.topo
+        du, dv = T.span[f]
+        dum, dup = T.cross_span(f, 3), T.cross_span(f, 1)
+        dvm, dvp = T.cross_span(f, 0), T.cross_span(f, 2)
+        su, sv = dum + du + dup, dvm + dv + dvp
+        if su <= 0 or sv <= 0:
+            raise ValueError("degenerate knot spans around face %d" % f)
+        cu, cv = CORNER_UV[c]
+        a = (dum + (du if cu else 0.0)) / su
+        b = (dvm + (dv if cv else 0.0)) / sv
+        q = T.quads[f]
+        out = {}
+        for cc, w in ((0, (1 - a) * (1 - b)), (1, a * (1 - b)), (2, a * b), (3, (1 - a) * b)):
+            if w != 0.0:
+                out[int(q[cc])] = out.get(int(q[cc]), 0.0) + w
         return out
 
     def edge_point(self, f, k, c):

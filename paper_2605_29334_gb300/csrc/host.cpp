@@ -231,6 +231,24 @@ static inline void dmap(int c, int i, int j, int& x, int& y) {
     }
 }
 
+// B-spline inner Bezier point of face f next to corner c as weights of the face's
+// four corner vertices: the legs are divided in the ratio of the knot spans on
+// either side (Boehm's B-spline-to-Bezier rule).  False on degenerate spans.
+static bool leg_division(const Topology& T, int64_t f, int c, double w[4]) {
+    double du = T.span[f * 2], dv = T.span[f * 2 + 1];
+    double dum = T.cross_span(f, 3), dup = T.cross_span(f, 1);
+    double dvm = T.cross_span(f, 0), dvp = T.cross_span(f, 2);
+    double su = dum + du + dup, sv = dvm + dv + dvp;
+    if (!(su > 0) || !(sv > 0)) return false;
+    double a = (dum + (CU[c] ? du : 0.0)) / su;
+    double b = (dvm + (CV[c] ? dv : 0.0)) / sv;
+    w[0] = (1 - a) * (1 - b);
+    w[1] = a * (1 - b);
+    w[2] = a * b;
+    w[3] = (1 - a) * b;
+    return true;
+}
+
 namespace {
 struct NetBuilder {
     const Topology& T;
@@ -255,18 +273,12 @@ struct NetBuilder {
         if (T.enriched[f]) {
             out.push_back({fdof(f, c), 1.0});
         } else {
-            double du = T.span[f * 2], dv = T.span[f * 2 + 1];
-            double dum = T.cross_span(f, 3), dup = T.cross_span(f, 1);
-            double dvm = T.cross_span(f, 0), dvp = T.cross_span(f, 2);
-            double su = dum + du + dup, sv = dvm + dv + dvp;
-            if (!(su > 0) || !(sv > 0)) {
+            double w[4];
+            if (!leg_division(T, f, c, w)) {
                 err = {WQ_ERR_MESH, "degenerate knot spans around face " + std::to_string(f)};
                 ok = false;
                 return inner_cache[key];
             }
-            double a = (dum + (CU[c] ? du : 0.0)) / su;
-            double b = (dvm + (CV[c] ? dv : 0.0)) / sv;
-            double w[4] = {(1 - a) * (1 - b), a * (1 - b), a * b, (1 - a) * b};
             for (int cc = 0; cc < 4; ++cc)
                 if (w[cc] != 0.0) out.push_back({(int64_t)T.quads[f * 4 + cc], w[cc]});
             lin_normalize(out);
@@ -519,24 +531,43 @@ bool build_basis(const wq_mesh_desc& mesh, BasisHost& B, Error& err) {
             B.fns[B.fn_ptr[e] + a] = (int32_t)(std::lower_bound(used.begin(), used.end(), ekeys[e][a]) - used.begin());
         std::copy(ecoef[e].begin(), ecoef[e].end(), B.coef.begin() + B.coef_ptr[e]);
     }
-    // control points
-    B.ctrl.assign(3 * B.n, 0.0);
-    std::vector<int64_t> enr;
+    // positions of the face-based control points: given, or the B-spline inner
+    // Bezier points of their faces
+    B.enr.clear();
     for (int64_t f = 0; f < F; ++f)
-        if (T.enriched[f]) enr.push_back(f);
+        if (T.enriched[f]) B.enr.push_back((int32_t)f);
+    const size_t n_enr = B.enr.size();
+    if (mesh.face_xyz) {
+        if (mesh.n_face_xyz != (int64_t)(4 * n_enr)) {
+            err = {WQ_ERR_ARG, "face_xyz holds " + std::to_string(mesh.n_face_xyz) + " points, the mesh has " +
+                                   std::to_string(n_enr) + " enriched faces (4 points each)"};
+            return false;
+        }
+        B.face_xyz.assign(mesh.face_xyz, mesh.face_xyz + 12 * n_enr);
+    } else {
+        B.face_xyz.assign(12 * n_enr, 0.0);
+        for (size_t r = 0; r < n_enr; ++r) {
+            const int64_t f = B.enr[r];
+            const int32_t* q = &T.quads[f * 4];
+            for (int c = 0; c < 4; ++c) {
+                double w[4];
+                if (!leg_division(T, f, c, w)) {
+                    err = {WQ_ERR_MESH, "degenerate knot spans around face " + std::to_string(f)};
+                    return false;
+                }
+                for (int cc = 0; cc < 4; ++cc)
+                    for (int d = 0; d < 3; ++d) B.face_xyz[(4 * r + c) * 3 + d] += w[cc] * B.xyz[q[cc] * 3 + d];
+            }
+        }
+    }
+    B.level0.resize(F);
+    for (int64_t f = 0; f < F; ++f) B.level0[f] = mesh.level0_face ? mesh.level0_face[f] : (int32_t)f;
+    // control points of the functions
+    B.ctrl.assign(3 * B.n, 0.0);
     for (int64_t i = 0; i < B.n; ++i) {
         int64_t k = used[i];
-        if (k < T.V) {
-            for (int d = 0; d < 3; ++d) B.ctrl[i * 3 + d] = B.xyz[k * 3 + d];
-        } else {
-            int64_t r = (k - T.V) / 4;
-            int c = (int)((k - T.V) % 4);
-            int64_t f = enr[r];
-            const int32_t* q = &T.quads[f * 4];
-            for (int d = 0; d < 3; ++d)
-                B.ctrl[i * 3 + d] = (4.0 * B.xyz[q[c] * 3 + d] + 2.0 * B.xyz[q[(c + 1) % 4] * 3 + d] +
-                                     2.0 * B.xyz[q[(c + 3) % 4] * 3 + d] + B.xyz[q[(c + 2) % 4] * 3 + d]) / 9.0;
-        }
+        const double* src = k < T.V ? &B.xyz[k * 3] : &B.face_xyz[(k - T.V) * 3];
+        for (int d = 0; d < 3; ++d) B.ctrl[i * 3 + d] = src[d];
     }
     // geometry nets relative to the control point of the element's first function:
     // x = ref + sum_j c_j (P_j - ref) (partition of unity), so that derivatives of the

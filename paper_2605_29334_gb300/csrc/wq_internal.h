@@ -51,6 +51,9 @@ struct BasisHost {
     int64_t n = 0, E = 0, V = 0;
     Topology topo;
     std::vector<double> xyz;            // [V][3]
+    std::vector<int32_t> level0;        // [F] initial-mesh face of every face (the face itself if none given)
+    std::vector<int32_t> enr;           // enriched faces, ascending
+    std::vector<double> face_xyz;       // [enr.size()][4][3] face-based control points
     std::vector<int32_t> elem_face;     // [E]
     std::vector<int8_t> etype;          // [E]
     std::vector<int32_t> nsub;          // [E] 1 or 4

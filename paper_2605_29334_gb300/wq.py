@@ -32,7 +32,8 @@ class WQError(RuntimeError):
 
 class _Mesh(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int64), ("xyz", C.POINTER(C.c_double)),
-                ("n_faces", C.c_int64), ("quads", C.POINTER(C.c_int32)), ("level0_face", C.POINTER(C.c_int32))]
+                ("n_faces", C.c_int64), ("quads", C.POINTER(C.c_int32)), ("level0_face", C.POINTER(C.c_int32)),
+                ("n_face_xyz", C.c_int64), ("face_xyz", C.POINTER(C.c_double))]
 
 
 class BasisInfo(C.Structure):
@@ -166,7 +167,7 @@ class Context:
 
 
 class Basis:
-    """wq_build_basis on a mesh dict {xyz, quads, level0_face, dim}."""
+    """wq_build_basis on a mesh dict {xyz, quads, level0_face, dim, face_xyz (optional)}."""
 
     def __init__(self, ctx, mesh):
         self.ctx = ctx
@@ -174,9 +175,13 @@ class Basis:
         self._quads = np.ascontiguousarray(mesh["quads"], dtype=np.int32)
         l0 = mesh.get("level0_face")
         self._l0 = None if l0 is None else np.ascontiguousarray(l0, dtype=np.int32)
+        fx = mesh.get("face_xyz")
+        self._fx = None if fx is None else np.ascontiguousarray(fx, dtype=np.float64).reshape(-1, 3)
         md = _Mesh(int(mesh.get("dim", 2)), len(self._xyz), self._xyz.ctypes.data_as(C.POINTER(C.c_double)),
                    len(self._quads), self._quads.ctypes.data_as(C.POINTER(C.c_int32)),
-                   None if self._l0 is None else self._l0.ctypes.data_as(C.POINTER(C.c_int32)))
+                   None if self._l0 is None else self._l0.ctypes.data_as(C.POINTER(C.c_int32)),
+                   0 if self._fx is None else len(self._fx),
+                   None if self._fx is None else self._fx.ctypes.data_as(C.POINTER(C.c_double)))
         h = C.c_void_p()
         ctx.check(lib().wq_build_basis(ctx.h, C.byref(md), C.byref(h)))
         self.h = h
