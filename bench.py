@@ -302,6 +302,7 @@ def bench_ours(args, rank, world):
                 "d2h_bytes_per_step": int(nnz * (8 if prec == wq.PREC_F64 else 4))},
         "clocks": clocks,
     }
+    res["refine"] = refine_measure(wq, basis, mesh, flush, max(args.steps // 20, 20), args.warmup, hbm)
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if not args.no_configs:
@@ -446,6 +447,29 @@ def _kernel_source_sha1(name):
     except ValueError:
         return None
     return hashlib.sha1(s.encode()).hexdigest()
+
+
+def refine_measure(wq, basis, mesh, flush, steps, warmup, hbm):
+    """One global refinement of the workload's control mesh (Sec. 3) on the device:
+    knot-insertion stencils for the vertex-based control points, de Casteljau splits of
+    the enriched faces' nets for the face-based ones.  Algorithmic bytes: every coarse
+    control point, stencil entry (4 B index + 8 B weight, 8 B row pointer), job, function
+    id and Bezier coefficient read once, every fine control point written once."""
+    import torch
+    r = wq.Refine(basis)
+    I = r.info
+    x = torch.tensor(np.ascontiguousarray(mesh["xyz"], dtype=np.float64), device="cuda")
+    fx = torch.tensor(basis.face_ctrl(), device="cuda").reshape(-1, 3)
+    xf = torch.empty((I.n_vertices, 3), dtype=torch.float64, device="cuda")
+    ff = torch.empty((I.n_face_xyz, 3), dtype=torch.float64, device="cuda")
+    ms = time_steps(lambda: r.apply(x, fx, out=(xf, ff)), steps, warmup, flush)
+    t = float(np.mean(ms)) / 1e3
+    byts = (24 * (I.n_coarse_vertices + I.n_coarse_face_xyz + I.n_vertices + I.n_face_xyz)
+            + 12 * I.n_stencil + 8 * (I.n_vertices + 1) + 24 * I.n_face_jobs + 4 * I.n_face_fns + 8 * I.n_face_coef)
+    return {"ms": t * 1e3, "coarse_vertices": I.n_coarse_vertices, "fine_vertices": I.n_vertices,
+            "fine_faces": I.n_faces, "fine_face_points": I.n_face_xyz, "face_jobs": I.n_face_jobs,
+            "algorithmic_bytes": byts, "achieved_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm,
+            "launches": 2}
 
 
 def assembly_work(rule, basis, n_terms):

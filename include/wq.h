@@ -87,6 +87,7 @@ typedef struct wq_ctx wq_ctx;
 typedef struct wq_basis wq_basis;
 typedef struct wq_rule wq_rule;
 typedef struct wq_batch wq_batch;
+typedef struct wq_refine wq_refine;
 
 /* Control mesh (host arrays, copied by wq_build_basis).
  *   dim          2 = planar domain (z ignored), 3 = surface in R^3
@@ -178,6 +179,11 @@ wq_status wq_basis_element(const wq_basis* basis, int64_t e, int32_t* face, int3
 /* Host copies: control points [n][3]; pattern row_ptr [n+1], col [nnz]. */
 wq_status wq_basis_ctrl(const wq_basis* basis, double* h_xyz);
 wq_status wq_basis_pattern(const wq_basis* basis, int64_t* h_row_ptr, int32_t* h_col);
+
+/* Positions of the face-based control points, as used by the basis (given in
+ * wq_mesh_desc.face_xyz or placed by the default rule): *n_face_xyz = 4 x the
+ * number of enriched faces; h_face_xyz [n_face_xyz][3] (NULL: count only). */
+wq_status wq_basis_face_ctrl(const wq_basis* basis, int64_t* n_face_xyz, double* h_face_xyz);
 
 /* Min-max point counts (Sec. 4.2, Eq. qp_allocation): side s_e of the s x s
  * grid of every element, h_side [E].  Host only. */
@@ -356,6 +362,74 @@ wq_status wq_rule_kernel_times(wq_rule* rule, int32_t max_calls, float* h_ms, in
  * built; a system needing more than 32 MiB of workspace), WQ_ERR_CUDA,
  * WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE. */
 wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, double* d_w, void* stream);
+
+/* --- global refinement (Sec. 3) ------------------------------------------------ */
+
+typedef struct {
+    int64_t n_vertices;          /* fine mesh vertices */
+    int64_t n_faces;             /* fine mesh faces */
+    int64_t n_face_xyz;          /* fine face-based control points (4 per fine enriched face) */
+    int64_t n_coarse_vertices;   /* the basis's mesh vertices */
+    int64_t n_coarse_face_xyz;   /* its face-based control points */
+    int64_t n_stencil;           /* non-zeros of the vertex stencils */
+    int64_t n_face_jobs;         /* coarse enriched faces (one de Casteljau split each) */
+    int64_t n_face_fns;          /* functions over all of them (control points each job reads) */
+    int64_t n_face_coef;         /* their Bezier coefficients (16 or 64 per function) */
+} wq_refine_info;
+
+/* Plan one global refinement of the basis's control mesh (Sec. 3: the enriched
+ * region keeps its size; vertex-based control points by knot insertion,
+ * face-based ones by de Casteljau's algorithm).  Host work: the fine topology,
+ * the knot-insertion stencil of every fine vertex and the coefficient tables of
+ * the coarse enriched elements; with a device context these are copied to the
+ * device.  The plan does not keep a pointer to the basis.
+ *   Topology: a face is halved in every direction whose knot span is non-zero
+ *   (active faces 2 x 2, faces of the passive ring 1 x 2 along the boundary,
+ *   passive corner faces whole).  Fine vertices: the coarse vertices [0, V),
+ *   then one per split edge in the order the edges are first met scanning faces
+ *   f = 0..F-1 and their edges k = 0..3 (edge k joins corners k and k+1), then one
+ *   per 2 x 2-split face centre in face order.  Fine faces in coarse face order;
+ *   the children of a 2 x 2 split are listed by the coarse corner they contain
+ *   (0, 1, 2, 3), those of a 1 x 2 split by increasing coordinate; each child
+ *   keeps its parent's orientation and initial-mesh face (level0_face, or the
+ *   coarse face index when the basis had none).
+ *   Vertex-based points: the midpoints of the non-zero knot spans are inserted
+ *   along both lines of the tensor chart of the fine vertex's parent (coarse
+ *   vertex, edge or face), the spans beyond the chart being the cross spans of
+ *   the neighbouring faces (0 beyond the boundary); a fine vertex at an EP keeps
+ *   the coarse position (the EP function is eliminated).
+ *   Face-based points: the four children of an enriched face carry the inner
+ *   points of the face's Bezier net split at 1/2 (for a 2 x 2-split irregular
+ *   face, of its sub-nets after the D-patch treatment); fine face-based point
+ *   16 r + 4 k + c is corner c of child k of the r-th coarse enriched face.
+ * Where the coarse geometry is a bicubic spline with the C1 rules of the Bezier
+ * nets (faces without an EP corner) the fine geometry equals the coarse one.
+ * Errors: WQ_ERR_ARG, WQ_ERR_MESH (a boundary vertex without exactly two
+ * boundary edges, an interior valence-4 chart that does not close, a split that
+ * needs a face beyond the boundary), WQ_ERR_OOM, WQ_ERR_CUDA. */
+wq_status wq_refine_create(const wq_basis* basis, wq_refine** out);
+void wq_refine_destroy(wq_refine* r);
+wq_status wq_refine_info_get(const wq_refine* r, wq_refine_info* info);
+
+/* Host copies of the fine topology: h_quads [n_faces][4] (counter-clockwise like
+ * the coarse faces), h_level0_face [n_faces].  NULL arrays are skipped. */
+wq_status wq_refine_mesh(const wq_refine* r, int32_t* h_quads, int32_t* h_level0_face);
+
+/* Host copies of the vertex stencils: fine vertex w = sum over k in
+ * [h_ptr[w], h_ptr[w+1]) of h_w[k] x coarse vertex h_src[k].  h_ptr [n_vertices+1],
+ * h_src / h_w [n_stencil].  NULL arrays are skipped. */
+wq_status wq_refine_stencils(const wq_refine* r, int64_t* h_ptr, int32_t* h_src, double* h_w);
+
+/* Apply the refinement on the device (two kernels on stream, no allocation, no
+ * synchronisation): d_xyz [n_coarse_vertices][3] and d_face_xyz
+ * [n_coarse_face_xyz][3] are the coarse control points (the basis's own, or any
+ * other values: the map is linear), d_xyz_fine [n_vertices][3] and
+ * d_face_xyz_fine [n_face_xyz][3] receive the fine ones, ready for
+ * wq_mesh_desc.xyz / face_xyz of the fine mesh.  All four are device arrays owned
+ * by the caller; the face arrays may be NULL when there is no enriched face.
+ * Errors: WQ_ERR_ARG, WQ_ERR_NO_DEVICE, WQ_ERR_CUDA (launch). */
+wq_status wq_refine_apply(const wq_refine* r, const double* d_xyz, const double* d_face_xyz, double* d_xyz_fine,
+                          double* d_face_xyz_fine, void* stream);
 
 #ifdef __cplusplus
 }

@@ -369,7 +369,7 @@ struct NetBuilder {
 }  // namespace
 
 // counter-clockwise fan (face, corner) around interior vertex v
-static bool fan(const Topology& T, int32_t v, std::vector<std::pair<int32_t, int>>& out, Error& err) {
+bool fan(const Topology& T, int32_t v, std::vector<std::pair<int32_t, int>>& out, Error& err) {
     out.clear();
     int32_t f = T.vf_face[T.vf_ptr[v]];
     int c = T.vf_corner[T.vf_ptr[v]];

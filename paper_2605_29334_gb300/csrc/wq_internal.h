@@ -77,7 +77,30 @@ struct BasisHost {
     int32_t m(int64_t e) const { return (int32_t)(fn_ptr[e + 1] - fn_ptr[e]); }
 };
 
+// One global refinement (Sec. 3): fine topology, knot-insertion stencils of the
+// vertex-based control points, and the coarse enriched elements whose Bezier nets
+// give the face-based control points (refine_host.cpp).
+struct RefineJob {
+    int64_t coef_off;     // element coefficients [m][nsub][4][4] in RefinePlan::coef
+    int32_t fn_off;       // raw control-variable ids of its m functions in RefinePlan::fn_raw
+    int32_t m, nsub;
+    int32_t out;          // first fine face-based point written (16 per job)
+};
+struct RefinePlan {
+    int64_t Vc = 0, n_fx_c = 0;           // coarse vertices, coarse face-based points
+    int64_t Vf = 0, Ff = 0, n_fx_f = 0;   // fine vertices, faces, face-based points
+    std::vector<int32_t> quads, level0;   // fine faces [Ff][4], [Ff]
+    std::vector<int64_t> st_ptr;          // [Vf+1] stencil of every fine vertex
+    std::vector<int32_t> st_src;          // coarse vertex ids
+    std::vector<double> st_w;
+    std::vector<RefineJob> jobs;          // one per coarse enriched face, ascending
+    std::vector<int32_t> fn_raw;
+    std::vector<double> coef;
+};
+
 // Host steps (host.cpp).  Return false and fill err on failure.
+bool fan(const Topology& T, int32_t v, std::vector<std::pair<int32_t, int>>& out, Error& err);
+bool build_refine(const BasisHost& B, RefinePlan& R, Error& err);
 bool build_topology(const wq_mesh_desc& mesh, Topology& T, Error& err);
 bool build_basis(const wq_mesh_desc& mesh, BasisHost& B, Error& err);
 bool point_counts(const BasisHost& B, int mode, std::vector<int32_t>& side, Error& err);

@@ -52,6 +52,12 @@ class RuleInfo(C.Structure):
                 ("tsvd_ms", C.c_double), ("tsvd_gflop", C.c_double)]
 
 
+class RefineInfo(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("n_faces", C.c_int64), ("n_face_xyz", C.c_int64),
+                ("n_coarse_vertices", C.c_int64), ("n_coarse_face_xyz", C.c_int64), ("n_stencil", C.c_int64),
+                ("n_face_jobs", C.c_int64), ("n_face_fns", C.c_int64), ("n_face_coef", C.c_int64)]
+
+
 EXPORTS = {
     "wq_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
     "wq_destroy": (None, [C.c_void_p]),
@@ -96,6 +102,13 @@ EXPORTS = {
     "wq_rule_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_double,
                                    C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p]),
     "wq_rule_kernel_times": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
+    "wq_basis_face_ctrl": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
+    "wq_refine_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "wq_refine_destroy": (None, [C.c_void_p]),
+    "wq_refine_info_get": (C.c_int, [C.c_void_p, C.POINTER(RefineInfo)]),
+    "wq_refine_mesh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "wq_refine_stencils": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "wq_refine_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -216,6 +229,14 @@ class Basis:
         self.ctx.check(lib().wq_basis_functions(self.h, _ptr(out)))
         return out
 
+    def face_ctrl(self):
+        """Face-based control points [4 per enriched face, 3] (wq_basis_face_ctrl)."""
+        n = C.c_int64()
+        self.ctx.check(lib().wq_basis_face_ctrl(self.h, C.byref(n), None))
+        out = np.zeros((n.value, 3))
+        self.ctx.check(lib().wq_basis_face_ctrl(self.h, C.byref(n), _ptr(out)))
+        return out
+
     def point_counts(self, mode=0):
         """Sides of the per-element point grids (wq_count_mode: 0 min-max, 1 Table 2)."""
         side = np.zeros(self.E, dtype=np.int32)
@@ -226,6 +247,73 @@ class Basis:
         if getattr(self, "h", None):
             lib().wq_basis_destroy(self.h)
             self.h = None
+
+
+class Refine:
+    """One global refinement of a basis's control mesh (wq_refine_*)."""
+
+    def __init__(self, basis):
+        self.ctx = basis.ctx
+        self.dim = basis.dim
+        h = C.c_void_p()
+        self.ctx.check(lib().wq_refine_create(basis.h, C.byref(h)))
+        self.h = h
+        info = RefineInfo()
+        self.ctx.check(lib().wq_refine_info_get(h, C.byref(info)))
+        self.info = info
+
+    def mesh(self):
+        """Fine topology: (quads [n_faces, 4] int32, level0_face [n_faces] int32)."""
+        q = np.zeros((self.info.n_faces, 4), dtype=np.int32)
+        l0 = np.zeros(self.info.n_faces, dtype=np.int32)
+        self.ctx.check(lib().wq_refine_mesh(self.h, _ptr(q), _ptr(l0)))
+        return q, l0
+
+    def stencils(self):
+        ptr = np.zeros(self.info.n_vertices + 1, dtype=np.int64)
+        src = np.zeros(self.info.n_stencil, dtype=np.int32)
+        w = np.zeros(self.info.n_stencil)
+        self.ctx.check(lib().wq_refine_stencils(self.h, _ptr(ptr), _ptr(src), _ptr(w)))
+        return ptr, src, w
+
+    def apply(self, xyz, face_xyz, out=None, stream=None):
+        """Coarse control points (CUDA float64 tensors [Vc, 3], [n_coarse_face_xyz, 3]) ->
+        fine ones ([n_vertices, 3], [n_face_xyz, 3]; new tensors unless out = (xyz_fine,
+        face_xyz_fine) is given)."""
+        import torch
+        xyz = xyz.contiguous()
+        face_xyz = face_xyz.contiguous()
+        if out is None:
+            fine = torch.empty((self.info.n_vertices, 3), dtype=torch.float64, device=xyz.device)
+            ffine = torch.empty((self.info.n_face_xyz, 3), dtype=torch.float64, device=xyz.device)
+        else:
+            fine, ffine = out
+        self.ctx.check(lib().wq_refine_apply(self.h, C.c_void_p(xyz.data_ptr()), C.c_void_p(face_xyz.data_ptr()),
+                                             C.c_void_p(fine.data_ptr()), C.c_void_p(ffine.data_ptr()),
+                                             _stream_handle(stream)))
+        return fine, ffine
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().wq_refine_destroy(self.h)
+            self.h = None
+
+
+def refine_mesh(ctx, mesh, levels=1):
+    """Refine a mesh dict ``levels`` times on the device: returns the fine mesh dict
+    (xyz, quads, level0_face, face_xyz, dim) with host arrays."""
+    import torch
+    for _ in range(levels):
+        b = Basis(ctx, mesh)
+        r = Refine(b)
+        x = torch.tensor(np.ascontiguousarray(mesh["xyz"], dtype=np.float64), device="cuda")
+        fx = torch.tensor(b.face_ctrl(), device="cuda").reshape(-1, 3)
+        xf, fxf = r.apply(x, fx)
+        q, l0 = r.mesh()
+        torch.cuda.synchronize()
+        mesh = {"xyz": xf.cpu().numpy(), "quads": q, "level0_face": l0, "face_xyz": fxf.cpu().numpy(),
+                "dim": b.dim}
+    return mesh
 
 
 class Rule:
