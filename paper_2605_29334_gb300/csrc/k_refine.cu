@@ -5,7 +5,8 @@
 // (refine_host.cpp); this file holds the kernels and the wq_refine_* C ABI.
 //
 // k_refine_vertices: one thread per fine vertex, x_w = sum_k w_k x_{src_k} over
-//   its stencil (at most 9 coarse vertices; gathers of 24-byte points).
+//   its stencil (at most 9 coarse vertices, padded to 9 and stored slot-major so
+//   that all of a thread's loads are in flight together; gathers of 24-byte points).
 // k_refine_faces: one block of 64 threads per coarse enriched face.  The block
 //   gathers the coarse control points of the element's functions into shared
 //   memory (64 at a time, all loads in flight together); thread p then contracts
@@ -25,8 +26,7 @@ struct wq_refine {
     int device = -1;
     wqi::RefinePlan plan;
     std::vector<wqi::DevBuf> bufs;
-    int64_t* d_st_ptr = nullptr;
-    int32_t* d_st_src = nullptr;
+    int32_t* d_st_src = nullptr;           // stencils padded to RF_SLOTS, slot-major [RF_SLOTS][Vf]
     double* d_st_w = nullptr;
     wqi::RefineJob* d_jobs = nullptr;
     int32_t* d_fn_raw = nullptr;
@@ -39,19 +39,30 @@ struct wq_refine {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_refine_vertices(int64_t nv, const int64_t* __restrict__ ptr,
-                                                         const int32_t* __restrict__ src,
+constexpr int RF_SLOTS = 9;   // longest stencil: the 3 x 3 vertex rule
+
+// Stencils padded to RF_SLOTS entries (weight 0, source 0), slot-major: entry k of
+// vertex v at k * nv + v, so that a warp reads each slot contiguously and every
+// load of a thread is issued before the first one is used.
+__global__ void __launch_bounds__(256) k_refine_vertices(int64_t nv, const int32_t* __restrict__ src,
                                                          const double* __restrict__ w,
                                                          const double* __restrict__ xyz, double* __restrict__ out) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
+    int32_t s[RF_SLOTS];
+    double c[RF_SLOTS];
+#pragma unroll
+    for (int k = 0; k < RF_SLOTS; ++k) {
+        s[k] = src[k * nv + v];
+        c[k] = w[k * nv + v];
+    }
     double x = 0.0, y = 0.0, z = 0.0;
-    for (int64_t k = ptr[v]; k < ptr[v + 1]; ++k) {
-        const double c = w[k];
-        const double* p = xyz + 3 * (int64_t)src[k];
-        x = fma(c, p[0], x);
-        y = fma(c, p[1], y);
-        z = fma(c, p[2], z);
+#pragma unroll
+    for (int k = 0; k < RF_SLOTS; ++k) {
+        const double* p = xyz + 3 * (int64_t)s[k];
+        x = fma(c[k], p[0], x);
+        y = fma(c[k], p[1], y);
+        z = fma(c[k], p[2], z);
     }
     out[3 * v] = x;
     out[3 * v + 1] = y;
@@ -100,6 +111,7 @@ __global__ void __launch_bounds__(64) k_refine_faces(int64_t n_jobs, const wqi::
         }
         __syncthreads();
         if (t < np) {
+#pragma unroll 8
             for (int a = 0; a < na; ++a) {
                 const double w = c[(int64_t)(a0 + a) * np];
                 x = fma(w, sP[0][a], x);
@@ -199,10 +211,21 @@ wq_status wq_refine_create(const wq_basis* basis, wq_refine** out) {
             return rfail(basis->ctx, WQ_ERR_CUDA, "cudaSetDevice failed");
         }
         const wqi::RefinePlan& P = R->plan;
+        std::vector<int32_t> ell_src((size_t)RF_SLOTS * P.Vf, 0);
+        std::vector<double> ell_w((size_t)RF_SLOTS * P.Vf, 0.0);
+        for (int64_t v = 0; v < P.Vf; ++v) {
+            if (P.st_ptr[v + 1] - P.st_ptr[v] > RF_SLOTS) {
+                delete R;
+                return rfail(basis->ctx, WQ_ERR_MESH, "refinement stencil longer than 9 entries");
+            }
+            for (int64_t k = P.st_ptr[v]; k < P.st_ptr[v + 1]; ++k) {
+                ell_src[(size_t)(k - P.st_ptr[v]) * P.Vf + v] = P.st_src[k];
+                ell_w[(size_t)(k - P.st_ptr[v]) * P.Vf + v] = P.st_w[k];
+            }
+        }
         wq_status s = WQ_OK;
-        if (s == WQ_OK) s = rupload(R, R->d_st_ptr, P.st_ptr);
-        if (s == WQ_OK) s = rupload(R, R->d_st_src, P.st_src);
-        if (s == WQ_OK) s = rupload(R, R->d_st_w, P.st_w);
+        if (s == WQ_OK) s = rupload(R, R->d_st_src, ell_src);
+        if (s == WQ_OK) s = rupload(R, R->d_st_w, ell_w);
         if (s == WQ_OK) s = rupload(R, R->d_jobs, P.jobs);
         if (s == WQ_OK) s = rupload(R, R->d_fn_raw, P.fn_raw);
         if (s == WQ_OK) s = rupload(R, R->d_coef, P.coef);
@@ -259,12 +282,14 @@ wq_status wq_refine_apply(const wq_refine* r, const double* d_xyz, const double*
     const wqi::RefinePlan& P = r->plan;
     if (!d_xyz || !d_xyz_fine || (P.n_fx_c > 0 && (!d_face_xyz || !d_face_xyz_fine)))
         return rfail(r->ctx, WQ_ERR_ARG, "null control-point array");
-    cudaError_t e = cudaSetDevice(r->device);
-    if (e != cudaSuccess) return rfail(r->ctx, WQ_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != r->device) e = cudaSetDevice(r->device);   // no call when already current
+    if (e != cudaSuccess) return rfail(r->ctx, WQ_ERR_CUDA, std::string("device selection: ") + cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
     if (P.Vf > 0) {
         const unsigned g = (unsigned)((P.Vf + 255) / 256);
-        k_refine_vertices<<<g, 256, 0, st>>>(P.Vf, r->d_st_ptr, r->d_st_src, r->d_st_w, d_xyz, d_xyz_fine);
+        k_refine_vertices<<<g, 256, 0, st>>>(P.Vf, r->d_st_src, r->d_st_w, d_xyz, d_xyz_fine);
     }
     const int64_t nj = (int64_t)P.jobs.size();
     if (nj > 0)
