@@ -36,9 +36,11 @@ Steps, in the paper's order:
 
 Parity: steps 1-3 pinned by Table 2 / well-posedness tests; step 5 pinned by
 planted-SVD and full-rank (Eq. w0) special cases and exactness; step 6 by
-"c = 1 gives the Gauss matrix" and zero stiffness row sums (tests/test_oracle_wq.py).
-For non-constant coefficients the WQ matrix itself has no closed form (parity
-unpinned beyond those properties).
+"c = 1 gives the Gauss matrix" and, for any coefficient, by identities that follow
+from x = sum_j P_j N_j and the partition of unity: zero stiffness row sums,
+sum_j M_ij = sum_q w_iq c_q, and sum_j A_ij P_j = sum_q w_iq c_q D x(x_q) for every
+component (tests/test_oracle_wq.py).  For non-constant coefficients the entries
+themselves have no closed form; those identities are their pins.
 """
 from __future__ import annotations
 

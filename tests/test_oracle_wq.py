@@ -7,7 +7,9 @@
   exactness A w = b; KKT (Z^-2 w in range(V_t)); brute force in rationals;
 * assembly: c = 1 gives the Gauss matrix (the exactness constraints, which is
   what Sec. 6 measures to ~1e-12), c = k gives k times it, stiffness row sums
-  vanish for any coefficient, and sum_j M_ij = sum_q w_iq c_q.
+  vanish for any coefficient, sum_j M_ij = sum_q w_iq c_q, and every operator
+  reproduces the coordinates (sum_j A_ij P_j = sum_q w_iq c_q D x(x_q)) for any
+  coefficient.
 """
 import os
 from fractions import Fraction
@@ -147,6 +149,26 @@ def test_assembly_rowsums_and_mass_sums(disk_rule):
         lhs = Mw[R.row_ptr[i]:R.row_ptr[i + 1]].sum()
         rhs = R.weights["N"][R.w_ptr[i]:R.w_ptr[i + 1]] @ kap[q]
         assert abs(lhs - rhs) < 1e-14
+
+
+def test_assembly_linear_reproduction_any_coefficient(disk_rule):
+    """x = sum_j P_j N_j reproduces the coordinates, so for any coefficient c and every
+    component d: sum_j A^d_ij P_j,k = sum_q w^d_iq c_q D_d x_k(x_q), with D_d x_k = delta_dk
+    for the gradient components, 0 for the planar Laplacian and x_k(x_q) for values."""
+    R = disk_rule
+    kap = meshes.kappa_sines(R.x)
+    P = R.basis.ctrl
+    col = R.col
+    for d, g in (("x", (1.0, 0.0)), ("y", (0.0, 1.0)), ("lap", (0.0, 0.0)), ("N", None)):
+        A = R.assemble([(d, kap)])
+        for i in range(0, R.basis.n, 3):
+            s = slice(R.row_ptr[i], R.row_ptr[i + 1])
+            lhs = A[s] @ P[col[s], :2]
+            q = R.row_points(i)
+            wk = R.weights[d][R.w_ptr[i]:R.w_ptr[i + 1]] * kap[q]
+            rhs = wk @ R.x[q, :2] if g is None else wk.sum() * np.array(g)
+            scale = np.abs(R.weights[d][R.w_ptr[i]:R.w_ptr[i + 1]]).sum() * np.max(np.abs(kap)) * (1 + np.max(np.abs(P)))
+            assert np.max(np.abs(lhs - rhs)) <= 1e-11 * scale, (d, i)
 
 
 def test_heat_tangent_is_the_residual_derivative(disk_rule):
