@@ -269,6 +269,10 @@ bool build_refine(const BasisHost& B, RefinePlan& R, Error& err) {
         R.coef.insert(R.coef.end(), B.coef.begin() + B.coef_ptr[e], B.coef.begin() + B.coef_ptr[e + 1]);
         R.jobs.push_back(j);
     }
+    if (R.fn_raw.size() > (size_t)INT32_MAX || R.n_fx_c > INT32_MAX / 4) {
+        err = {WQ_ERR_ARG, "enriched region too large for 32-bit job offsets"};
+        return false;
+    }
     R.n_fx_f = 16 * (int64_t)B.enr.size();
     return true;
 }
