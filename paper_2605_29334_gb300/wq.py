@@ -151,6 +151,22 @@ def _dev_view(ptr, shape, dtype, strides=None, owner=None):
     return torch.as_tensor(_CAI(ptr, shape, typestr, strides, owner), device="cuda")
 
 
+def _need(t, name, dtype, min_numel):
+    """The library reads and writes through raw device pointers with implied sizes:
+    refuse, before the call, a tensor that is not a contiguous CUDA tensor of the
+    expected type holding at least min_numel elements."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, not %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() < min_numel:
+        raise ValueError("%s holds %d elements, %d needed" % (name, t.numel(), min_numel))
+    return t
+
+
 def _stream_handle(stream):
     if stream is None:
         import torch
@@ -288,6 +304,11 @@ class Refine:
             ffine = torch.empty((self.info.n_face_xyz, 3), dtype=torch.float64, device=xyz.device)
         else:
             fine, ffine = out
+        if self.ctx.device >= 0:
+            _need(xyz, "xyz", torch.float64, 3 * self.info.n_coarse_vertices)
+            _need(face_xyz, "face_xyz", torch.float64, 3 * self.info.n_coarse_face_xyz)
+            _need(fine, "xyz_fine", torch.float64, 3 * self.info.n_vertices)
+            _need(ffine, "face_xyz_fine", torch.float64, 3 * self.info.n_face_xyz)
         self.ctx.check(lib().wq_refine_apply(self.h, C.c_void_p(xyz.data_ptr()), C.c_void_p(face_xyz.data_ptr()),
                                              C.c_void_p(fine.data_ptr()), C.c_void_p(ffine.data_ptr()),
                                              _stream_handle(stream)))
@@ -394,10 +415,17 @@ class Rule:
         self.ctx.check(lib().wq_moments(self.h, int(comp), C.c_void_p(out.data_ptr()), _stream_handle(stream)))
         return out
 
+    def _coef_rows(self, op):
+        return 1 + (3 if self.basis_dim == 3 else 2) if int(op) == OP_HEAT_J else 1
+
     def assemble(self, op, coef, alpha=0.0, prec=PREC_F64, out=None, stream=None):
         import torch
+        vt = torch.float64 if prec == PREC_F64 else torch.float32
         if out is None:
-            out = torch.empty(self.nnz, dtype=torch.float64 if prec == PREC_F64 else torch.float32, device="cuda")
+            out = torch.empty(self.nnz, dtype=vt, device="cuda")
+        _need(out, "out", vt, self.nnz)
+        if coef is not None:
+            _need(coef, "coef", torch.float64, self._coef_rows(op) * self.Q)
         cp = C.c_void_p(coef.data_ptr()) if coef is not None else C.c_void_p(0)
         self.ctx.check(lib().wq_assemble(self.h, int(op), cp, float(alpha), int(prec), C.c_void_p(out.data_ptr()),
                                          _stream_handle(stream)))
@@ -405,8 +433,12 @@ class Rule:
 
     def gq_assemble(self, op, coef_gauss, alpha=0.0, prec=PREC_F64, out=None, stream=None):
         import torch
+        vt = torch.float64 if prec == PREC_F64 else torch.float32
         if out is None:
-            out = torch.empty(self.nnz, dtype=torch.float64 if prec == PREC_F64 else torch.float32, device="cuda")
+            out = torch.empty(self.nnz, dtype=vt, device="cuda")
+        _need(out, "out", vt, self.nnz)
+        if coef_gauss is not None:
+            _need(coef_gauss, "coef_gauss", torch.float64, self._coef_rows(op) * self.G)
         cp = C.c_void_p(coef_gauss.data_ptr()) if coef_gauss is not None else C.c_void_p(0)
         self.ctx.check(lib().wq_gq_assemble(self.h, int(op), cp, float(alpha), int(prec),
                                             C.c_void_p(out.data_ptr()), _stream_handle(stream)))
@@ -414,6 +446,7 @@ class Rule:
 
     def interp(self, u, stream=None):
         import torch
+        _need(u, "u", torch.float64, self.n)
         uq = torch.empty(self.Q, dtype=torch.float64, device="cuda")
         gr = torch.empty((self.Q, 3), dtype=torch.float64, device="cuda")
         self.ctx.check(lib().wq_interp(self.h, C.c_void_p(u.data_ptr()), C.c_void_p(uq.data_ptr()),
@@ -426,6 +459,8 @@ class Rule:
         if out is None:
             out = torch.empty(self.n, dtype=torch.float64, device="cuda")
         hc = np.ascontiguousarray(comps, dtype=np.int32)
+        _need(out, "out", torch.float64, self.n)
+        _need(g, "g", torch.float64, len(hc) * self.Q)
         self.ctx.check(lib().wq_apply(self.h, len(hc), _ptr(hc), C.c_void_p(g.data_ptr()), C.c_void_p(out.data_ptr()),
                                       _stream_handle(stream)))
         return out
@@ -439,6 +474,10 @@ class Rule:
             kappa = torch.empty((ng, self.Q) if jacobian else self.Q, dtype=torch.float64, device="cuda")
         if g is None:
             g = torch.empty((ng, self.Q), dtype=torch.float64, device="cuda")
+        _need(u, "u", torch.float64, self.n)
+        _need(u_old, "u_old", torch.float64, self.n)
+        _need(kappa, "kappa", torch.float64, (ng if jacobian else 1) * self.Q)
+        _need(g, "g", torch.float64, ng * self.Q)
         self.ctx.check(lib().wq_heat_fields(self.h, C.c_void_p(u.data_ptr()), C.c_void_p(u_old.data_ptr()),
                                             float(dt), float(k0), float(k2), float(f), int(bool(jacobian)),
                                             C.c_void_p(kappa.data_ptr()), C.c_void_p(g.data_ptr()),
@@ -457,6 +496,8 @@ class Rule:
     def weights_noalloc(self, comp, out, stream=None):
         """Recompute the weights of comp into the caller's device tensor out [sum_r]
         using the library's fixed scratch array (no device allocation)."""
+        import torch
+        _need(out, "out", torch.float64, self.info.sum_r)
         self.ctx.check(lib().wq_rule_weights_noalloc(self.h, int(comp), C.c_void_p(out.data_ptr()),
                                                      _stream_handle(stream)))
         return out
@@ -465,6 +506,9 @@ class Rule:
         """wq_rule_autotune: pick the fastest float mode within tol for (op, gauss) by
         measurement; later calls with prec=PREC_AUTO use it.  Returns {"chosen": mode
         or -1, "err": [TC, F32, F32_FAST], "ms": [...]} (-1: not available / not timed)."""
+        import torch
+        if coef is not None:
+            _need(coef, "coef", torch.float64, self._coef_rows(op) * (self.G if gauss else self.Q))
         chosen = C.c_int32(0)
         err = np.zeros(3, dtype=np.float64)
         ms = np.zeros(3, dtype=np.float32)

@@ -90,3 +90,19 @@ def test_errors_are_status_codes(wq):
     with pytest.raises(wq.WQError) as ei:
         wq.Rule(b)
     assert ei.value.code == wq.WQ_ERR_NO_DEVICE
+
+
+def test_binding_refuses_host_tensors(wq):
+    """The binding checks tensors before the library dereferences their pointers."""
+    import torch
+    r = wq.Rule.__new__(wq.Rule)
+    r.Q, r.G, r.n, r.nnz, r.basis_dim, r.h, r.ctx = 10, 20, 5, 30, 2, None, None
+    host = torch.zeros(30, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        r.assemble(wq.OP_MASS, torch.zeros(10, dtype=torch.float64), out=host)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        r.gq_assemble(wq.OP_MASS, None, out=host)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        r.interp(torch.zeros(5, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        wq._need([1.0], "x", torch.float64, 1)
