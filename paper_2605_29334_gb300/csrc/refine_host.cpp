@@ -23,7 +23,7 @@
 // At an EP (no tensor chart) the fine point keeps the coarse position; the EP
 // function is eliminated at every level, so this value enters no function.
 //
-// Face-based points: for every coarse enriched face, the elements's Bezier
+// Face-based points: for every coarse enriched face, the element's Bezier
 // coefficients and function ids; the device contracts them with the coarse
 // control points into the face's net, splits it at 1/2 (de Casteljau) and
 // writes the inner points of the four children (k_refine.cu).
