@@ -15,6 +15,7 @@ MESHES = {
     "rotated_L0": lambda: meshes.rotated(levels=0),       # faces with several EPs
     "rotated_L1": lambda: meshes.rotated(levels=1),
     "grid": lambda: meshes.grid(4, 3),
+    "grid1x1": lambda: meshes.grid(1, 1),                 # one active element
     "sphere": lambda: meshes.cube_sphere(pre=1, levels=1),
 }
 
