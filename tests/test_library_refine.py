@@ -86,3 +86,16 @@ def test_apply_needs_a_device(wq):
     with pytest.raises(wq.WQError) as ei:
         r.apply(x, f, stream=0)
     assert ei.value.code == wq.WQ_ERR_NO_DEVICE
+
+
+def test_null_arguments_are_status_codes(wq):
+    import ctypes as C
+    L = wq.lib()
+    h = C.c_void_p()
+    assert L.wq_refine_create(None, C.byref(h)) == wq.WQ_ERR_ARG
+    assert L.wq_refine_info_get(None, None) == wq.WQ_ERR_ARG
+    assert L.wq_refine_apply(None, None, None, None, None, None) == wq.WQ_ERR_ARG
+    ctx = wq.Context(-1)
+    r = wq.Refine(wq.Basis(ctx, meshes.disk(mu=5, n=4)))
+    assert L.wq_refine_mesh(r.h, None, None) == wq.WQ_OK          # NULL arrays are skipped
+    assert L.wq_refine_stencils(r.h, None, None, None) == wq.WQ_OK
