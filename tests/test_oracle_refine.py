@@ -199,12 +199,13 @@ def _check_reproduction(coarse, seed):
     return fine, n_exact, n_near, worst_near
 
 
-@pytest.mark.parametrize("name", ["disk5", "disk3", "rotated", "grid"])
+@pytest.mark.parametrize("name", ["disk5", "disk3", "rotated", "grid", "sphere"])
 def test_geometry_reproduced_twice(name):
     m = {"disk5": lambda: meshes.disk(mu=5, n=4),
          "disk3": lambda: meshes.disk(mu=3, n=4),
          "rotated": lambda: meshes.rotated(levels=1),
-         "grid": lambda: meshes.grid(4, 3)}[name]()
+         "grid": lambda: meshes.grid(4, 3),
+         "sphere": lambda: meshes.cube_sphere(pre=1, levels=1)}[name]()     # closed surface, 8 EPs
     coarse = _random_xyz(m, 21)
     fine, n_exact, n_near, worst = _check_reproduction(coarse, 1)
     n_irr = int(Basis(coarse).topo.irregular.sum())
