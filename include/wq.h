@@ -180,9 +180,10 @@ wq_status wq_basis_element(const wq_basis* basis, int64_t e, int32_t* face, int3
 wq_status wq_basis_ctrl(const wq_basis* basis, double* h_xyz);
 wq_status wq_basis_pattern(const wq_basis* basis, int64_t* h_row_ptr, int32_t* h_col);
 
-/* Positions of the face-based control points, as used by the basis (given in
- * wq_mesh_desc.face_xyz or placed by the default rule): *n_face_xyz = 4 x the
- * number of enriched faces; h_face_xyz [n_face_xyz][3] (NULL: count only). */
+/* Positions of the face-based control points (Sec. 3, the extra DOFs of enriched
+ * faces), as used by the basis (given in wq_mesh_desc.face_xyz or placed by the
+ * default rule): *n_face_xyz = 4 x the number of enriched faces; h_face_xyz
+ * [n_face_xyz][3] host, caller-owned (NULL: count only).  Errors: WQ_ERR_ARG. */
 wq_status wq_basis_face_ctrl(const wq_basis* basis, int64_t* n_face_xyz, double* h_face_xyz);
 
 /* Min-max point counts (Sec. 4.2, Eq. qp_allocation): side s_e of the s x s
@@ -408,16 +409,21 @@ typedef struct {
  * boundary edges, an interior valence-4 chart that does not close, a split that
  * needs a face beyond the boundary), WQ_ERR_OOM, WQ_ERR_CUDA. */
 wq_status wq_refine_create(const wq_basis* basis, wq_refine** out);
+/* Frees the plan and its device tables (NULL is ignored). */
 void wq_refine_destroy(wq_refine* r);
+/* Sizes of the plan (wq_refine_info).  Errors: WQ_ERR_ARG (null argument). */
 wq_status wq_refine_info_get(const wq_refine* r, wq_refine_info* info);
 
-/* Host copies of the fine topology: h_quads [n_faces][4] (counter-clockwise like
- * the coarse faces), h_level0_face [n_faces].  NULL arrays are skipped. */
+/* Host copies of the fine topology (Sec. 3 refinement, numbering as described at
+ * wq_refine_create): h_quads [n_faces][4] (counter-clockwise like the coarse
+ * faces), h_level0_face [n_faces]; caller-owned host arrays, NULL ones are
+ * skipped.  Errors: WQ_ERR_ARG (null plan). */
 wq_status wq_refine_mesh(const wq_refine* r, int32_t* h_quads, int32_t* h_level0_face);
 
-/* Host copies of the vertex stencils: fine vertex w = sum over k in
- * [h_ptr[w], h_ptr[w+1]) of h_w[k] x coarse vertex h_src[k].  h_ptr [n_vertices+1],
- * h_src / h_w [n_stencil].  NULL arrays are skipped. */
+/* Host copies of the knot-insertion stencils (Sec. 3): fine vertex w = sum over k
+ * in [h_ptr[w], h_ptr[w+1]) of h_w[k] x coarse vertex h_src[k].  h_ptr
+ * [n_vertices+1], h_src / h_w [n_stencil]; caller-owned host arrays, NULL ones are
+ * skipped.  Errors: WQ_ERR_ARG (null plan). */
 wq_status wq_refine_stencils(const wq_refine* r, int64_t* h_ptr, int32_t* h_src, double* h_w);
 
 /* Apply the refinement on the device (two kernels on stream, no allocation, no
