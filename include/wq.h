@@ -152,9 +152,14 @@ typedef struct {
 
 /* device >= 0: bind the context to that CUDA device.  device = -1: host-only
  * context (basis construction and host queries; rule builds return
- * WQ_ERR_NO_DEVICE).  *out receives the handle. */
+ * WQ_ERR_NO_DEVICE).  *out receives the handle, owned by the caller until
+ * wq_destroy.  Errors: WQ_ERR_ARG (null out), WQ_ERR_NO_DEVICE (no such device),
+ * WQ_ERR_CUDA (cudaSetDevice failed), WQ_ERR_OOM (host allocation). */
 wq_status wq_create(int device, wq_ctx** out);
+/* Frees the context (NULL is ignored). */
 void wq_destroy(wq_ctx* ctx);
+/* Message of the last failed call on ctx ("null context" for NULL); the string
+ * belongs to ctx and stays valid until the next call on it. */
 const char* wq_last_error(const wq_ctx* ctx);
 
 /* --- spline space (host, Sec. 3) ------------------------------------------ */
@@ -165,18 +170,24 @@ const char* wq_last_error(const wq_ctx* ctx);
  * Sec. 3 / Fig. 2) and the exactness-set pattern (Eq. 10).  Host only.
  * Errors: WQ_ERR_ARG (null/size), WQ_ERR_MESH (assumptions violated). */
 wq_status wq_build_basis(wq_ctx* ctx, const wq_mesh_desc* mesh, wq_basis** out);
+/* Frees the basis (NULL is ignored); rules built on it must be destroyed first. */
 void wq_basis_destroy(wq_basis* basis);
+/* Sizes and Table 1-style counts of the space (wq_basis_info).  Errors: WQ_ERR_ARG. */
 wq_status wq_basis_info_get(const wq_basis* basis, wq_basis_info* info);
 
 /* Element e (0 <= e < E) as host arrays: its face id, type (wq_basis_info order),
  * m (functions), nsub (1 or 4); fns [m] function ids ascending; coef
  * [m][nsub][4][4] Bernstein coefficients (index i along corner0->corner1,
- * j along corner0->corner3; sub-element s = su + 2 sv).  Pass NULL for arrays
- * not wanted; call once with NULL arrays to learn m and nsub. */
+ * j along corner0->corner3; sub-element s = su + 2 sv; the Bezier form of Sec. 3
+ * / Fig. 2).  Pass NULL for arrays not wanted; call once with NULL arrays to learn
+ * m and nsub.  Host arrays, caller-owned.  Errors: WQ_ERR_ARG (null basis, e out
+ * of range). */
 wq_status wq_basis_element(const wq_basis* basis, int64_t e, int32_t* face, int32_t* type,
                            int32_t* m, int32_t* nsub, int32_t* h_fns, double* h_coef);
 
-/* Host copies: control points [n][3]; pattern row_ptr [n+1], col [nnz]. */
+/* Host copies (caller-owned arrays): control points of the functions [n][3]
+ * (x = sum_j P_j N_j, Sec. 3); the exactness-set pattern (Eq. 10) row_ptr [n+1],
+ * col [nnz] (NULL arrays skipped).  Errors: WQ_ERR_ARG (null basis; null h_xyz). */
 wq_status wq_basis_ctrl(const wq_basis* basis, double* h_xyz);
 wq_status wq_basis_pattern(const wq_basis* basis, int64_t* h_row_ptr, int32_t* h_col);
 
@@ -186,8 +197,10 @@ wq_status wq_basis_pattern(const wq_basis* basis, int64_t* h_row_ptr, int32_t* h
  * [n_face_xyz][3] host, caller-owned (NULL: count only).  Errors: WQ_ERR_ARG. */
 wq_status wq_basis_face_ctrl(const wq_basis* basis, int64_t* n_face_xyz, double* h_face_xyz);
 
-/* Min-max point counts (Sec. 4.2, Eq. qp_allocation): side s_e of the s x s
- * grid of every element, h_side [E].  Host only. */
+/* Min-max point counts (Sec. 4.2, Eq. qp_allocation), or Table 2's fixed counts
+ * (count_mode): side s_e of the s x s grid of every element, h_side [E] (host,
+ * caller-owned).  Host only.  Errors: WQ_ERR_ARG (null argument, unknown mode),
+ * WQ_ERR_ILLPOSED (r_i < n_i after the repair). */
 wq_status wq_point_counts(const wq_basis* basis, int32_t count_mode, int32_t* h_side);
 
 /* --- quadrature rule (device, Sec. 4) ---------------------------------------- */
@@ -199,33 +212,41 @@ wq_status wq_point_counts(const wq_basis* basis, int32_t count_mode, int32_t* h_
  * Errors: WQ_ERR_NO_DEVICE, WQ_ERR_OOM, WQ_ERR_CUDA, WQ_ERR_ILLPOSED,
  * WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE. */
 wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out);
+/* Frees the rule and its device arrays (NULL is ignored). */
 void wq_rule_destroy(wq_rule* rule);
+/* Sizes and weight statistics (wq_rule_info).  Errors: WQ_ERR_ARG. */
 wq_status wq_rule_info_get(const wq_rule* rule, wq_rule_info* info);
 
-/* Device views: WQ point coordinates [Q][3] (caller evaluates c(x_q) there),
- * Gauss point coordinates [G][3]. */
+/* Device views owned by the rule: WQ point coordinates [Q][3] (Sec. 4.1; the
+ * caller evaluates c(x_q) there), Gauss point coordinates [G][3].  Errors:
+ * WQ_ERR_ARG (null rule). */
 wq_status wq_rule_points(const wq_rule* rule, const double** d_x, int64_t* n_points);
 wq_status wq_rule_gauss_points(const wq_rule* rule, const double** d_x, int64_t* n_gauss);
 
-/* Device view of the CSR pattern (int32 row_ptr [n+1], col [nnz]). */
+/* Device view, owned by the rule, of the CSR pattern S_i (Eq. 10; int32 row_ptr
+ * [n+1], col [nnz]).  Errors: WQ_ERR_ARG (null rule). */
 wq_status wq_pattern(const wq_rule* rule, int64_t* n, int64_t* nnz,
                      const int32_t** d_row_ptr, const int32_t** d_col);
 
 /* Device view of the weights of component comp: w [sum_r], with row i's
  * weights at [w_ptr[i], w_ptr[i+1]) ordered by support element (ascending) then
- * by point (u fastest); w_ptr int64 [n+1]. */
+ * by point (u fastest); w_ptr int64 [n+1] (Sec. 4.3 truncated-SVD weights; owned
+ * by the rule).  Errors: WQ_ERR_ARG (component not built). */
 wq_status wq_rule_weights(const wq_rule* rule, int32_t comp, const double** d_w, const int64_t** d_w_ptr);
 
 /* Device view of the point tables (Sec. 4.1 evaluation): gauss = 0 for the WQ
  * points, 1 for the Gauss points.  Element e's block starts at table +
  * off[e] and is laid out [point][comp][m_e] with comp = N, d_x, d_y, (d_z),
  * lap (ncomp = dim + 2); points of e are [pt_ptr[e], pt_ptr[e+1]); Gauss
- * weights (w_g times the area element) d_gw [G] (gauss = 1 only). */
+ * weights (w_g times the area element) d_gw [G] (gauss = 1 only).  Owned by the
+ * rule.  Errors: WQ_ERR_ARG (null rule). */
 wq_status wq_rule_table(const wq_rule* rule, int32_t gauss, const double** d_table, const int64_t** d_off,
                         const int64_t** d_pt_ptr, const double** d_gw, int32_t* ncomp);
 
 /* Device copy of the Gauss component matrix G^c (c = 1), the moments b of
- * component comp (Sec. 2, "entries of b are precomputed"), into d_vals [nnz]. */
+ * component comp (Sec. 2: b precomputed), into the caller's d_vals [nnz]
+ * (asynchronous on stream).  Errors: WQ_ERR_ARG (component not built, null
+ * d_vals), WQ_ERR_CUDA. */
 wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* stream);
 
 /* WQ assembly (Eqs. 9, 11, 12, S):
@@ -236,23 +257,29 @@ wq_status wq_moments(const wq_rule* rule, int32_t comp, double* d_vals, void* st
  * No allocation, no host synchronisation; asynchronous on stream.  The FP32
  * modes launch two kernels (element blocks, then per-entry sums) through a
  * rule-owned slot buffer, so FP32 assemblies on one rule must not overlap on the
- * GPU.  Errors: WQ_ERR_ARG (op not built into this rule, bad precision). */
+ * GPU.  Errors: WQ_ERR_ARG (null rule or d_vals, op not built into this rule,
+ * unknown precision, WQ_PREC_TC on a rule with more than 64 points in an
+ * element), WQ_ERR_CUDA (launch). */
 wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha,
                       int32_t prec, void* d_vals, void* stream);
 
 /* Same operator by element-wise 4x4 Gauss quadrature (the paper's reference,
  * Table 2 right column), coefficient at the Gauss points d_coef [G] (rows of G
- * for WQ_OP_HEAT_J). */
+ * for WQ_OP_HEAT_J); layout, ownership and errors as wq_assemble. */
 wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, double alpha,
                          int32_t prec, void* d_vals, void* stream);
 
-/* u_h and grad u_h at the WQ points (Sec. 5): d_u [n] -> d_uq [Q], d_grad [Q][3]. */
+/* u_h and grad u_h at the WQ points (Sec. 5): d_u [n] -> d_uq [Q], d_grad [Q][3]
+ * (caller-owned device arrays; asynchronous on stream).  Errors: WQ_ERR_ARG (null
+ * rule, d_u or d_uq), WQ_ERR_CUDA. */
 wq_status wq_interp(const wq_rule* rule, const double* d_u, double* d_uq, double* d_grad, void* stream);
 
 /* Matrix-free WQ functional (the residual form of Sec. 5; NEXT: operator apply):
  *   y_i = sum_t sum_{q in pts(supp N_i)} w^{comps[t]}_iq * g_t(x_q)
  * h_comps [n_terms] (host, wq_comp, 1 <= n_terms <= 4); d_g [n_terms][Q] point
- * data (term-major); d_y [n].  No allocation; asynchronous on stream. */
+ * data (term-major); d_y [n] (caller-owned device arrays).  No allocation;
+ * asynchronous on stream.  Errors: WQ_ERR_ARG (null pointer, n_terms outside
+ * 1..4, a component not built), WQ_ERR_CUDA. */
 wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps, const double* d_g, double* d_y,
                    void* stream);
 
@@ -262,13 +289,15 @@ wq_status wq_apply(const wq_rule* rule, int32_t n_terms, const int32_t* h_comps,
  * g_{1+d} = kappa d_d u, so that wq_apply(N, x, y[, z]) gives the residual R_A
  * of Eq. heat_residual_discrete.  With jacobian != 0, d_kappa is [1 + dim][Q]
  * and rows 1 + d hold k'(u) d_d u = 2 k2 u d_d u: the coefficient rows of
- * WQ_OP_HEAT_J.  No allocation; asynchronous on stream. */
+ * WQ_OP_HEAT_J.  Caller-owned device arrays; no allocation; asynchronous on
+ * stream.  Errors: WQ_ERR_ARG (null pointer, dt <= 0), WQ_ERR_CUDA. */
 wq_status wq_heat_fields(const wq_rule* rule, const double* d_u, const double* d_u_old, double dt, double k0,
                          double k2, double f, int32_t jacobian, double* d_kappa, double* d_g, void* stream);
 
 /* Control-variable id of every function (host) [n]: < n_vertices: the vertex
  * of a vertex-based function; otherwise n_vertices + 4 * (rank of the enriched
- * face) + corner for a face-based function. */
+ * face) + corner for a face-based function (the control variables of Sec. 3).
+ * Host array, caller-owned.  Errors: WQ_ERR_ARG. */
 wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
 
 /* Host-buffer round trip for end-to-end use: copies h_coef [Q] to the device,
@@ -278,7 +307,8 @@ wq_status wq_basis_functions(const wq_basis* basis, int64_t* h_raw_ids);
  * addressing), the per-entry sums write it directly over the host link, 8 or 16
  * bytes per store where h_vals is so aligned; otherwise the values go through a
  * library-owned device buffer and one copy.  Operators with one coefficient row
- * only (not WQ_OP_HEAT_J). */
+ * only (not WQ_OP_HEAT_J); the operators of Eqs. 9, 11, 12, S.  Errors: those of
+ * wq_assemble, WQ_ERR_ARG for WQ_OP_HEAT_J, WQ_ERR_CUDA (copies). */
 wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef, double alpha,
                            int32_t prec, void* h_vals, void* stream);
 
@@ -297,6 +327,7 @@ wq_status wq_assemble_host(const wq_rule* rule, int32_t op, const double* h_coef
  * WQ_ERR_ARG (k out of range, mixed rules, null output, operator not built),
  * WQ_ERR_OOM, WQ_ERR_CUDA. */
 wq_status wq_batch_create(int32_t k, const wq_rule* const* rules, wq_batch** out);
+/* Frees the batch plan (NULL is ignored); the rules stay. */
 void wq_batch_destroy(wq_batch* batch);
 wq_status wq_assemble_batched(const wq_batch* batch, int32_t op, const void* const* h_coefs, double alpha,
                               int32_t prec, void* const* h_vals, void* stream);
