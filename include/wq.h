@@ -77,6 +77,17 @@ typedef enum {
                              (WQ_PREC_F32 until it has run); float values */
 } wq_prec;
 
+/* Kernels of the float modes (WQ_PREC_F32, WQ_PREC_F32_FAST), all with the same
+ * arithmetic per element block and the same per-entry sum order: the tile engine stages
+ * each 16 x 16 element block's data by bulk copies, in chunks of up to 12 points for
+ * operators of one or two terms (TILE12; 8 / 4 points for 3-4 / 5-8 terms, the chunks of
+ * SLOTMAP, so the values are bitwise those of SLOTMAP) or up to 16 points (TILE16; one
+ * chunk per block for 4 x 4 points, so other extraction constants and values within the
+ * FP32 rounding of TILE12's), then sums each CSR row from a row-major slot layout;
+ * SLOTMAP is the earlier kernel pair (per-lane staged copies, blocks scattered through a
+ * slot map, per-entry sums). */
+typedef enum { WQ_VARIANT_TILE12 = 0, WQ_VARIANT_TILE16 = 1, WQ_VARIANT_SLOTMAP = 2 } wq_variant;
+
 /* Point-count rule (Sec. 4.2). */
 /* Per-element point counts (Sec. 4.2): the min-max rule of eq. qp_allocation, or
  * Table 2's fixed values by element type (3 x 3 / 4 x 4 near high-valence or
@@ -359,18 +370,38 @@ wq_status wq_rule_set_timing(wq_rule* rule, int32_t capacity);
 /* Kernel choice by measurement (autotuner; no counterpart in the paper).  For
  * operator op on this rule (gauss = 0: WQ assembly, 1: Gauss assembly) and the
  * coefficient d_coef (as for wq_assemble / wq_gq_assemble): assembles once in FP64
- * and once in each float mode (WQ_PREC_TC, WQ_PREC_F32, WQ_PREC_F32_FAST),
- * measures each mode's normwise error max|A - A_64| / max|A_64|, times the modes
- * within tol on the device (CUDA events on stream; two warm-ups, then `reps`
- * assemblies, no cache flush), and records the fastest of them as the rule's
- * WQ_PREC_AUTO choice for (op, gauss).  *chosen = that mode, or -1 when no float
- * mode is within tol (WQ_PREC_AUTO then stays WQ_PREC_F32).  h_err[3] and h_ms[3]
- * (optional) receive the errors and the mean times in the order TC, F32, F32_FAST
- * (a mode not available for this rule or operator: error -1; not timed: time -1).
+ * and once with each candidate -- the tensor-core slices (WQ_PREC_TC), and WQ_PREC_F32
+ * and WQ_PREC_F32_FAST each with every kernel variant (wq_variant) -- measures each
+ * candidate's normwise error max|A - A_64| / max|A_64|, times the candidates within
+ * tol on the device (CUDA events on stream; two warm-ups, then `reps` assemblies, no
+ * cache flush), and records the fastest as the rule's WQ_PREC_AUTO choice for
+ * (op, gauss) together with its variant (the variant the float modes then use, unless
+ * wq_rule_set_variant overrides it).  *chosen = that mode, or -1 when no candidate is
+ * within tol (WQ_PREC_AUTO then stays WQ_PREC_F32 with WQ_VARIANT_SLOTMAP).  h_err[3]
+ * and h_ms[3] (optional) receive, per mode in the order TC, F32, F32_FAST, the error and
+ * the mean time of its fastest variant (error -1: the mode is not available for this
+ * rule or operator; time -1: not timed); wq_rule_autotune_report gives every candidate.
  * Allocates temporary device buffers and synchronises stream.  Errors: WQ_ERR_ARG,
  * WQ_ERR_OOM, WQ_ERR_CUDA. */
 wq_status wq_rule_autotune(wq_rule* rule, int32_t op, const void* d_coef, double alpha, int32_t gauss, double tol,
                            int32_t reps, void* stream, int32_t* chosen, double* h_err, float* h_ms);
+
+/* Kernel variant (wq_variant) of the float modes for operator op (gauss = 0: WQ
+ * assembly, 1: Gauss assembly): variant -1 returns to the autotuner's choice
+ * (WQ_VARIANT_TILE12 until wq_rule_autotune has run).  Host-side setting, no device
+ * work.  Errors: WQ_ERR_ARG (bad op / gauss / variant; a tile variant on a rule whose
+ * elements exceed the tile engine's limits: more than 240 functions or 255 points). */
+wq_status wq_rule_set_variant(wq_rule* rule, int32_t op, int32_t gauss, int32_t variant);
+/* The variant the float modes use now for (op, gauss).  Errors: WQ_ERR_ARG. */
+wq_status wq_rule_get_variant(const wq_rule* rule, int32_t op, int32_t gauss, int32_t* variant);
+
+/* Candidates of the last wq_rule_autotune for (op, gauss): *n = their number (0 before
+ * any), and for the first `capacity` of them the mode (wq_prec), the kernel variant
+ * (wq_variant; -1 for WQ_PREC_TC), the normwise error against FP64 (-1: not
+ * available) and the mean time in ms (-1: not timed, its error above tol).  Host arrays,
+ * caller-owned; NULL ones are skipped.  Errors: WQ_ERR_ARG. */
+wq_status wq_rule_autotune_report(const wq_rule* rule, int32_t op, int32_t gauss, int32_t capacity, int32_t* n,
+                                  int32_t* h_mode, int32_t* h_variant, double* h_err, float* h_ms);
 
 /* Durations of the recorded calls in call order: h_ms[2k] and h_ms[2k + 1] are
  * the first and second kernel of call k (milliseconds); *n_calls = number of

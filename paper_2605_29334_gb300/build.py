@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libwq.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 
-CU_SOURCES = ["api.cu", "k_eval.cu", "k_assemble.cu", "k_tc.cu", "k_tsvd.cu", "noalloc.cu", "k_refine.cu"]
+CU_SOURCES = ["api.cu", "k_eval.cu", "k_assemble.cu", "k_tile.cu", "k_tc.cu", "k_tsvd.cu", "noalloc.cu", "k_refine.cu"]
 CPP_SOURCES = ["host.cpp", "refine_host.cpp"]
 HEADERS = ["wq_internal.h", "dev.cuh", "kernels.h", "rule.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -116,6 +116,50 @@ bool op_terms(const wq_rule* R, int op, double alpha, bool need_weights, wqd::Te
     }
 }
 
+// Terms of the tile kernels (k_tile.cu) from an operator's terms: test components
+// (weight columns for WQ, table components of the Gauss test pack) and trial table
+// components as indices into the staged ranges.  False if a range is wider than the
+// kernel stages (min(terms, 4) components per side).
+bool tile_terms(const wqd::Terms& tm, bool gauss, wqd::TileTerms& tt) {
+    const int ntk = tm.nt <= 4 ? tm.nt : 8;
+    const int cm = ntk < 4 ? ntk : 4;
+    int slo = 1 << 20, shi = -1, rlo = 1 << 20, rhi = -1;
+    for (int t = 0; t < tm.nt; ++t) {
+        const int sc = gauss ? tm.t[t].sc : tm.t[t].wc, rc = tm.t[t].tc;
+        slo = std::min(slo, sc);
+        shi = std::max(shi, sc);
+        rlo = std::min(rlo, rc);
+        rhi = std::max(rhi, rc);
+    }
+    if (tm.nt < 1 || shi - slo + 1 > cm || rhi - rlo + 1 > cm) return false;
+    tt = wqd::TileTerms{};
+    tt.nt = tm.nt;
+    tt.s_lo = slo;
+    tt.s_n = shi - slo + 1;
+    tt.r_lo = rlo;
+    tt.r_n = rhi - rlo + 1;
+    tt.cstride = tm.cstride;
+    tt.ncrow = 0;
+    for (int t = 0; t < ntk; ++t) {
+        const bool real = t < tm.nt;
+        tt.tcomp[t] = real ? (gauss ? tm.t[t].sc : tm.t[t].wc) - slo : 0;
+        tt.rcomp[t] = real ? tm.t[t].tc - rlo : 0;
+        tt.crow[t] = real ? tm.t[t].crow : -1;
+        const double sc = real ? tm.t[t].scale : 0.0;   // padding terms contribute zero
+        tt.shi[t] = (float)sc;
+        tt.slo[t] = (float)(sc - (double)tt.shi[t]);
+        tt.ncrow = std::max(tt.ncrow, tt.crow[t] + 1);
+    }
+    return tt.ncrow <= 4;
+}
+
+// Kernel variant of the float modes for (op, gauss): wq_rule_set_variant's, else the
+// autotuner's choice (WQ_VARIANT_TILE12 until it has run).
+int float_variant(const wq_rule* R, int op, int gauss) {
+    const int v = R->set_var[op][gauss];
+    return v >= 0 ? v : R->auto_var[op][gauss];
+}
+
 }  // namespace
 
 
@@ -486,6 +530,76 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
             }
     }
     R->kscr_len = kptr[E];
+    // tile engine (k_tile.cu): element-major packs [component][point][16-row block][16]
+    // per element (WQ test = split weights, WQ trial = split table, Gauss test = Gauss
+    // weight x table, Gauss trial = split Gauss table), 16 x 16 tiles of every element
+    // block (elements with more points and column blocks first), and the per-row sum plan
+    std::vector<int32_t> Pw(E), Pg(E), rowslot(n + 1, 0), kdst(B.fn_ptr[E], 0);
+    std::vector<uint16_t> pos2;
+    std::vector<int64_t> sw_off(E + 1, 0), tw_off(E + 1, 0), sg_off(E + 1, 0), tg_off(E + 1, 0);
+    std::vector<int4> ti_wq, ti_gq, tm_wq, tm_gq;
+    std::vector<int64_t> tmx_off(E + 1, 0);
+    R->tile_ok = true;
+    for (int64_t e = 0; e < E; ++e) {
+        const int ncb = (m[e] + 15) / 16;
+        Pw[e] = side[e] * side[e];
+        Pg[e] = 16 * nsub[e];
+        if (ncb > 15 || Pw[e] > 255 || Pg[e] > 255) R->tile_ok = false;
+        sw_off[e + 1] = sw_off[e] + (int64_t)R->nwc * Pw[e] * ncb * 16;
+        tw_off[e + 1] = tw_off[e] + (int64_t)nc * Pw[e] * ncb * 16;
+        sg_off[e + 1] = sg_off[e] + (int64_t)nc * Pg[e] * ncb * 16;
+        tg_off[e + 1] = tg_off[e] + (int64_t)nc * Pg[e] * ncb * 16;
+        tmx_off[e + 1] = tmx_off[e] + (int64_t)nc * ncb;
+    }
+    if (std::max({sw_off[E], tw_off[E], sg_off[E], tg_off[E]}) > INT32_MAX) R->tile_ok = false;
+    // row-major slot layout of the element blocks: row i's support entries in support
+    // order, each ceil(m_e / 16) blocks of 16 slots; the slot block of (row i, element e)
+    // receives element e's block row of function i (kdst), pos2 the positions in row i
+    {
+        int64_t ns = 0;
+        for (int64_t i = 0; i < n && R->tile_ok; ++i) {
+            rowslot[i] = (int32_t)ns;
+            for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) ns += 16 * ((m[B.supp[s]] + 15) / 16);
+            if (ns > INT32_MAX) R->tile_ok = false;
+        }
+        rowslot[n] = (int32_t)ns;
+        R->kslot_len = ns;
+        if (R->tile_ok) {
+            pos2.assign((size_t)ns, (uint16_t)0xFFFF);
+            for (int64_t i = 0; i < n; ++i) {
+                int64_t x = rowslot[i];
+                for (int64_t s = B.supp_ptr[i]; s < B.supp_ptr[i + 1]; ++s) {
+                    const int32_t e = B.supp[s];
+                    kdst[B.fn_ptr[e] + il[s]] = (int32_t)x;
+                    for (int b = 0; b < m[e]; ++b) pos2[x + b] = pos[pos_ptr[s] + b];
+                    x += 16 * ((m[e] + 15) / 16);
+                }
+            }
+        }
+    }
+    if (R->tile_ok) {
+        auto make_tiles = [&](bool gauss, std::vector<int4>& item, std::vector<int4>& meta) {
+            const std::vector<int32_t>& P = gauss ? Pg : Pw;
+            std::vector<int32_t> ord(E);
+            for (int64_t e = 0; e < E; ++e) ord[e] = (int32_t)e;
+            std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+                const int cx = (m[x] + 15) / 16, cy = (m[y] + 15) / 16;
+                return (int64_t)P[x] * cx * cx > (int64_t)P[y] * cy * cy;
+            });
+            for (int32_t e : ord) {
+                const int ncb = (m[e] + 15) / 16;
+                for (int ta = 0; ta < ncb; ++ta)
+                    for (int tb = 0; tb < ncb; ++tb) {
+                        item.push_back(make_int4((int)(gauss ? sg_off[e] : sw_off[e]), (int)(gauss ? tg_off[e] : tw_off[e]),
+                                                 (int)(gauss ? gp_ptr[e] : pt_ptr[e]), (int)B.fn_ptr[e]));
+                        meta.push_back(make_int4(m[e] | P[e] << 8 | ta << 16 | tb << 20 | ncb << 24, 0,
+                                                 (int)tmx_off[e], 0));
+                    }
+            }
+        };
+        make_tiles(false, ti_wq, tm_wq);
+        make_tiles(true, ti_gq, tm_gq);
+    }
     std::vector<int32_t> row_ptr32(n + 1);
     for (int64_t i = 0; i <= n; ++i) row_ptr32[i] = (int32_t)B.row_ptr[i];
     if (B.row_ptr[n] > INT32_MAX) return bail(fail(ctx, WQ_ERR_ARG, "nnz exceeds 32-bit row pointers"));
@@ -512,6 +626,22 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         !upload(R, R->d_tcel_gq, tcel_gq, sst) || !upload(R, R->d_bsp_wq, bsp_wq, sst) ||
         !upload(R, R->d_bsp_gq, bsp_gq, sst) || !upload(R, R->d_it2_wq, it2_wq, sst) ||
         !upload(R, R->d_it2_gq, it2_gq, sst))
+        return bail(sst);
+    int32_t *d_Pw = nullptr, *d_Pg = nullptr;
+    int64_t *d_sw_off = nullptr, *d_tw_off = nullptr, *d_sg_off = nullptr, *d_tg_off = nullptr, *d_wbase = nullptr;
+    int64_t* d_tmx_off = nullptr;
+    if (R->tile_ok &&
+        (!upload(R, R->d_ti_wq, ti_wq, sst) || !upload(R, R->d_tm_wq, tm_wq, sst) ||
+         !upload(R, R->d_ti_gq, ti_gq, sst) || !upload(R, R->d_tm_gq, tm_gq, sst) ||
+         !upload(R, R->d_rowslot, rowslot, sst) || !upload(R, R->d_kdst, kdst, sst) ||
+         !upload(R, R->d_pos2, pos2, sst) || !dalloc(R, R->d_kslot, (size_t)std::max<int64_t>(R->kslot_len, 1), sst) ||
+         !upload(R, d_Pw, Pw, sst) || !upload(R, d_Pg, Pg, sst) || !upload(R, d_sw_off, sw_off, sst) ||
+         !upload(R, d_tw_off, tw_off, sst) || !upload(R, d_sg_off, sg_off, sst) || !upload(R, d_tg_off, tg_off, sst) ||
+         !upload(R, d_wbase, wbase, sst) || !upload(R, d_tmx_off, tmx_off, sst) ||
+         !dalloc(R, R->d_tmx_wq, (size_t)tmx_off[E], sst) || !dalloc(R, R->d_tmx_gq, (size_t)tmx_off[E], sst) ||
+         !dalloc(R, R->d_pk_sw, (size_t)sw_off[E], sst) ||
+         !dalloc(R, R->d_pk_tw, (size_t)tw_off[E], sst) || !dalloc(R, R->d_pk_sg, (size_t)sg_off[E], sst) ||
+         !dalloc(R, R->d_pk_tg, (size_t)tg_off[E], sst)))
         return bail(sst);
     if (R->tc_ok &&
         (!dalloc(R, R->d_bs_wq, (size_t)bsp_wq[E], sst) || !dalloc(R, R->d_bs_gq, (size_t)bsp_gq[E], sst) ||
@@ -589,6 +719,15 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     R->tit_gq = {(int64_t)it_gq.size(), R->d_it_gq, R->d_kb_gq, R->d_it2_gq, R->n_sm};
     R->h_it_wq = it_wq;
     R->h_kb_wq = kb_wq;
+    if (R->tile_ok) {
+        R->tj_wq = {(int64_t)ti_wq.size(), R->d_ti_wq, R->d_tm_wq, {R->d_pk_sw, R->d_pk_tw, R->d_kslot, R->d_kdst, R->d_tmx_wq, R->nwc, nc},
+                    nullptr, R->d_status};
+        R->tj_gq = {(int64_t)ti_gq.size(), R->d_ti_gq, R->d_tm_gq, {R->d_pk_sg, R->d_pk_tg, R->d_kslot, R->d_kdst, R->d_tmx_gq, nc, nc},
+                    nullptr, R->d_status};
+        R->rsrc = {n, R->d_row_ptr, R->d_rowslot, R->d_pos2, R->d_kslot, R->max_n_i};
+        R->h_ti_wq = ti_wq;
+        R->h_tm_wq = tm_wq;
+    }
 
     // Gauss-Legendre 4-point rule on [0, 1] (closed form)
     {
@@ -603,6 +742,10 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
             ww[k] = 0.5 * w[k];
         }
         wqd::set_gauss_constants(x, ww);
+    }
+    if (R->tile_ok) {
+        cudaError_t pe = wqd::prepare_tile_kernels();
+        if (pe != cudaSuccess) return bail(fail(ctx, WQ_ERR_CUDA, std::string("tile kernels: ") + cudaGetErrorString(pe)));
     }
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
@@ -685,6 +828,46 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gtable, R->d_gtable2, gbt_ptr[E], st);
     if (ce == cudaSuccess) ce = wqd::launch_split_rows(R->d_W, R->d_wrow_dst, R->d_W2, R->sum_r, R->nwc, R->n_sm, st);
     if (ce == cudaSuccess) ce = wqd::launch_copy_rows(R->d_W, R->d_wrow_dst, R->d_We, R->sum_r, R->nwc, R->n_sm, st);
+    // element-major packs of the tile engine
+    if (R->tile_ok) {
+        wqd::PackJob pj{};
+        pj.E = E;
+        pj.m = R->d_m;
+        pj.nc = nc;
+        pj.nwc = R->nwc;
+        pj.kind = wqd::PK_W2E;   // WQ test side: the split weights
+        pj.ncomp = R->nwc;
+        pj.P = d_Pw;
+        pj.src_off = d_wbase;
+        pj.out_off = d_sw_off;
+        pj.f2 = R->d_W2;
+        pj.out = R->d_pk_sw;
+        if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
+        pj.kind = wqd::PK_TABLE2;   // WQ trial side: the split table
+        pj.ncomp = nc;
+        pj.src_off = R->d_bt_ptr;
+        pj.out_off = d_tw_off;
+        pj.f2 = R->d_table2;
+        pj.out = R->d_pk_tw;
+        if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
+        if (ce == cudaSuccess) ce = wqd::launch_pack_max(pj, d_tmx_off, R->d_tmx_wq, st);
+        pj.kind = wqd::PK_GAUSS;   // Gauss test side: Gauss weight x table, split
+        pj.P = d_Pg;
+        pj.src_off = R->d_gbt_ptr;
+        pj.out_off = d_sg_off;
+        pj.f64 = R->d_gtable;
+        pj.gw = R->d_gw;
+        pj.pt0 = R->d_gp_ptr;
+        pj.out = R->d_pk_sg;
+        if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
+        pj.kind = wqd::PK_TABLE2;   // Gauss trial side: the split Gauss table
+        pj.pt0 = nullptr;
+        pj.out_off = d_tg_off;
+        pj.f2 = R->d_gtable2;
+        pj.out = R->d_pk_tg;
+        if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
+        if (ce == cudaSuccess) ce = wqd::launch_pack_max(pj, d_tmx_off, R->d_tmx_gq, st);
+    }
     // trial-side slices and test-side bounds of the tensor-core contraction
     if (R->tc_ok) {
         if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gw, R->d_gw2, R->G, st);
@@ -901,6 +1084,10 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
         e = wqd::launch_elem_f64(rule->it_wq, rule->src64_wq, tm, 0, (const double*)d_coef, (double*)d_vals, st, evs);
     else if (prec == WQ_PREC_TC)
         e = wqd::launch_elem_tc(rule->tit_wq, rule->tc_wq, tm, 0, (const double*)d_coef, (float*)d_vals, st, evs);
+    else if (wqd::TileTerms tt; float_variant(rule, op, 0) != WQ_VARIANT_SLOTMAP && rule->tile_ok &&
+                                    tile_terms(tm, false, tt))
+        e = wqd::launch_tile_f32(rule->tj_wq, rule->rsrc, tt, (const double*)d_coef, (float*)d_vals,
+                                 prec == WQ_PREC_F32, float_variant(rule, op, 0), rule->n_sm, st, evs);
     else
         e = wqd::launch_elem_f32(rule->it_wq, rule->src_wq, tm, 0, (const double*)d_coef, (float*)d_vals,
                                  prec == WQ_PREC_F32, st, evs);
@@ -926,6 +1113,10 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
         e = wqd::launch_elem_f64(rule->it_gq, rule->src64_gq, tm, 1, (const double*)d_coef, (double*)d_vals, st, evs);
     else if (prec == WQ_PREC_TC)
         e = wqd::launch_elem_tc(rule->tit_gq, rule->tc_gq, tm, 1, (const double*)d_coef, (float*)d_vals, st, evs);
+    else if (wqd::TileTerms tt; float_variant(rule, op, 1) != WQ_VARIANT_SLOTMAP && rule->tile_ok &&
+                                    tile_terms(tm, true, tt))
+        e = wqd::launch_tile_f32(rule->tj_gq, rule->rsrc, tt, (const double*)d_coef, (float*)d_vals,
+                                 prec == WQ_PREC_F32, float_variant(rule, op, 1), rule->n_sm, st, evs);
     else
         e = wqd::launch_elem_f32(rule->it_gq, rule->src_gq, tm, 1, (const double*)d_coef, (float*)d_vals,
                                  prec == WQ_PREC_F32, st, evs);
@@ -1094,11 +1285,13 @@ wq_status wq_rule_autotune(wq_rule* rule, int32_t op, const void* d_coef, double
     double* d64 = nullptr;
     float* d32 = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int32_t saved_var = rule->set_var[op][gauss];
     auto release = [&]() {
         if (d64) cudaFree(d64);
         if (d32) cudaFree(d32);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
+        rule->set_var[op][gauss] = saved_var;
     };
     if (cudaMalloc(&d64, std::max<int64_t>(nnz, 1) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&d32, std::max<int64_t>(nnz, 1) * sizeof(float)) != cudaSuccess) {
@@ -1127,13 +1320,29 @@ wq_status wq_rule_autotune(wq_rule* rule, int32_t op, const void* d_coef, double
     }
     double amax = 0.0;
     for (double v : a64) amax = std::max(amax, std::fabs(v));
-    const int32_t modes[3] = {WQ_PREC_TC, WQ_PREC_F32, WQ_PREC_F32_FAST};
-    int32_t best = -1;
+    // candidates: the tensor-core slices, then each SIMT mode with each kernel variant
+    struct Cand {
+        int32_t mode, variant;
+    };
+    const Cand cand[WQ_TUNE_MAX] = {{WQ_PREC_TC, -1},
+                                    {WQ_PREC_F32, WQ_VARIANT_SLOTMAP},
+                                    {WQ_PREC_F32, WQ_VARIANT_TILE12},
+                                    {WQ_PREC_F32, WQ_VARIANT_TILE16},
+                                    {WQ_PREC_F32_FAST, WQ_VARIANT_SLOTMAP},
+                                    {WQ_PREC_F32_FAST, WQ_VARIANT_TILE12},
+                                    {WQ_PREC_F32_FAST, WQ_VARIANT_TILE16}};
+    int32_t best = -1, best_var = WQ_VARIANT_SLOTMAP;
     float best_ms = 0.0f;
-    for (int k = 0; k < 3; ++k) {
+    double mode_err[3] = {-1.0, -1.0, -1.0};
+    float mode_ms[3] = {-1.0f, -1.0f, -1.0f};
+    wq_rule::TuneRow* tab = rule->tune[op][gauss];
+    int nt = 0;
+    for (const Cand& c : cand) {
+        if (c.variant >= 0 && c.variant != WQ_VARIANT_SLOTMAP && !rule->tile_ok) continue;
+        rule->set_var[op][gauss] = c.variant >= 0 ? c.variant : saved_var;
         double err = -1.0;
         float ms = -1.0f;
-        if (run(modes[k], d32) == WQ_OK) {   // a mode this rule or operator does not take is skipped
+        if (run(c.mode, d32) == WQ_OK) {   // a mode this rule or operator does not take is skipped
             if (nnz > 0 && (cudaMemcpyAsync(a32.data(), d32, nnz * sizeof(float), cudaMemcpyDeviceToHost, st) !=
                                 cudaSuccess ||
                             cudaStreamSynchronize(st) != cudaSuccess)) {
@@ -1144,26 +1353,70 @@ wq_status wq_rule_autotune(wq_rule* rule, int32_t op, const void* d_coef, double
             for (int64_t x = 0; x < nnz; ++x) dmax = std::max(dmax, std::fabs((double)a32[x] - a64[x]));
             err = amax > 0.0 ? dmax / amax : dmax;
             if (err <= tol) {
-                for (int w = 0; w < 2; ++w) run(modes[k], d32);
+                for (int w = 0; w < 2; ++w) run(c.mode, d32);
                 cudaEventRecord(e0, st);
-                for (int r = 0; r < reps; ++r) run(modes[k], d32);
+                for (int r = 0; r < reps; ++r) run(c.mode, d32);
                 cudaEventRecord(e1, st);
                 if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
                     release();
                     return fail(rule->ctx, WQ_ERR_CUDA, "autotune: timing failed");
                 }
                 ms /= (float)reps;
-                if (best < 0 || ms < best_ms) best = modes[k], best_ms = ms;
+                if (best < 0 || ms < best_ms) {
+                    best = c.mode;
+                    best_var = c.variant >= 0 ? c.variant : best_var;
+                    best_ms = ms;
+                }
             }
         } else {
             rule->ctx->err.clear();
         }
-        if (h_err) h_err[k] = err;
-        if (h_ms) h_ms[k] = ms;
+        const int k = c.mode == WQ_PREC_TC ? 0 : (c.mode == WQ_PREC_F32 ? 1 : 2);
+        if (err >= 0.0 && (mode_err[k] < 0.0 || (ms >= 0.0f && (mode_ms[k] < 0.0f || ms < mode_ms[k])))) {
+            mode_err[k] = err;
+            if (ms >= 0.0f) mode_ms[k] = ms;
+        }
+        tab[nt++] = {c.mode, c.variant, err, ms};
     }
+    rule->ntune[op][gauss] = nt;
     release();
     rule->auto_prec[op][gauss] = best >= 0 ? best : WQ_PREC_F32;
+    rule->auto_var[op][gauss] = best >= 0 ? best_var : WQ_VARIANT_SLOTMAP;
     if (chosen) *chosen = best;
+    for (int k = 0; k < 3; ++k) {
+        if (h_err) h_err[k] = mode_err[k];
+        if (h_ms) h_ms[k] = mode_ms[k];
+    }
+    return WQ_OK;
+}
+
+wq_status wq_rule_autotune_report(const wq_rule* rule, int32_t op, int32_t gauss, int32_t capacity, int32_t* n,
+                                  int32_t* h_mode, int32_t* h_variant, double* h_err, float* h_ms) {
+    if (!rule || op < 0 || op > 4 || (gauss != 0 && gauss != 1) || capacity < 0 || !n) return WQ_ERR_ARG;
+    const int nt = rule->ntune[op][gauss];
+    *n = nt;
+    for (int k = 0; k < std::min(nt, (int)capacity); ++k) {
+        const wq_rule::TuneRow& t = rule->tune[op][gauss][k];
+        if (h_mode) h_mode[k] = t.mode;
+        if (h_variant) h_variant[k] = t.variant;
+        if (h_err) h_err[k] = t.err;
+        if (h_ms) h_ms[k] = t.ms;
+    }
+    return WQ_OK;
+}
+
+wq_status wq_rule_set_variant(wq_rule* rule, int32_t op, int32_t gauss, int32_t variant) {
+    if (!rule || op < 0 || op > 4 || (gauss != 0 && gauss != 1) || variant < -1 || variant > WQ_VARIANT_SLOTMAP)
+        return fail(rule ? rule->ctx : nullptr, WQ_ERR_ARG, "set_variant: bad argument");
+    if (variant >= 0 && variant != WQ_VARIANT_SLOTMAP && !rule->tile_ok)
+        return fail(rule->ctx, WQ_ERR_ARG, "set_variant: this rule has no tile-engine plan");
+    rule->set_var[op][gauss] = variant;
+    return WQ_OK;
+}
+
+wq_status wq_rule_get_variant(const wq_rule* rule, int32_t op, int32_t gauss, int32_t* variant) {
+    if (!rule || op < 0 || op > 4 || (gauss != 0 && gauss != 1) || !variant) return WQ_ERR_ARG;
+    *variant = float_variant(rule, op, gauss);
     return WQ_OK;
 }
 

@@ -6,13 +6,16 @@
 
 namespace wqd {
 
+constexpr int WQ_TERMS_MAX = 8;   // terms of an operator (padded to 1, 2, 3, 4 or 8)
+
 // Status flags written by kernels (bitwise OR into a device word).
 enum : unsigned int {
     ST_NOT_CONVERGED = 1u,
     ST_NONFINITE = 2u,
     ST_ILLPOSED = 4u,
     ST_BAD_INDEX = 8u,
-    ST_GEOMETRY = 16u
+    ST_GEOMETRY = 16u,
+    ST_TIMEOUT = 32u         // a bounded wait for staged data ran out (k_tile.cu)
 };
 
 // Per-element spline data and point tables of one rule.
@@ -126,26 +129,97 @@ struct TcPrep {
     float* vmax;
 };
 
+// Tile kernels (k_tile.cu).  Per rule and quadrature: element-major packs of the test
+// side (S0: WQ weights, or Gauss weight x test table) and the trial side (T0: basis
+// table), [16-function block][component][point][16] per element, zero beyond m_e.
+struct TileSrc {
+    const float2* S0;
+    const float2* T0;
+    float2* kslot;           // row-major slots (see RowSrc)
+    const int32_t* kdst;     // [sum_e m_e]: slot block of element e's row a at kdst[fn_ptr[e] + a]
+    const float* tmx;        // bounds of |T_hi| per (element, 16-function block, trial component)
+    int n_test, n_trial;     // components of the test and trial packs
+};
+// item[k] = {test pack base, trial pack base (float2 units), first point of the element
+// (coefficient rows), fn_ptr[e] (kdst)}; meta[k] = {m | P << 8 | (a0 / 16) << 16 | (b0 / 16) << 20 |
+// ncb << 24, rule (batched launches), offset of the element in tmx, 0}.
+struct TileJob {
+    int64_t n_items;
+    const int4* item;
+    const int4* meta;
+    TileSrc one;
+    const TileSrc* srcs;     // per rule (batched launches, device array)
+    unsigned* status;        // ST_TIMEOUT
+};
+// Terms of an operator for the tile kernels: staged component indices (test side from
+// s_lo, s_n components; trial side from r_lo, r_n), coefficient row (-1: the constant
+// (shi, slo)), rows cstride apart.
+struct TileTerms {
+    int nt;
+    int tcomp[WQ_TERMS_MAX], rcomp[WQ_TERMS_MAX], crow[WQ_TERMS_MAX];
+    float shi[WQ_TERMS_MAX], slo[WQ_TERMS_MAX];
+    int ncrow;
+    int64_t cstride;
+    int s_lo, s_n, r_lo, r_n;
+};
+// Per-row sums of the element blocks (k_rowsum_f32): row i's slots are
+// [rowslot[i], rowslot[i+1]) of kslot, its support entries in support order, each
+// ceil(m_e / 16) blocks of 16 slots holding the element block's row of the row's
+// function; pos gives each slot's position in the row (0xFFFF: padding).
+struct RowSrc {
+    int64_t n;
+    const int32_t* row_ptr;
+    const int32_t* rowslot;  // [n+1]
+    const uint16_t* pos;
+    const float2* kslot;
+    int max_n_i;
+};
+// Batched row sums: block b sums 16 rows of rule blk_rule[b] from row blk_row[b].
+struct RowBatch {
+    int64_t n_blocks;
+    const int32_t* blk_rule;
+    const int64_t* blk_row;
+    const RowSrc* src;       // device array
+    int max_n_i;             // over the rules
+};
+// Pack construction (rule set-up, k_pack).
+enum { PK_TABLE2 = 0, PK_W2E = 1, PK_GAUSS = 2 };
+struct PackJob {
+    int64_t E;
+    int kind, ncomp, nc, nwc;
+    const int32_t* m;
+    const int32_t* P;
+    const int64_t* src_off;  // table offset (PK_TABLE2, PK_GAUSS) or element-major weight row (PK_W2E)
+    const int64_t* out_off;
+    const int64_t* pt0;      // first Gauss point (PK_GAUSS)
+    const float2* f2;
+    const double* f64;
+    const double* gw;
+    float2* out;
+};
+
 // (hi, lo) float pair of a double v with hi + lo = v to 2^-47 |v|: hi is v cut to 24
 // significant bits, lo the next 24 bits of the remainder (cut as well).  Built from the
 // encoding with integer instructions for 2^-60 < |v| < 2^100 (the FP64 conversions run on
-// the slow FP64 pipe of this GPU); outside that range, and for 0, by conversions.
+// the slow FP64 pipe of this GPU); outside that range, and for 0, by conversions in an
+// out-of-line function, so that the common path carries no FP64 instruction (a short
+// branch would otherwise be if-converted and every call would issue the conversions).
+static __device__ __noinline__ float2 split_double_by_conversion(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
 __device__ __forceinline__ float2 split_double(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((b >> 52) & 0x7ffu) - 1023;
-    if (ex <= -60 || ex >= 100) {
-        const float h = __double2float_rn(v);
-        return make_float2(h, __double2float_rn(v - (double)h));
-    }
+    if (ex <= -60 || ex >= 100) return split_double_by_conversion(v);
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;                  // 52 bits
     const float hi = __uint_as_float(sign | ((unsigned)(ex + 127) << 23) | (unsigned)(mant >> 29));
     const unsigned r = (unsigned)(mant & 0x1FFFFFFFu);                      // the other 29 bits
-    if (r == 0u) return make_float2(hi, 0.0f);
-    const int msb = 31 - __clz(r);                                          // 0..28
+    const int msb = 31 - __clz(r | 1u);                                     // 0..28 (r = 0: lo = 0 below)
     const unsigned m24 = msb >= 23 ? (r >> (msb - 23)) : (r << (23 - msb));  // leading one at bit 23
     const float lo = __uint_as_float(sign | ((unsigned)(ex - 52 + msb + 127) << 23) | (m24 & 0x7FFFFFu));
-    return make_float2(hi, lo);
+    return make_float2(hi, r == 0u ? 0.0f : lo);
 }
 
 // Per-call device pointers, passed as a kernel parameter (N = 1 for one rule).

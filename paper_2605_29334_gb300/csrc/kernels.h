@@ -125,6 +125,23 @@ cudaError_t launch_heat_fields(const Elems& el, const int32_t* pt_elem, const in
 cudaError_t launch_apply(const Rows& rw, const int32_t* pt_of_w, int nt, int4 wc4, const double* W, int nwc,
                          const double* g, int64_t Q, double* y, cudaStream_t st);
 
+// Tile engine (k_tile.cu): element blocks staged by bulk copies, then per-row sums
+// (programmatic dependent launch); float CSR values.  variant 0 / 1: chunks of up to
+// 12 / 6 points (2 terms).  n_sm = multiprocessors (persistent grid).  evs: 3 events
+// (before, between, after) or null.  prepare_tile_kernels() sets the kernels' shared
+// memory size on the current device (once, before any launch or capture).
+cudaError_t prepare_tile_kernels();
+cudaError_t launch_tile_f32(const TileJob& job, const RowSrc& rs, const TileTerms& tm, const double* coef,
+                            float* vals, bool compensated, int variant, int n_sm, cudaStream_t st,
+                            cudaEvent_t* evs = nullptr);
+// The same for k <= WQ_BATCH_MAX rules (items carry their rule; rows in RowBatch blocks).
+cudaError_t launch_tile_batch(const TileJob& job, const RowBatch& rb, const double* const* coefs, float* const* vals,
+                              int k, const TileTerms& tm, bool compensated, int variant, int n_sm, cudaStream_t st);
+// Element-major pack of a table or of the weights (rule set-up), and the bound table of a
+// trial pack (max |hi| per element, 16-function block and component).
+cudaError_t launch_pack(const PackJob& pj, cudaStream_t st);
+cudaError_t launch_pack_max(const PackJob& pj, const int64_t* tmx_off, float* tmx, cudaStream_t st);
+
 // Convert double arrays to (hi, lo) float pairs.
 cudaError_t launch_split_f32(const double* src, float2* dst, int64_t n, cudaStream_t st);
 

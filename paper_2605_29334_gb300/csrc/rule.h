@@ -9,6 +9,8 @@
 #include "kernels.h"
 #include "wq_internal.h"
 
+constexpr int WQ_TUNE_MAX = 7;   // autotune candidates: TC, and 2 SIMT modes x 3 kernel variants
+
 struct wq_ctx {
     int device = -1;
     std::string err;
@@ -40,6 +42,16 @@ struct wq_rule {
     int max_sweeps = 40;
     int count_mode = 0;
     int32_t auto_prec[5][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}, {1, 1}};   // WQ_PREC_AUTO per (op, gauss)
+    int32_t auto_var[5][2] = {{2, 2}, {2, 2}, {2, 2}, {2, 2}, {2, 2}};    // float-mode kernel variant chosen
+    // the last autotune's candidates per (op, gauss): mode, variant, error, time
+    struct TuneRow {
+        int32_t mode, variant;
+        double err;
+        float ms;
+    };
+    TuneRow tune[5][2][WQ_TUNE_MAX] = {};
+    int32_t ntune[5][2] = {};
+    int32_t set_var[5][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};   // wq_rule_set_variant (-1: auto)
     std::vector<wqi::DevBuf> bufs;
     // device arrays
     int32_t *d_m = nullptr, *d_nsub = nullptr, *d_side = nullptr, *d_pt_elem = nullptr, *d_gp_elem = nullptr;
@@ -96,6 +108,21 @@ struct wq_rule {
         if (tcount >= tcap) return nullptr;
         return tev.data() + 3 * (tcount++);
     }
+    // tile engine (k_tile.cu): element-major packs (WQ test / trial, Gauss test / trial),
+    // 16 x 16 tiles per quadrature, the per-row sum plan
+    bool tile_ok = false;
+    float2 *d_pk_sw = nullptr, *d_pk_tw = nullptr, *d_pk_sg = nullptr, *d_pk_tg = nullptr;
+    int4 *d_ti_wq = nullptr, *d_ti_gq = nullptr;
+    int4 *d_tm_wq = nullptr, *d_tm_gq = nullptr;
+    float *d_tmx_wq = nullptr, *d_tmx_gq = nullptr;
+    int32_t *d_rowslot = nullptr, *d_kdst = nullptr;
+    uint16_t* d_pos2 = nullptr;
+    float2* d_kslot = nullptr;
+    int64_t kslot_len = 0;
+    wqd::TileJob tj_wq{}, tj_gq{};
+    wqd::RowSrc rsrc{};
+    std::vector<int4> h_ti_wq;            // host copies of the WQ tiles (batched assembly)
+    std::vector<int4> h_tm_wq;
     wqd::Elems el{};
     wqd::Rows rw{};
     wq_rule_info info{};
@@ -114,6 +141,9 @@ struct wq_batch {
     std::vector<const wq_rule*> rules;
     std::vector<wqi::DevBuf> bufs;
     wqd::BatchPlan plan{};
+    bool tile_ok = false;                 // every rule has the tile engine's plan
+    wqd::TileJob tj{};
+    wqd::RowBatch rb{};
     ~wq_batch() {
         for (auto& b : bufs)
             if (b.p) cudaFree(b.p);

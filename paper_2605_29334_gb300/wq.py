@@ -21,6 +21,7 @@ WQ_OK, WQ_ERR_ARG, WQ_ERR_MESH, WQ_ERR_ILLPOSED, WQ_ERR_NOT_CONVERGED, WQ_ERR_NO
 OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S, OP_HEAT_J = range(5)
 COMP_N, COMP_X, COMP_Y, COMP_Z, COMP_LAP = range(5)
 PREC_F64, PREC_F32, PREC_F32_FAST, PREC_TC, PREC_AUTO = 0, 1, 2, 3, 4
+VARIANT_TILE12, VARIANT_TILE16, VARIANT_SLOTMAP = 0, 1, 2
 TYPE_NAMES = ["passive", "boundary", "irregular", "enriched_transition", "transition", "enriched_regular", "regular"]
 
 
@@ -93,6 +94,10 @@ EXPORTS = {
                                  C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_basis_functions": (C.c_int, [C.c_void_p, C.c_void_p]),
     "wq_rule_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "wq_rule_set_variant": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "wq_rule_get_variant": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+    "wq_rule_autotune_report": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_rule_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "wq_batch_create": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "wq_batch_destroy": (None, [C.c_void_p]),
@@ -516,7 +521,32 @@ class Rule:
         self.ctx.check(lib().wq_rule_autotune(self.h, int(op), cp, float(alpha), int(bool(gauss)),
                                               float(tol), int(reps), _stream_handle(stream), C.byref(chosen),
                                               _ptr(err), _ptr(ms)))
-        return {"chosen": chosen.value, "err": err.tolist(), "ms": ms.tolist()}
+        return {"chosen": chosen.value, "err": err.tolist(), "ms": ms.tolist(),
+                "variant": self.variant(op, gauss=gauss), "candidates": self.autotune_report(op, gauss=gauss)}
+
+    def autotune_report(self, op, gauss=False):
+        """Every candidate of the last autotune: list of {mode, variant, err, ms}."""
+        n = C.c_int32(0)
+        cap = 16
+        mode = np.zeros(cap, dtype=np.int32)
+        var = np.zeros(cap, dtype=np.int32)
+        err = np.zeros(cap, dtype=np.float64)
+        ms = np.zeros(cap, dtype=np.float32)
+        self.ctx.check(lib().wq_rule_autotune_report(self.h, int(op), int(bool(gauss)), cap, C.byref(n), _ptr(mode),
+                                                     _ptr(var), _ptr(err), _ptr(ms)))
+        k = min(n.value, cap)
+        return [{"mode": int(mode[i]), "variant": int(var[i]), "err": float(err[i]), "ms": float(ms[i])}
+                for i in range(k)]
+
+    def set_variant(self, op, variant, gauss=False):
+        """wq_rule_set_variant: kernel variant of the float modes for (op, gauss); -1 = the
+        autotuner's choice."""
+        self.ctx.check(lib().wq_rule_set_variant(self.h, int(op), int(bool(gauss)), int(variant)))
+
+    def variant(self, op, gauss=False):
+        v = C.c_int32(0)
+        self.ctx.check(lib().wq_rule_get_variant(self.h, int(op), int(bool(gauss)), C.byref(v)))
+        return v.value
 
     def set_timing(self, capacity):
         """Record per-kernel CUDA events for the next `capacity` assembly calls (0: off)."""

@@ -1,4 +1,4 @@
-"""wq_rule_autotune / WQ_PREC_AUTO: the library measures the float modes on the
+"""wq_rule_autotune / WQ_PREC_AUTO: the library measures the float modes and kernel variants on the
 rule's own data (error against its FP64 result, then device time of the modes within
 the tolerance) and WQ_PREC_AUTO assembles with the fastest of them."""
 import numpy as np
@@ -49,3 +49,33 @@ def test_autotune_without_an_eligible_mode(setup):
     res = r.autotune(wq.OP_MASS, cq, tol=0.0, reps=2)
     assert res["chosen"] == -1 and all(t == -1.0 for t in res["ms"])
     assert torch.equal(r.assemble(wq.OP_MASS, cq, prec=wq.PREC_AUTO), r.assemble(wq.OP_MASS, cq, prec=wq.PREC_F32))
+
+
+@pytest.mark.parametrize("gauss", [False, True])
+def test_autotune_chooses_mode_and_kernel_variant(setup, gauss):
+    """The candidates are the tensor-core mode and each SIMT mode with each kernel variant;
+    the recorded choice is the fastest timed candidate, WQ_PREC_AUTO reproduces it bit
+    for bit, and an explicit variant overrides it until reset."""
+    import torch
+    wq, r, cq, cg = setup
+    coef = cg if gauss else cq
+    res = r.autotune(wq.OP_STIFF, coef, gauss=gauss, tol=1e-6, reps=5)
+    cands = res["candidates"]
+    assert len(cands) == 7
+    pairs = {(c["mode"], c["variant"]) for c in cands}
+    for mode in (wq.PREC_F32, wq.PREC_F32_FAST):
+        for v in (wq.VARIANT_SLOTMAP, wq.VARIANT_TILE12, wq.VARIANT_TILE16):
+            assert (mode, v) in pairs
+    timed = [c for c in cands if c["ms"] > 0.0]
+    assert timed and all(0.0 <= c["err"] <= 1e-6 for c in timed)
+    best = min(timed, key=lambda c: c["ms"])
+    assert res["chosen"] == best["mode"]
+    if best["mode"] != wq.PREC_TC:
+        assert res["variant"] == best["variant"]
+    asm = r.gq_assemble if gauss else r.assemble
+    got = asm(wq.OP_STIFF, coef, prec=wq.PREC_AUTO)
+    r.set_variant(wq.OP_STIFF, res["variant"], gauss=gauss)
+    ref = asm(wq.OP_STIFF, coef, prec=res["chosen"])
+    r.set_variant(wq.OP_STIFF, -1, gauss=gauss)
+    assert torch.equal(got, ref)
+    assert r.variant(wq.OP_STIFF, gauss=gauss) == res["variant"]
