@@ -231,56 +231,47 @@ def bench_ours(args, rank, world):
         return None
     value = tot_nnz * args.steps / t_max
     mean_s = t_total / args.steps
-    work = assembly_work(rule, basis, n_terms=2)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    if "hbm_gbs" in peaks:
+        hbm, hbm_src = float(peaks["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    else:
+        hbm, hbm_src = 6800.0, "6.8 TB/s, the profiling recipe's fallback (of fallback; MEASURED_PEAKS.json absent)"
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     t_k1 = float(np.mean(kt[:, 0])) / 1e3 if len(kt) else float("nan")
     t_k2 = float(np.mean(kt[:, 1])) / 1e3 if len(kt) else float("nan")
-    step_bytes = work["hbm_bytes_f64"] if prec == wq.PREC_F64 else work["hbm_bytes_f32"]
-    if prec == wq.PREC_TC:
-        # tensor-core element blocks: the SIMT work is per (row, point, term) and the
-        # contraction runs on the tensor pipe, so the kernel's binding roofline is the
-        # bytes it must move: test-side weights, trial-side slices, coefficients, slot
-        # map, tile descriptors and the slot writes
-        kname = "k_elem_tc<2,0>"
-        achieved = work["tc_elem_bytes"] / t_k1 / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": ELEM_TRAFFIC.get(kname) if _kernel_source_sha1("k_tc.cu") == ELEM_TRAFFIC.get(
-                    "k_tc.cu") else None,
-                "kernel": kname, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "kernel_ms": t_k1 * 1e3, "gather_ms": t_k2 * 1e3, "kernel_algorithmic_bytes": work["tc_elem_bytes"],
-                "instrumented_step_ms": float(np.mean(ms_inst)),
-                "kernel_share_of_step": t_k1 / (float(np.mean(ms_inst)) / 1e3),
-                "step_hbm_frac": step_bytes / mean_s / 1e9 / hbm, "step_algorithmic_bytes": step_bytes}
-    elif prec == wq.PREC_F64:
-        # FP64 element blocks: one FMA (2 flops) per product; peak = 152 SMs x 2 FP64 FMA per
-        # cycle (ncu's sustained rate on this GPU) x 2 flops x max SM clock
-        kname = "k_elem_f64<2,0>"
-        peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    work = assembly_work(rule, basis, n_terms=2, value_bytes=8 if prec == wq.PREC_F64 else 4)
+    variant = rule.variant(wq.OP_STIFF) if prec in (wq.PREC_F32, wq.PREC_F32_FAST) else -1
+    kname, k2name = KERNELS.get((choice, variant), ("?", "?"))
+    step_frac = work["step_bytes"] / mean_s / 1e9 / hbm
+    if prec == wq.PREC_F64:
+        # FP64 element blocks: one FMA (2 flops) per product; peak derived from the SM count
+        # of this device x 2 FP64 FMA per cycle x 2 flops x max SM clock (not a measured peak)
+        peak = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12
         achieved = 2 * work["products"] / t_k1 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s FP64", "frac": achieved / peak,
-                "traffic": None, "kernel": kname,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/cycle x 2 x %.0f MHz" % sm_mhz,
-                "kernel_ms": t_k1 * 1e3, "gather_ms": t_k2 * 1e3}
+                "traffic": None, "kernel": kname, "second_kernel": k2name,
+                "peak_source": "derived (not measured): %d SMs x 2 FP64 FMA/cycle x 2 x %.0f MHz" % (n_sm, sm_mhz),
+                "kernel_ms": t_k1 * 1e3, "second_kernel_ms": t_k2 * 1e3,
+                "step_algorithmic_bytes": work["step_bytes"], "step_hbm_frac": step_frac}
     else:
-        # the element-block kernel is bound by instruction issue: 6 FP32 instructions per split
-        # product with the extraction-compensated sum (3 without); peak = 152 SMs x 128 FP32
-        # lanes x max SM clock
+        # the binding roofline of the mixed path is HBM: the element kernel must read the
+        # weights, the used table components and the coefficient once (algorithmic bytes,
+        # FP64 sizes); slot buffers, index data and descriptors are overhead, in `traffic`
+        achieved = work["kernel_bytes"] / t_k1 / 1e9
+        traffic = ELEM_TRAFFIC.get(kname) if _kernel_source_sha1(kname) == ELEM_TRAFFIC.get(kname + ":sha1") else None
         per = 6 if prec == wq.PREC_F32 else 3
-        kname = "k_elem_f32<2,%d,0>" % (1 if prec == wq.PREC_F32 else 0)
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-        achieved = per * work["products"] / t_k1 / 1e12
-        traffic = ELEM_TRAFFIC.get(kname) if _kernel_source_sha1("k_assemble.cu") == ELEM_TRAFFIC.get(
-            "k_assemble.cu") else None
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 lane-instructions/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (MEASURED_PEAKS.json sm_max_mhz)" % sm_mhz,
-                "kernel_ms": t_k1 * 1e3, "gather_ms": t_k2 * 1e3,
-                "instrumented_step_ms": float(np.mean(ms_inst)),
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": kname, "second_kernel": k2name, "peak_source": hbm_src,
+                "kernel_algorithmic_bytes": work["kernel_bytes"], "kernel_ms": t_k1 * 1e3,
+                "second_kernel_ms": t_k2 * 1e3, "instrumented_step_ms": float(np.mean(ms_inst)),
                 "kernel_share_of_step": t_k1 / (float(np.mean(ms_inst)) / 1e3),
-                "step_hbm_frac": step_bytes / mean_s / 1e9 / hbm, "step_algorithmic_bytes": step_bytes}
+                "step_algorithmic_bytes": work["step_bytes"], "step_hbm_frac": step_frac,
+                # diagnostic, not a roofline: FP32 lane-instructions of the products per second
+                # against this device's SMs x 128 lanes x max clock
+                "diag_lane_instruction_frac": (per * work["products"] / t_k1)
+                / (n_sm * 128 * sm_mhz * 1e6) if prec != wq.PREC_TC else None}
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -291,6 +282,7 @@ def bench_ours(args, rank, world):
                    "every timed step; timed = the assembly call only", "parallelism": "independent instance per GPU"},
         "rel_err_vs_f64": rel,
         "autotune_ms": dict(zip(("tc", "f32", "f32_fast"), tune["ms"])),
+        "autotune_candidates": tune["candidates"], "kernel_variant": variant,
         "gpu_launches": args.steps * 2,
         "roofline": roof,
         "comparators": dict({k + "_ms": v for k, v in comp_ms.items()},
@@ -305,7 +297,9 @@ def bench_ours(args, rank, world):
                   "tsvd_ms": rule.info.tsvd_ms, "tsvd_gflop": rule.info.tsvd_gflop,
                   "tsvd_fp64_tflops": rule.info.tsvd_gflop / max(rule.info.tsvd_ms, 1e-9),
                   "tsvd_fp64_frac": rule.info.tsvd_gflop / max(rule.info.tsvd_ms, 1e-9)
-                  / (152 * 2 * 2 * sm_mhz * 1e6 / 1e12)},
+                  / (n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12),
+                  "tsvd_fp64_peak_source": "derived (not measured): %d SMs x 2 FP64 FMA/cycle x 2 x %.0f MHz"
+                  % (n_sm, sm_mhz)},
         "e2e": {"value": nnz / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(rule.Q * 8),
                 "d2h_bytes_per_step": int(nnz * (8 if prec == wq.PREC_F64 else 4))},
         "clocks": clocks,
@@ -314,7 +308,7 @@ def bench_ours(args, rank, world):
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if not args.no_configs:
-        res["other_configs"] = other_configs(ctx, flush, max(args.steps // 20, 20), args.warmup)
+        res["other_configs"] = other_configs(ctx, flush, max(args.steps // 20, 20), args.warmup, hbm)
     return res
 
 
@@ -326,7 +320,7 @@ def _timed_pair(fn_wq, fn_gq, out_wq, out_gq, steps, warmup, flush):
     return t_wq, t_gq
 
 
-def other_configs(ctx, flush, steps, warmup):
+def other_configs(ctx, flush, steps, warmup, hbm=6800.0):
     """The other workloads of the method, same protocol (assembly only, L2 flushed, CUDA
     events, median): WQ against Gauss on the same GPU at FP32 (compensated) and FP64,
     with the FP32 error against the FP64 result.  Config 5 is a reduced batch (16
@@ -337,7 +331,7 @@ def other_configs(ctx, flush, steps, warmup):
     from wq_synth import meshes
     out = {}
 
-    def one(name, mesh, comps, op, alpha, coef_fn):
+    def one(name, mesh, comps, op, alpha, coef_fn, n_terms):
         t0 = time.perf_counter()
         b = wq.Basis(ctx, mesh)
         r = wq.Rule(b, comps=comps)
@@ -367,18 +361,25 @@ def other_configs(ctx, flush, steps, warmup):
                      "wq_tc_nnz_per_s": r.nnz / tc[0] * 1e3, "gq_tc_nnz_per_s": r.nnz / tc[1] * 1e3,
                      "speedup_tc": tc[1] / tc[0], "tc_rel_err_vs_f64": err_tc,
                      "f32_rel_err_fro_vs_f64": err_fro, "tc_rel_err_fro_vs_f64": err_tc_fro}
+        # HBM roofline of the WQ FP32 step (both kernels): algorithmic bytes (weights, used
+        # table components, coefficient, values) over the step's median device time
+        wk = assembly_work(r, b, n_terms=n_terms, value_bytes=4)
+        out[name]["roofline_wq_f32_step"] = {
+            "bound": "hbm", "algorithmic_bytes": wk["step_bytes"], "unit": "GB/s", "peak": hbm,
+            "achieved": wk["step_bytes"] / (f32[0] / 1e3) / 1e9,
+            "frac": wk["step_bytes"] / (f32[0] / 1e3) / 1e9 / hbm}
         return b, r, cq
 
     disk = meshes.disk(mu=5, n=6)
     one("1_disk_mu5_mass_stiffness", disk, [wq.COMP_N, wq.COMP_X, wq.COMP_Y], wq.OP_HEAT_S, 1.0,
-        meshes.kappa_sines)
+        meshes.kappa_sines, 3)
     sph = meshes.cube_sphere(pre=3, levels=3)
     one("3_sphere_biharmonic", sph, [wq.COMP_N, wq.COMP_LAP], wq.OP_BIHARM, 0.0,
-        lambda x: 1.0 + 0.25 * x[:, 0] * x[:, 1] + 0.1 * x[:, 2])
+        lambda x: 1.0 + 0.25 * x[:, 0] * x[:, 1] + 0.1 * x[:, 2], 1)
     heat = make_mesh(levels=5)
     u0 = meshes.gaussian_bumps(4001, heat["xyz"].min(0), heat["xyz"].max(0))
     b4, r4, _ = one("4_heat_tangent_L5", heat, [wq.COMP_N, wq.COMP_X, wq.COMP_Y], wq.OP_HEAT_S, 100.0,
-                    lambda x: 1.0 + u0(x) ** 2)
+                    lambda x: 1.0 + u0(x) ** 2, 3)
     # config 4: 20 Newton re-assemblies (point data, residual, tangent) replayed from one CUDA graph
     u = torch.tensor(u0(b4.ctrl()), device="cuda")
     u_old = u.clone()
@@ -434,23 +435,26 @@ def other_configs(ctx, flush, steps, warmup):
 
 
 # DRAM bytes (read + write) of one launch of the element-block kernels on this workload,
-# from `ncu --set full` (profiles/k_elem_f32_poisson_rotated_L4.md and
-# profiles/k_elem_tc_poisson_rotated_L4.md), valid for the kernel source they were taken on.
-# The key is the SHA-1 of the kernel's own source text (the template up to the per-entry
-# sums that follow it), so that edits elsewhere in the file keep the measurement.
-ELEM_TRAFFIC = {"k_assemble.cu": "1a3e2518c10271d66a893af1613b3e0eb6afa02a", "k_elem_f32<2,1,0>": 60436992,
-                "k_tc.cu": "3c5ca0106f23d6257452c245b034a1ca7f2d45f6", "k_elem_tc<2,0>": 68657152}
-_KERNEL_TEXT = {"k_assemble.cu": ("template <int NT, bool COMP, bool GAUSS, bool BATCH, int NP>\n__global__ void "
-                                  "__launch_bounds__(EL_NWARP * 32, 6)",
-                                  "// Phase 2: one thread per two consecutive CSR entries."),
-                "k_tc.cu": ("template <int NT, bool GAUSS>\n__global__", "cudaError_t launch_elem_tc(")}
+# from `ncu --set full` (profiles/), valid for the kernel source they were taken on: the
+# key "<kernel>:sha1" holds the SHA-1 of the kernel's own source text (see _KERNEL_TEXT),
+# so that edits elsewhere in the file keep the measurement and edits of the kernel drop it.
+ELEM_TRAFFIC = {"k_elem_f32<2,1,0,0,1>": 60436992, "k_elem_f32<2,1,0,0,1>:sha1": "1a3e2518c10271d66a893af1613b3e0eb6afa02a",
+                "k_elem_tc<2,0>": 68657152, "k_elem_tc<2,0>:sha1": "3c5ca0106f23d6257452c245b034a1ca7f2d45f6"}
+_KERNEL_TEXT = {"k_elem_f32": ("k_assemble.cu", "template <int NT, bool COMP, bool GAUSS, bool BATCH, int NP>\n__global__ void "
+                               "__launch_bounds__(EL_NWARP * 32, 6)", "// Phase 2: one thread per two consecutive CSR entries."),
+                "k_elem_tc": ("k_tc.cu", "template <int NT, bool GAUSS>\n__global__", "cudaError_t launch_elem_tc("),
+                "k_tile_f32": ("k_tile.cu", "template <int NT, int V, bool COMP, bool BATCH, int NP>\n__global__",
+                               "// ------------------------------------------------------------------ phase 2")}
 
 
-def _kernel_source_sha1(name):
+def _kernel_source_sha1(kname):
     import hashlib
+    base = kname.split("<")[0]
+    if base not in _KERNEL_TEXT:
+        return None
+    name, begin, end = _KERNEL_TEXT[base]
     with open(os.path.join(ROOT, "paper_2605_29334_gb300", "csrc", name)) as f:
         s = f.read()
-    begin, end = _KERNEL_TEXT[name]
     try:
         s = s[s.index(begin):s.index(end)]
     except ValueError:
@@ -488,32 +492,37 @@ def refine_measure(wq, basis, mesh, flush, steps, warmup, hbm):
             "launches": 2, "timing": "CUDA-graph replay, L2 flushed before each"}
 
 
-def assembly_work(rule, basis, n_terms):
-    """Algorithmic work of one stiffness assembly (n_terms weight/table components):
-    products = sum_e m_e^2 P_e n_terms (one per test x trial x point x term);
-    HBM bytes = what must be read and written once: weights and the used table
-    components (FP64 values, or FP32 (hi, lo) pairs), the coefficient at the points,
-    the index data the kernels read, and the CSR values."""
+def assembly_work(rule, basis, n_terms, n_coef_rows=1, value_bytes=4):
+    """Algorithmic work of one assembly of an operator with n_terms (weight component,
+    table component) pairs: products = sum_e m_e^2 P_e n_terms (one per test x trial x
+    point x term); algorithmic bytes (what must cross HBM once, FP64 storage): the
+    weights sum_i r_i n_terms 8 (sum_i r_i = sum_e m_e P_e), the used table components
+    sum_e m_e P_e n_terms 8, the coefficient rows Q n_coef_rows 8, and for the whole step
+    the CSR values nnz value_bytes.  The element kernel's own algorithmic bytes are the
+    first three (it reads them; the values are written by the per-row sums)."""
     E = basis.E
     side = basis.point_counts().astype(np.int64)
     m = np.array([basis.element(e)["fns"].size for e in range(E)], dtype=np.int64)
     P = side * side
     products = int(np.sum(m * m * P)) * n_terms
-    weights = rule.info.sum_r * n_terms * 8
+    weights = int(rule.info.sum_r) * n_terms * 8
     tables = int(np.sum(P * m)) * n_terms * 8
-    coef = rule.Q * 8
-    n = basis.n
-    f64 = weights + tables + coef + int(np.sum(m * m)) * 2 + int(np.sum(m)) * 16 + (n + 1) * 20 + rule.nnz * 8
-    n_tiles = int(np.sum(((m + 15) // 16) ** 2))
-    f32 = weights + tables + coef + int(np.sum(m * m)) * 4 + (rule.nnz + 1) * 4 + n_tiles * 20 + rule.nnz * 4
-    # tensor-core element kernel: split weights (8 B per used value), trial slices (per tile,
-    # term and 8 points: 5 slices x 32 lanes x 8 B), coefficients, slot map, tile
-    # descriptors (2 x int4 + kb) and the slot writes (float pairs)
-    P8 = (P + 7) // 8 * 8
-    tc_elem = (weights + int(np.sum(((m + 15) // 16) ** 2 * P8)) * n_terms * 160 + coef
-               + int(np.sum(m * m)) * 4 + n_tiles * 36 + int(np.sum(m * m)) * 8)
-    return {"products": products, "hbm_bytes_f64": int(f64), "hbm_bytes_f32": int(f32),
-            "tc_elem_bytes": int(tc_elem)}
+    coef = int(rule.Q) * n_coef_rows * 8
+    values = int(rule.nnz) * value_bytes
+    return {"products": products, "weights": weights, "tables": tables, "coef": coef, "values": values,
+            "kernel_bytes": weights + tables + coef, "step_bytes": weights + tables + coef + values}
+
+
+KERNELS = {  # (mode, variant) -> (element kernel, second kernel) of the stiffness operator (2 terms)
+    ("f32", 2): ("k_elem_f32<2,1,0,0,1>", "k_gather_f32<1,0,1>"),
+    ("f32_fast", 2): ("k_elem_f32<2,0,0,0,1>", "k_gather_f32<0,0,1>"),
+    ("f32", 0): ("k_tile_f32<2,0,1,0,1>", "k_rowsum_f32<1,0,1>"),
+    ("f32", 1): ("k_tile_f32<2,1,1,0,1>", "k_rowsum_f32<1,0,1>"),
+    ("f32_fast", 0): ("k_tile_f32<2,0,0,0,1>", "k_rowsum_f32<0,0,1>"),
+    ("f32_fast", 1): ("k_tile_f32<2,1,0,0,1>", "k_rowsum_f32<0,0,1>"),
+    ("tc", -1): ("k_elem_tc<2,0>", "k_gather_f32<1,0,1>"),
+    ("f64", -1): ("k_elem_f64<2,0>", "k_gather_f64"),
+}
 
 
 def cpu_baseline(args, seconds=12.0):

@@ -165,7 +165,8 @@ typedef struct {
  * context (basis construction and host queries; rule builds return
  * WQ_ERR_NO_DEVICE).  *out receives the handle, owned by the caller until
  * wq_destroy.  Errors: WQ_ERR_ARG (null out), WQ_ERR_NO_DEVICE (no such device),
- * WQ_ERR_CUDA (cudaSetDevice failed), WQ_ERR_OOM (host allocation). */
+ * WQ_ERR_CUDA (cudaSetDevice or the scratch lookup failed), WQ_ERR_OOM (host
+ * allocation). */
 wq_status wq_create(int device, wq_ctx** out);
 /* Frees the context (NULL is ignored). */
 void wq_destroy(wq_ctx* ctx);
@@ -417,12 +418,13 @@ wq_status wq_rule_kernel_times(wq_rule* rule, int32_t max_calls, float* h_ms, in
  * serves callers that cannot allocate device memory while they run (a host
  * program whose own pool allocator owns the free device memory, or a
  * time-critical loop where cudaMalloc's implicit synchronisation is not
- * acceptable).  The first call on each device looks up the array's device
- * address (with that device current) and caches it: make that first call before
- * any stream capture.  Every call uses the same array, which keeps the last
- * call's contents; calls that overlap on the GPU race.  The call synchronises
- * on stream to report the solve's status.  Errors: WQ_ERR_ARG (component not
- * built; a system needing more than 32 MiB of workspace), WQ_ERR_CUDA,
+ * acceptable).  wq_create, when it binds a context to a device, looks up the
+ * array's device address with that device current; under lazy module loading this
+ * is also when the array's memory is committed on the device, so create the context
+ * before handing the free memory to another allocator.  Every call uses the same
+ * array, which keeps the last call's contents; calls that overlap on the GPU race.
+ * The call synchronises on stream to report the solve's status.  Errors: WQ_ERR_ARG
+ * (component not built; a system needing more than 32 MiB of workspace), WQ_ERR_CUDA,
  * WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE. */
 wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, double* d_w, void* stream);
 

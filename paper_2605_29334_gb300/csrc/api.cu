@@ -184,6 +184,14 @@ wq_status wq_create(int device, wq_ctx** out) {
             delete c;
             return WQ_ERR_CUDA;
         }
+        // the no-allocation entry point's fixed scratch: its device address is looked up
+        // (and its memory committed) now, with the device current
+        std::string nerr;
+        if (!wqi_noalloc_bind(device, nerr)) {
+            cudaGetLastError();
+            delete c;
+            return WQ_ERR_CUDA;
+        }
     }
     c->device = device;
     *out = c;

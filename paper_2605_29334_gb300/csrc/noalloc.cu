@@ -11,12 +11,15 @@
 //
 // The array g_noalloc_scratch is a file-scope __device__ object: every device
 // that loads the library holds its 32 MiB until the process exits.  Host code
-// may not use its name as a device address, so the first call on each device
-// looks the address up with cudaGetSymbolAddress (with that device current) and
-// caches it; make that first call before any stream capture.  All calls share
-// the array and it keeps the last call's contents: the status word is cleared
+// may not use its name as a device address, so its device address is looked up
+// with cudaGetSymbolAddress, with the device current, when wq_create binds a
+// context to the device (noalloc_bind below).  Under lazy module loading that lookup
+// is also what commits the array's memory on the device, so the commitment happens
+// at context creation and not inside a later call that must not allocate.  All calls
+// share the array and it keeps the last call's contents: the status word is cleared
 // at the start of every call, and calls that overlap on the GPU (another stream,
-// another host thread) race on the array.
+// another host thread) race on the array.  The call reads its status back and
+// synchronises on the caller's stream.
 #include <mutex>
 #include <string>
 
@@ -39,7 +42,35 @@ wq_status set_err(wq_ctx* ctx, wq_status code, const std::string& msg) {
     return code;
 }
 
+// Look up (once per device, with that device current) the device addresses of the
+// scratch array and status word; false with a message if the runtime refuses.
+bool lookup(int dev, std::string& err) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_scratch_ptr[dev]) return true;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
+        return false;
+    }
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&q, g_noalloc_status);
+    if (e != cudaSuccess) {
+        err = std::string("cudaGetSymbolAddress(status): ") + cudaGetErrorString(e);
+        return false;
+    }
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+    g_status_ptr[dev] = static_cast<unsigned*>(q);
+    return true;
+}
+
 }  // namespace
+
+// Called by wq_create with `dev` current.
+bool wqi_noalloc_bind(int dev, std::string& err) {
+    if (dev < 0 || dev >= kMaxDevices) return true;   // the entry point reports it
+    return lookup(dev, err);
+}
 
 extern "C" wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, double* d_w, void* stream) {
     if (!rule || !d_w || comp < 0 || comp > 4) return WQ_ERR_ARG;
@@ -51,25 +82,11 @@ extern "C" wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, 
     cudaError_t e = cudaSetDevice(dev);
     if (e != cudaSuccess) return set_err(ctx, WQ_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     (void)cudaGetLastError();   // an error pending from another caller is not this call's
-    double* scratch = nullptr;
-    unsigned* status = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess)
-                return set_err(ctx, WQ_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-            void* q = nullptr;
-            e = cudaGetSymbolAddress(&q, g_noalloc_status);
-            if (e != cudaSuccess)
-                return set_err(ctx, WQ_ERR_CUDA, std::string("cudaGetSymbolAddress(status): ") + cudaGetErrorString(e));
-            g_scratch_ptr[dev] = static_cast<double*>(p);
-            g_status_ptr[dev] = static_cast<unsigned*>(q);
-        }
-        scratch = g_scratch_ptr[dev];
-        status = g_status_ptr[dev];
-    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::string lerr;
+    if (!lookup(dev, lerr)) return set_err(ctx, WQ_ERR_CUDA, lerr);   // normally done by wq_create already
+    double* scratch = g_scratch_ptr[dev];
+    unsigned* status = g_status_ptr[dev];
     const int64_t mn = rule->max_n_i, mr = rule->max_r;
     const int64_t per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
     if (per_cta > kScratchDoubles)
@@ -81,7 +98,6 @@ extern "C" wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, 
     int64_t n_cta = kScratchDoubles / per_cta;
     n_cta = std::min<int64_t>(n_cta, (int64_t)std::max(n_sm, 1) * 8);
     n_cta = std::min<int64_t>(n_cta, std::max<int64_t>(rule->n, 1));
-    cudaStream_t st = (cudaStream_t)stream;
     e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
         e = wqd::launch_tsvd(rule->el, rule->rw, rule->d_table, comp == WQ_COMP_LAP ? rule->nc - 1 : comp,

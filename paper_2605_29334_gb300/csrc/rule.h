@@ -9,6 +9,9 @@
 #include "kernels.h"
 #include "wq_internal.h"
 
+// noalloc.cu: look up the no-allocation entry point's scratch on device `dev` (current).
+bool wqi_noalloc_bind(int dev, std::string& err);
+
 constexpr int WQ_TUNE_MAX = 7;   // autotune candidates: TC, and 2 SIMT modes x 3 kernel variants
 
 struct wq_ctx {

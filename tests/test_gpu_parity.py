@@ -3,12 +3,11 @@
 a2 placement, a3 basis tables at WQ and Gauss points, a4 Gauss moments,
 a5 truncated-SVD weights, a6 WQ assembly (FP64 to 1e-11 normwise -- the bar of
 the FP64 path -- or, where the weight systems' conditioning makes that
-unreachable for any two FP64 implementations, 4x the oracle's own spread: the
-larger of the spread between two LAPACK SVD drivers and the spread caused by
-16-ulp perturbations of the solves' inputs (the size of the GPU-vs-oracle
-differences of the basis tables); FP32 split-product path: 1e-6 against
-the GPU's FP64 result, and max(1e-6, the FP64 bar) against the oracle; tensor-core
-slices: the same), a7
+unreachable for any two FP64 implementations, 4x the oracle's own spread
+between two LAPACK SVD drivers, gesdd and gesvd; FP32 split-product path: 1e-6
+against the GPU's FP64 result, and max(1e-6, the FP64 bar) against the oracle;
+tensor-core slices: the same; every achieved error and bar is recorded as a test
+property), a7
 interpolation, a8 Gauss assembly.  Meshes cover one EP of valence 3..8 (m_e up to 37 > 32 lanes),
 refined enriched regions, clustered EPs, an EP-free grid, a closed surface and
 a mesh with a single active element.
@@ -60,16 +59,13 @@ def case(request, W):
     B = Basis(mesh)
     R = owq.Rule(B, comps)
     R.compute_weights()
-    # the oracle's reproducibility floor: same steps with LAPACK gesvd instead of
-    # gesdd, and with 16-ulp perturbations of every weight solve's inputs
+    # the oracle's reproducibility floor: the same steps with LAPACK gesvd instead of gesdd
     R2 = owq.Rule(B, comps)
     R2.compute_weights(driver="gesvd")
-    R3 = owq.Rule(B, comps)
-    R3.compute_weights(perturb_seed=77)
     ctx = W.Context(0)
     b = W.Basis(ctx, mesh)
     r = W.Rule(b, comps=[COMP_ID[c] for c in comps])
-    return {"name": request.param, "B": B, "R": R, "R2": R2, "R3": R3, "ctx": ctx, "b": b, "r": r, "comps": comps}
+    return {"name": request.param, "B": B, "R": R, "R2": R2, "ctx": ctx, "b": b, "r": r, "comps": comps}
 
 
 def fp64_tol(spread, factor=4.0):
@@ -121,15 +117,31 @@ def test_moments(case):
         assert nerr(got, R.moments[c]) < 1e-13, c
 
 
-def test_weights(case):
+def test_weights(case, record_property):
+    """The weights are an intermediate, unique only up to each system's conditioning
+    (near-threshold singular values move them far more than the assembled matrices),
+    so they are held to what defines them: per row, the exactness constraints
+    A w = b (Sec. 4.3) on the oracle's own system, to the residual the oracle's weights
+    leave (x 10, at least 1e-12 of |b|), the truncation counts, and -- recorded, not a
+    bar -- their distance to the oracle's weights next to the driver spread."""
     R, r = case["R"], case["r"]
     for c in case["comps"]:
         w, wp = r.weights(COMP_ID[c])
         w = w.cpu().numpy()
         assert np.array_equal(wp.cpu().numpy(), R.w_ptr)
-        # weights are an intermediate (unique only up to the system's conditioning): 10x the spread
-        spread = max(nerr(case["R2"].weights[c], R.weights[c]), nerr(case["R3"].weights[c], R.weights[c]))
-        assert nerr(w, R.weights[c]) < fp64_tol(spread, 10.0), c
+        record_property("weights_%s_dist_to_oracle" % c, nerr(w, R.weights[c]))
+        record_property("weights_%s_driver_spread" % c, nerr(case["R2"].weights[c], R.weights[c]))
+        worst = 0.0
+        for i in range(R.basis.n):
+            A, _ = R.local_system(i, c)
+            b = R.moments[c][R.row_ptr[i]:R.row_ptr[i + 1]]
+            sl = slice(R.w_ptr[i], R.w_ptr[i + 1])
+            bs = max(np.max(np.abs(b)), 1e-300)
+            res_gpu = np.max(np.abs(A @ w[sl] - b)) / bs
+            res_ora = np.max(np.abs(A @ R.weights[c][sl] - b)) / bs
+            worst = max(worst, res_gpu)
+            assert res_gpu <= max(1e-12, 10.0 * res_ora), (c, i, res_gpu, res_ora)
+        record_property("weights_%s_exactness_residual" % c, worst)
         n_trunc = int(np.sum(R.rank[c] < np.diff(R.row_ptr)))
         assert r.info.n_truncated[COMP_ID[c]] == n_trunc, c
 
@@ -149,7 +161,7 @@ def _ops(case, kap, alpha):
     return ops
 
 
-def test_assembly_f64_and_f32(case, W):
+def test_assembly_f64_and_f32(case, W, record_property):
     import torch
     R, r = case["R"], case["r"]
     kap = _kappa(R.x)
@@ -157,8 +169,14 @@ def test_assembly_f64_and_f32(case, W):
     kd = torch.tensor(kap, device="cuda")
     for op, terms in _ops(case, kap, alpha).items():
         ref = R.assemble(terms)
-        tol = fp64_tol(max(nerr(case["R2"].assemble(terms), ref), nerr(case["R3"].assemble(terms), ref)))
+        spread = nerr(case["R2"].assemble(terms), ref)
+        tol = fp64_tol(spread)
         got = r.assemble(op, kd, alpha=alpha, prec=W.PREC_F64).cpu().numpy()
+        record_property("op%d_fp64_err_vs_oracle" % op, nerr(got, ref))
+        record_property("op%d_driver_spread" % op, spread)
+        record_property("op%d_fp64_bar" % op, tol)
+        print(case["name"], "op", op, "FP64 error vs oracle %.3e, bar %.3e (driver spread %.3e)"
+              % (nerr(got, ref), tol, spread))
         assert nerr(got, ref) < tol, (op, nerr(got, ref), tol)
         got32 = r.assemble(op, kd, alpha=alpha, prec=W.PREC_F32).cpu().numpy()
         assert nerr(got32, got) < 1e-6, (op, nerr(got32, got))
@@ -255,7 +273,7 @@ def test_heat_tangent_operator(case, W):
     terms = ([("N", "N", np.full(R.Q, alpha))] + [(g, g, kap_q) for g in grads]
              + [(g, "N", dks[d](R.x)) for d, g in enumerate(grads)])
     ref = R.assemble(terms)
-    spread = max(nerr(case["R2"].assemble(terms), ref), nerr(case["R3"].assemble(terms), ref))
+    spread = nerr(case["R2"].assemble(terms), ref)
     coef = torch.tensor(np.stack([kap_q] + [f(R.x) for f in dks]), device="cuda")
     got = r.assemble(W.OP_HEAT_J, coef, alpha=alpha, prec=W.PREC_F64).cpu().numpy()
     assert nerr(got, ref) < fp64_tol(spread), (nerr(got, ref), fp64_tol(spread))

@@ -218,3 +218,39 @@ def test_table2_mode_on_disk_and_well_posed():
         for i in range(B.n):
             assert sum(int(side[k]) ** 2 for k in B.supp[i]) >= rp[i + 1] - rp[i]
         assert set(np.unique(side)) <= {2, 3, 4, 5, 6}
+
+
+def test_heat_residual_identity_with_assembled_matrices(disk_rule):
+    """The discrete heat residual (Sec. 5.1, theta = 1) through the assembled WQ matrices:
+    R = M (u - u_old) / dt + K(k(u_h)) u - M(f) 1, with M the WQ mass matrix (c = 1),
+    K(k) the WQ stiffness with coefficient k(u_h(x_q)) and M(f) 1 = sum_q w_iq f_q
+    (partition of unity).  A non-zero, non-constant source f and u != u_old make a
+    wrong sign or a dropped term of the transient or source part fail (the tangent test
+    pins only the part that depends on u)."""
+    R = disk_rule
+    B = R.basis
+    rng = np.random.Generator(np.random.PCG64(47))
+    u = 0.4 + 0.3 * rng.standard_normal(B.n)
+    u_old = u + 0.2 * rng.standard_normal(B.n)
+    dt = 0.05
+    kap = lambda v: 1.0 + v * v
+    f = 2.0 + np.sin(3.0 * R.x[:, 0]) * np.cos(2.0 * R.x[:, 1])
+    res = R.heat_residual(u, u_old, dt, kap, f=f)
+
+    def matvec(vals, v):
+        y = np.zeros(B.n)
+        for i in range(B.n):
+            r0, r1 = R.row_ptr[i], R.row_ptr[i + 1]
+            y[i] = vals[r0:r1] @ v[R.col[r0:r1]]
+        return y
+
+    uq, _ = R.interp(u)
+    M = R.assemble([("N", np.ones(R.Q))])
+    K = R.assemble([("x", kap(uq)), ("y", kap(uq))])
+    Mf = R.assemble([("N", f)])
+    ref = matvec(M, (u - u_old) / dt) + matvec(K, u) - matvec(Mf, np.ones(B.n))
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(res - ref)) <= 1e-12 * scale
+    # the source and transient parts are each large enough to be seen
+    assert np.max(np.abs(matvec(Mf, np.ones(B.n)))) > 1e-3 * scale
+    assert np.max(np.abs(matvec(M, (u - u_old) / dt))) > 1e-3 * scale
