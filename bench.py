@@ -311,9 +311,103 @@ def bench_ours(args, rank, world):
         res["cpu_ref"] = cpu_ref_measure(rule, basis, coef.cpu().numpy(), coef_g.cpu().numpy(), a64, g64)
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
-    if not args.no_configs:
+    if not args.no_configs and world == 1:
         res["other_configs"] = other_configs(ctx, flush, max(args.steps // 20, 20), args.warmup, hbm)
+        res["other_configs"]["5_batched_%d_instances" % args.config5_instances] = config5_measure(
+            ctx, flush, max(args.steps // 100, 10), args.warmup, hbm, args.config5_instances)
     return res
+
+
+def config5_measure(ctx, flush, steps, warmup, hbm=6800.0, n_instances=256):
+    """Batched assembly of many independent instances: n_instances planar meshes of
+    500-50,000 elements (log-uniform target; each mesh is the refinement level nearest
+    to it), 1-20 EPs of valence 3-8.  All rules are built by one call whose weight
+    systems -- every row of the N, d_x and d_y components of every instance -- are
+    solved in one persistent launch; the rules leave out the tensor-core and tile
+    plans (device memory).  Mass + stiffness (coefficient kappa at the points) in
+    compensated FP32: one batched launch pair per operator, against one call per
+    instance and against per-instance Gauss assembly, same protocol (L2 flushed, CUDA
+    events, median).  The FP32 error is measured against FP64 on the eight largest
+    instances."""
+    import gc
+    import torch
+    from paper_2605_29334_gb300 import wq
+    from wq_synth import meshes
+    t0 = time.perf_counter()
+    ms = meshes.instances(5001, n_instances, 500, 50000, workers=max(1, min(16, os.cpu_count() or 1)))
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bases = [wq.Basis(ctx, m) for m in ms]
+    t_basis = time.perf_counter() - t0
+    n_faces = [len(m["quads"]) for m in ms]
+    del ms
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    t0 = time.perf_counter()
+    rules = wq.build_rules(bases, comps=[wq.COMP_N, wq.COMP_X, wq.COMP_Y],
+                           skip_plans=wq.PLAN_NO_TC | wq.PLAN_NO_TILE)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    rule_bytes = free0 - torch.cuda.mem_get_info()[0]
+    info = rules[0].info
+    cqs = [torch.tensor(meshes.kappa_sines(rr.points().cpu().numpy()), device="cuda") for rr in rules]
+    cgs = [torch.tensor(meshes.kappa_sines(rr.gauss_points().cpu().numpy()), device="cuda") for rr in rules]
+    om = [torch.empty(rr.nnz, dtype=torch.float32, device="cuda") for rr in rules]
+    ok = [torch.empty(rr.nnz, dtype=torch.float32, device="cuda") for rr in rules]
+    batch = wq.Batch(rules)
+    nnz = sum(rr.nnz for rr in rules)
+    nnz5 = 2 * nnz                                   # mass + stiffness
+
+    def b_wq():
+        batch.assemble(wq.OP_MASS, cqs, prec=wq.PREC_F32, outs=om)
+        batch.assemble(wq.OP_STIFF, cqs, prec=wq.PREC_F32, outs=ok)
+
+    def per_wq():
+        for rr, c, a, b in zip(rules, cqs, om, ok):
+            rr.assemble(wq.OP_MASS, c, prec=wq.PREC_F32, out=a)
+            rr.assemble(wq.OP_STIFF, c, prec=wq.PREC_F32, out=b)
+
+    def per_gq():
+        for rr, c, a, b in zip(rules, cgs, om, ok):
+            rr.gq_assemble(wq.OP_MASS, c, prec=wq.PREC_F32, out=a)
+            rr.gq_assemble(wq.OP_STIFF, c, prec=wq.PREC_F32, out=b)
+    tb = float(np.median(time_steps(b_wq, steps, warmup, flush)))
+    tp = float(np.median(time_steps(per_wq, steps, warmup, flush)))
+    tq = float(np.median(time_steps(per_gq, steps, warmup, flush)))
+    # FP32 error against FP64 on the largest instances
+    errs = []
+    for k in np.argsort([-rr.nnz for rr in rules])[:8]:
+        rr, c = rules[int(k)], cqs[int(k)]
+        for op in (wq.OP_MASS, wq.OP_STIFF):
+            a64 = rr.assemble(op, c, prec=wq.PREC_F64)
+            a32 = rr.assemble(op, c, prec=wq.PREC_F32).to(torch.float64)
+            errs.append(float((a32 - a64).abs().max() / a64.abs().max()))
+    # algorithmic HBM bytes of the batched step (sum_e m_e P_e = sum_i r_i): weights and
+    # used table components 8 B per (weight row, term) each, the coefficient 8 B per point
+    # per operator, the float values; mass 1 term, stiffness 2
+    sum_r = sum(int(rr.info.sum_r) for rr in rules)
+    n_pts = sum(int(rr.Q) for rr in rules)
+    step_bytes = 2 * (sum_r * 3 * 8) + 2 * n_pts * 8 + nnz5 * 4
+    achieved = step_bytes / (tb * 1e-3) / 1e9
+    out = {"n_instances": len(rules), "n_faces": int(sum(n_faces)), "faces_min": int(min(n_faces)),
+           "faces_max": int(max(n_faces)), "n_elements": int(sum(bb.E for bb in bases)),
+           "n_functions": int(sum(bb.n for bb in bases)), "nnz_mass_plus_stiffness": int(nnz5),
+           "n_weight_systems": 3 * int(sum(bb.n for bb in bases)),
+           "wq_f32_batched_nnz_per_s": nnz5 / tb * 1e3, "wq_f32_per_instance_nnz_per_s": nnz5 / tp * 1e3,
+           "gq_f32_per_instance_nnz_per_s": nnz5 / tq * 1e3, "batched_ms": tb, "per_instance_ms": tp,
+           "gq_per_instance_ms": tq, "speedup_batched_over_per_instance": tp / tb,
+           "speedup_batched_wq_over_gq": tq / tb, "f32_rel_err_vs_f64_max_largest8": max(errs),
+           "roofline_wq_f32_batched_step": {"bound": "hbm", "algorithmic_bytes": int(step_bytes), "unit": "GB/s",
+                                            "peak": hbm, "achieved": achieved, "frac": achieved / hbm},
+           "setup": {"generate_s": t_gen, "host_basis_s": t_basis, "rule_build_wall_s": t_build,
+                     "batched_tsvd_ms": info.tsvd_ms, "batched_tsvd_gflop": info.tsvd_gflop,
+                     "batched_tsvd_fp64_tflops": info.tsvd_gflop / max(info.tsvd_ms, 1e-9),
+                     "rule_device_bytes": int(rule_bytes)},
+           "steps": steps}
+    del batch, om, ok, cqs, cgs, rules, bases
+    gc.collect()
+    torch.cuda.empty_cache()
+    return out
 
 
 def _timed_pair(fn_wq, fn_gq, out_wq, out_gq, steps, warmup, flush):
@@ -327,9 +421,8 @@ def _timed_pair(fn_wq, fn_gq, out_wq, out_gq, steps, warmup, flush):
 def other_configs(ctx, flush, steps, warmup, hbm=6800.0):
     """The other workloads of the method, same protocol (assembly only, L2 flushed, CUDA
     events, median): WQ against Gauss on the same GPU at FP32 (compensated) and FP64,
-    with the FP32 error against the FP64 result.  Config 5 is a reduced batch (16
-    instances of 500-5,000 elements instead of 256 of 500-50,000), assembled by one
-    launch pair and compared with one call per instance."""
+    with the FP32 error against the FP64 result (configs 1, 3 and 4; the batched
+    instances are config5_measure)."""
     import torch
     from paper_2605_29334_gb300 import wq
     from wq_synth import meshes
@@ -405,34 +498,6 @@ def other_configs(ctx, flush, steps, warmup, hbm=6800.0):
                     "linear_iterations": o["linear_iterations"], "wall_s": o["wall_s"]}
         del nt
     out["4_heat_tangent_L5"]["newton_20_iterations"] = runs
-    # config 5 (reduced): batched against per-instance calls and Gauss
-    ms = meshes.instances(5001, 16, 500, 5000)
-    bases = [wq.Basis(ctx, m) for m in ms]
-    rules = [wq.Rule(bb, comps=[wq.COMP_N, wq.COMP_X, wq.COMP_Y]) for bb in bases]
-    cqs = [torch.tensor(meshes.kappa_sines(rr.points().cpu().numpy()), device="cuda") for rr in rules]
-    cgs = [torch.tensor(meshes.kappa_sines(rr.gauss_points().cpu().numpy()), device="cuda") for rr in rules]
-    outs = [torch.empty(rr.nnz, dtype=torch.float32, device="cuda") for rr in rules]
-    batch = wq.Batch(rules)
-    nnz5 = 2 * sum(rr.nnz for rr in rules)             # mass + stiffness
-    def b_wq():
-        batch.assemble(wq.OP_MASS, cqs, prec=wq.PREC_F32, outs=outs)
-        batch.assemble(wq.OP_STIFF, cqs, prec=wq.PREC_F32, outs=outs)
-    def per_wq():
-        for rr, c, o in zip(rules, cqs, outs):
-            rr.assemble(wq.OP_MASS, c, prec=wq.PREC_F32, out=o)
-            rr.assemble(wq.OP_STIFF, c, prec=wq.PREC_F32, out=o)
-    def per_gq():
-        for rr, c, o in zip(rules, cgs, outs):
-            rr.gq_assemble(wq.OP_MASS, c, prec=wq.PREC_F32, out=o)
-            rr.gq_assemble(wq.OP_STIFF, c, prec=wq.PREC_F32, out=o)
-    tb = float(np.median(time_steps(b_wq, steps, warmup, flush)))
-    tp = float(np.median(time_steps(per_wq, steps, warmup, flush)))
-    tq = float(np.median(time_steps(per_gq, steps, warmup, flush)))
-    out["5_batched_16_instances"] = {"n_instances": len(rules), "n_elements": int(sum(bb.E for bb in bases)),
-                                     "nnz_mass_plus_stiffness": nnz5,
-                                     "wq_f32_batched_nnz_per_s": nnz5 / tb * 1e3,
-                                     "wq_f32_per_instance_nnz_per_s": nnz5 / tp * 1e3,
-                                     "gq_f32_per_instance_nnz_per_s": nnz5 / tq * 1e3}
     return out
 
 
@@ -645,6 +710,7 @@ def main():
     ap.add_argument("--prec", default="auto", choices=["auto", "tc", "f32", "f32_fast", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (configs 1, 3, 4, 5)")
+    ap.add_argument("--config5-instances", type=int, default=256, help="instances of the batched workload")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

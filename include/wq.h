@@ -145,7 +145,14 @@ typedef struct {
     double tsvd_rel_tol;      /* keep sigma_k >= tol * sigma_max (paper: tiny sigma dropped); 1e-12 */
     int32_t max_sweeps;       /* Jacobi sweep cap (default 40 when 0) */
     void* stream;             /* stream for the build (NULL: legacy default) */
+    uint32_t skip_plans;      /* wq_plan bits: assembly plans not to build (0: all) */
 } wq_rule_opts;
+
+/* Assembly plans a rule may leave out to save device memory (wq_rule_opts.skip_plans):
+ * WQ_PLAN_NO_TC drops the tensor-core slices (WQ_PREC_TC then returns WQ_ERR_ARG; about
+ * 15 KB per regular element), WQ_PLAN_NO_TILE the tile engine's element-major packs (the
+ * float modes then use WQ_VARIANT_SLOTMAP; about 20 KB per regular element). */
+typedef enum { WQ_PLAN_NO_TC = 1, WQ_PLAN_NO_TILE = 2 } wq_plan;
 
 typedef struct {
     int64_t n_points;         /* Q: WQ points (Sec. 4.1 placement) */
@@ -224,6 +231,19 @@ wq_status wq_point_counts(const wq_basis* basis, int32_t count_mode, int32_t* h_
  * Errors: WQ_ERR_NO_DEVICE, WQ_ERR_OOM, WQ_ERR_CUDA, WQ_ERR_ILLPOSED,
  * WQ_ERR_NOT_CONVERGED, WQ_ERR_NONFINITE. */
 wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out);
+/* The rules of k >= 1 bases (independent mesh instances on one device) with the same
+ * options, their truncated-SVD systems (Sec. 4.3) -- every row of every built
+ * component of every instance -- solved in ONE persistent launch whose CTAs take
+ * the systems from a queue ordered by estimated Jacobi work (n_i^2 r_i, largest
+ * first), so that the uneven systems next to extraordinary points spread over the
+ * GPU.  Each system is solved by the same code as in wq_rule_build, so the weights
+ * are bitwise those of k separate builds.  out [k] (host, caller-owned array)
+ * receives the rules, each freed by wq_rule_destroy; on error every entry is NULL
+ * and nothing is kept.  wq_rule_info.tsvd_ms and tsvd_gflop of each rule report the
+ * shared launch; setup_ms runs from the rule's first device step to its last.
+ * The paper builds one mesh at a time; this is the batching of many.  Errors: those
+ * of wq_rule_build, WQ_ERR_ARG (k < 1, null base, bases on different devices). */
+wq_status wq_rule_build_batched(int32_t k, wq_basis* const* bases, const wq_rule_opts* opts, wq_rule** out);
 /* Frees the rule and its device arrays (NULL is ignored). */
 void wq_rule_destroy(wq_rule* rule);
 /* Sizes and weight statistics (wq_rule_info).  Errors: WQ_ERR_ARG. */

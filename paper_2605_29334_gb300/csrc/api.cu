@@ -323,13 +323,43 @@ uint64_t basis_fingerprint(const wqi::BasisHost& B) {
     mix(B.topo.quads.data(), B.topo.quads.size() * sizeof(int32_t));
     return h;
 }
+
+// What a rule build carries from its first device phase (plan, uploads, point tables,
+// moments) through the weight solves to its last phase (split copies, packs,
+// tensor-core plan).  The device arrays belong to the rule.
+struct BuildState {
+    cudaStream_t st = nullptr;
+    double tol = 1e-12;
+    int sweeps = 40;
+    const SavedRule* saved = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int32_t* d_rank = nullptr;      // [nwc][n] rank of every system
+    uint8_t* d_zid = nullptr;       // [nwc][n] Z = I flags
+    double* d_flops = nullptr;
+    int32_t *d_Pw = nullptr, *d_Pg = nullptr;
+    int64_t *d_sw_off = nullptr, *d_tw_off = nullptr, *d_sg_off = nullptr, *d_tg_off = nullptr;
+    int64_t *d_wbase = nullptr, *d_tmx_off = nullptr;
+    int64_t bt_E = 0, gbt_E = 0;
+    int64_t per_cta = 0;            // weight-solve scratch per CTA (doubles)
+    std::vector<double> row_cost;   // n_i^2 r_i: the Jacobi work of each row's system
+    BuildState() = default;
+    BuildState(const BuildState&) = delete;
+    BuildState& operator=(const BuildState&) = delete;
+    ~BuildState() {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
 }  // namespace
 
 // A CUDA error left pending by another caller (or by a teardown) must not be reported
 // by this library's next launch check: entry points that launch work drop it first.
 static inline void drop_stale_error() { (void)cudaGetLastError(); }
 
-static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, const SavedRule* saved, wq_rule** out) {
+// First phase of a rule build: host plan, uploads, placement, basis tables and Gauss
+// moments (queued on the build stream, not waited for).  On failure the rule is freed.
+static wq_status rule_prepare(wq_basis* basis, const wq_rule_opts* opts, const SavedRule* saved, wq_rule** out,
+                              BuildState& bs) {
     if (!basis || !opts || !out) return WQ_ERR_ARG;
     *out = nullptr;
     wq_ctx* ctx = basis->ctx;
@@ -396,6 +426,7 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
     std::vector<uint8_t> il(R->nsupp);
     for (int64_t s = 0; s < R->nsupp; ++s) pos_ptr[s + 1] = pos_ptr[s] + m[B.supp[s]];
     std::vector<uint16_t> pos(pos_ptr[R->nsupp]);
+    bs.row_cost.assign(n, 0.0);
     for (int64_t i = 0; i < n; ++i) {
         const int32_t* c0 = B.col.data() + B.row_ptr[i];
         const int32_t* c1 = B.col.data() + B.row_ptr[i + 1];
@@ -415,6 +446,8 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         }
         w_ptr[i + 1] = w_ptr[i] + r;
         R->max_r = std::max<int>(R->max_r, (int)r);
+        const double ni = (double)(B.row_ptr[i + 1] - B.row_ptr[i]);
+        bs.row_cost[i] = ni * ni * (double)r;
         if (r < B.row_ptr[i + 1] - B.row_ptr[i])
             return bail(fail(ctx, WQ_ERR_ILLPOSED, "r_i < n_i for test function " + std::to_string(i)));
     }
@@ -504,6 +537,7 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         bsp_gq[e + 1] = bsp_gq[e] + (int64_t)nc * ncb * ((pg + 3) / 4) * wqd::WQ_TC_QUARTER_WORDS;
     }
     if (bsp_wq[E] > INT32_MAX || bsp_gq[E] > INT32_MAX || B.fn_ptr[E] > INT32_MAX) R->tc_ok = false;
+    if (opts->skip_plans & WQ_PLAN_NO_TC) R->tc_ok = false;
     for (size_t x = 0; x < it_wq.size(); ++x) {
         const int32_t e = ie_wq[x];
         it2_wq[x] = make_int4((int)B.fn_ptr[e], (int)bsp_wq[e], e, (side[e] * side[e] + 3) / 4 * 4);
@@ -560,6 +594,7 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         tmx_off[e + 1] = tmx_off[e] + (int64_t)nc * ncb;
     }
     if (std::max({sw_off[E], tw_off[E], sg_off[E], tg_off[E]}) > INT32_MAX) R->tile_ok = false;
+    if (opts->skip_plans & WQ_PLAN_NO_TILE) R->tile_ok = false;
     // row-major slot layout of the element blocks: row i's support entries in support
     // order, each ceil(m_e / 16) blocks of 16 slots; the slot block of (row i, element e)
     // receives element e's block row of function i (kdst), pos2 the positions in row i
@@ -669,20 +704,30 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         return bail(sst);
     for (int c = 0; c < 5; ++c)
         if (R->wcidx[c] >= 0 && !dalloc(R, R->d_mom[c], (size_t)R->nnz, sst)) return bail(sst);
-    int32_t* d_rank = nullptr;
-    uint8_t* d_zid = nullptr;
-    double* d_flops = nullptr;
-    if (!dalloc(R, d_rank, (size_t)n, sst) || !dalloc(R, d_zid, (size_t)n, sst) || !dalloc(R, d_flops, 1, sst))
+    const int64_t nw = std::max(R->nwc, 1);
+    if (!dalloc(R, bs.d_rank, (size_t)(n * nw), sst) || !dalloc(R, bs.d_zid, (size_t)(n * nw), sst) ||
+        !dalloc(R, bs.d_flops, 1, sst))
         return bail(sst);
-    // TSVD scratch: one slice per resident CTA
+    // weight-solve scratch per CTA (allocated by the solve, freed after it)
     const int64_t mn = R->max_n_i, mr = R->max_r;
-    const int64_t per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
+    bs.per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
     R->n_sm = std::max(n_sm, 1);
-    int n_cta = (int)std::min<int64_t>(n, (int64_t)std::max(n_sm, 1) * 8);
-    double* d_scratch = nullptr;
-    if (!saved && !dalloc(R, d_scratch, (size_t)per_cta * n_cta, sst)) return bail(sst);
+    bs.st = st;
+    bs.tol = tol;
+    bs.sweeps = sweeps;
+    bs.saved = saved;
+    bs.d_Pw = d_Pw;
+    bs.d_Pg = d_Pg;
+    bs.d_sw_off = d_sw_off;
+    bs.d_tw_off = d_tw_off;
+    bs.d_sg_off = d_sg_off;
+    bs.d_tg_off = d_tg_off;
+    bs.d_wbase = d_wbase;
+    bs.d_tmx_off = d_tmx_off;
+    bs.bt_E = bt_ptr[E];
+    bs.gbt_E = gbt_ptr[E];
 
     wqd::Elems& el = R->el;
     el.dim = B.dim;
@@ -755,15 +800,12 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         cudaError_t pe = wqd::prepare_tile_kernels();
         if (pe != cudaSuccess) return bail(fail(ctx, WQ_ERR_CUDA, std::string("tile kernels: ") + cudaGetErrorString(pe)));
     }
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    auto cleanup_events = [&]() {
-        cudaEventDestroy(ev0);
-        cudaEventDestroy(ev1);
-    };
-    cudaEventRecord(ev0, st);
-    cudaError_t ce = cudaMemsetAsync(R->d_status, 0, sizeof(unsigned), st);
+    if (cudaEventCreate(&bs.ev0) != cudaSuccess || cudaEventCreate(&bs.ev1) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, WQ_ERR_CUDA, "rule build: event creation failed"));
+    }
+    cudaError_t ce = cudaEventRecord(bs.ev0, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(R->d_status, 0, sizeof(unsigned), st);
     // a2 + a3: placement and basis tables at WQ and Gauss points
     if (ce == cudaSuccess)
         ce = wqd::launch_eval(el, R->d_pt_elem, R->Q, 0, R->d_table, R->d_x, nullptr, R->d_status, st);
@@ -775,48 +817,87 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         ce = wqd::launch_moments_f64(rw, R->d_desc_gq, table_comp(R, c), nc, R->d_gtable, R->d_gw, R->d_mom[c],
                                      R->max_n_i, st);
     }
-    // a5: truncated-SVD weights per component (timed, FP64 operations counted)
+    if (ce != cudaSuccess) return bail(fail(ctx, WQ_ERR_CUDA, std::string("rule build: ") + cudaGetErrorString(ce)));
+    *out = R;
+    return WQ_OK;
+}
+
+// Weight statistics (truncated systems, Z = I fallbacks) of every built component from
+// the per-row ranks and flags the solves wrote; waits for the build stream.
+static cudaError_t weight_stats(wq_rule* R, BuildState& bs) {
+    const int64_t n = R->n;
+    const wqi::BasisHost& B = R->basis->B;
     std::vector<int32_t> rank(n);
     std::vector<uint8_t> zid(n);
-    cudaEvent_t evt0 = nullptr, evt1 = nullptr;
-    if (!saved && ce == cudaSuccess) {
-        ce = cudaMemsetAsync(d_flops, 0, sizeof(double), st);
-        if (ce == cudaSuccess) ce = cudaEventCreate(&evt0);
-        if (ce == cudaSuccess) ce = cudaEventCreate(&evt1);
-        if (ce == cudaSuccess) ce = cudaEventRecord(evt0, st);
-    }
-    for (int c = 0; c < 5 && ce == cudaSuccess && !saved; ++c) {
+    for (int c = 0; c < 5; ++c) {
         if (R->wcidx[c] < 0) continue;
-        ce = wqd::launch_tsvd(el, rw, R->d_table, table_comp(R, c), R->d_mom[c], R->d_W, R->nwc, R->wcidx[c], tol,
-                              sweeps, d_scratch, per_cta, n_cta, d_rank, d_zid, R->d_status, d_flops, st);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(rank.data(), d_rank, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(zid.data(), d_zid, n, cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        if (ce == cudaSuccess) {
-            int trunc = 0, zcount = 0;
-            for (int64_t i = 0; i < n; ++i) {
-                trunc += rank[i] < (B.row_ptr[i + 1] - B.row_ptr[i]);
-                zcount += zid[i];
-            }
-            R->info.n_truncated[c] = trunc;
-            R->info.n_z_identity[c] = zcount;
+        const int64_t k = R->wcidx[c];
+        cudaError_t ce = cudaSuccess;
+        if (n > 0) {
+            ce = cudaMemcpyAsync(rank.data(), bs.d_rank + k * n, n * sizeof(int32_t), cudaMemcpyDeviceToHost, bs.st);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(zid.data(), bs.d_zid + k * n, n, cudaMemcpyDeviceToHost, bs.st);
         }
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(bs.st);
+        if (ce != cudaSuccess) return ce;
+        int trunc = 0, zcount = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            trunc += rank[i] < (B.row_ptr[i + 1] - B.row_ptr[i]);
+            zcount += zid[i];
+        }
+        R->info.n_truncated[c] = trunc;
+        R->info.n_z_identity[c] = zcount;
     }
-    if (evt0 && evt1 && ce == cudaSuccess) {
-        // the per-component synchronisations above sit inside this interval; they wait on
-        // the device, which is what the interval measures
-        double fl = 0.0;
-        float tms = 0.0f;
-        ce = cudaEventRecord(evt1, st);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&fl, d_flops, sizeof(double), cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tms, evt0, evt1);
-        R->info.tsvd_ms = tms;
-        R->info.tsvd_gflop = fl * 1e-9;
+    return cudaSuccess;
+}
+
+// a5 for one rule: the truncated-SVD weights of every built component, one launch per
+// component (timed, FP64 operations counted); the scratch lives for the solves only.
+static wq_status rule_weights_single(wq_rule* R, BuildState& bs) {
+    wq_ctx* ctx = R->ctx;
+    const int n_cta = (int)std::min<int64_t>(R->n, (int64_t)R->n_sm * 8);
+    double* d_scratch = nullptr;
+    if (n_cta > 0 && cudaMalloc(&d_scratch, (size_t)bs.per_cta * n_cta * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, WQ_ERR_OOM, "weight-solve scratch allocation failed");
     }
+    cudaEvent_t evt0 = nullptr, evt1 = nullptr;
+    cudaError_t ce = cudaMemsetAsync(bs.d_flops, 0, sizeof(double), bs.st);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&evt0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&evt1);
+    if (ce == cudaSuccess) ce = cudaEventRecord(evt0, bs.st);
+    for (int c = 0; c < 5 && ce == cudaSuccess; ++c) {
+        if (R->wcidx[c] < 0) continue;
+        const int64_t k = R->wcidx[c];
+        ce = wqd::launch_tsvd(R->el, R->rw, R->d_table, table_comp(R, c), R->d_mom[c], R->d_W, R->nwc, (int)k, bs.tol,
+                              bs.sweeps, d_scratch, bs.per_cta, n_cta, bs.d_rank + k * R->n, bs.d_zid + k * R->n,
+                              R->d_status, bs.d_flops, bs.st);
+    }
+    double fl = 0.0;
+    float tms = 0.0f;
+    if (ce == cudaSuccess) ce = cudaEventRecord(evt1, bs.st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&fl, bs.d_flops, sizeof(double), cudaMemcpyDeviceToHost, bs.st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(bs.st);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tms, evt0, evt1);
     if (evt0) cudaEventDestroy(evt0);
     if (evt1) cudaEventDestroy(evt1);
-    if (saved && ce == cudaSuccess) {
+    if (d_scratch) cudaFree(d_scratch);   // after the synchronisation (cudaFree waits itself otherwise)
+    if (ce == cudaSuccess) ce = weight_stats(R, bs);
+    if (ce != cudaSuccess) return fail(ctx, WQ_ERR_CUDA, std::string("weight solves: ") + cudaGetErrorString(ce));
+    R->info.tsvd_ms = tms;
+    R->info.tsvd_gflop = fl * 1e-9;
+    return WQ_OK;
+}
+
+// Last phase: saved weights (loaded rule), FP32 split copies, element-major packs,
+// tensor-core plan; waits for the build stream and reads the device status.
+static wq_status rule_finish(wq_rule* R, BuildState& bs) {
+    wq_ctx* ctx = R->ctx;
+    const SavedRule* saved = bs.saved;
+    cudaStream_t st = bs.st;
+    const int64_t E = R->E;
+    const int nc = R->nc;
+    cudaError_t ce = cudaSuccess;
+    if (saved) {
         // weights and moments from the file (host buffers live until the synchronisation below)
         ce = cudaMemcpyAsync(R->d_W, saved->W.data(), saved->W.size() * sizeof(double), cudaMemcpyHostToDevice, st);
         int k = 0;
@@ -832,8 +913,8 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         }
     }
     // FP32 split copies for the mixed-precision assembly
-    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_table, R->d_table2, bt_ptr[E], st);
-    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gtable, R->d_gtable2, gbt_ptr[E], st);
+    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_table, R->d_table2, bs.bt_E, st);
+    if (ce == cudaSuccess) ce = wqd::launch_split_f32(R->d_gtable, R->d_gtable2, bs.gbt_E, st);
     if (ce == cudaSuccess) ce = wqd::launch_split_rows(R->d_W, R->d_wrow_dst, R->d_W2, R->sum_r, R->nwc, R->n_sm, st);
     if (ce == cudaSuccess) ce = wqd::launch_copy_rows(R->d_W, R->d_wrow_dst, R->d_We, R->sum_r, R->nwc, R->n_sm, st);
     // element-major packs of the tile engine
@@ -845,24 +926,24 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         pj.nwc = R->nwc;
         pj.kind = wqd::PK_W2E;   // WQ test side: the split weights
         pj.ncomp = R->nwc;
-        pj.P = d_Pw;
-        pj.src_off = d_wbase;
-        pj.out_off = d_sw_off;
+        pj.P = bs.d_Pw;
+        pj.src_off = bs.d_wbase;
+        pj.out_off = bs.d_sw_off;
         pj.f2 = R->d_W2;
         pj.out = R->d_pk_sw;
         if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
         pj.kind = wqd::PK_TABLE2;   // WQ trial side: the split table
         pj.ncomp = nc;
         pj.src_off = R->d_bt_ptr;
-        pj.out_off = d_tw_off;
+        pj.out_off = bs.d_tw_off;
         pj.f2 = R->d_table2;
         pj.out = R->d_pk_tw;
         if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
-        if (ce == cudaSuccess) ce = wqd::launch_pack_max(pj, d_tmx_off, R->d_tmx_wq, st);
+        if (ce == cudaSuccess) ce = wqd::launch_pack_max(pj, bs.d_tmx_off, R->d_tmx_wq, st);
         pj.kind = wqd::PK_GAUSS;   // Gauss test side: Gauss weight x table, split
-        pj.P = d_Pg;
+        pj.P = bs.d_Pg;
         pj.src_off = R->d_gbt_ptr;
-        pj.out_off = d_sg_off;
+        pj.out_off = bs.d_sg_off;
         pj.f64 = R->d_gtable;
         pj.gw = R->d_gw;
         pj.pt0 = R->d_gp_ptr;
@@ -870,11 +951,11 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
         if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
         pj.kind = wqd::PK_TABLE2;   // Gauss trial side: the split Gauss table
         pj.pt0 = nullptr;
-        pj.out_off = d_tg_off;
+        pj.out_off = bs.d_tg_off;
         pj.f2 = R->d_gtable2;
         pj.out = R->d_pk_tg;
         if (ce == cudaSuccess) ce = wqd::launch_pack(pj, st);
-        if (ce == cudaSuccess) ce = wqd::launch_pack_max(pj, d_tmx_off, R->d_tmx_gq, st);
+        if (ce == cudaSuccess) ce = wqd::launch_pack_max(pj, bs.d_tmx_off, R->d_tmx_gq, st);
     }
     // trial-side slices and test-side bounds of the tensor-core contraction
     if (R->tc_ok) {
@@ -886,30 +967,150 @@ static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, cons
             ce = wqd::launch_tc_prep(E, nc, R->nwc, R->d_m, R->d_gtable, nullptr,
                                      {R->d_tcel_gq, R->d_bsp_gq, R->d_bs_gq, R->d_fexp_gq, R->d_vmax_gq}, st);
     }
-    if (ce == cudaSuccess) ce = cudaEventRecord(ev1, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(bs.ev1, st);
     unsigned hstat = 0;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstat, R->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) {
-        cleanup_events();
-        return bail(fail(ctx, WQ_ERR_CUDA, std::string("rule build: ") + cudaGetErrorString(ce)));
-    }
+    if (ce != cudaSuccess) return fail(ctx, WQ_ERR_CUDA, std::string("rule build: ") + cudaGetErrorString(ce));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    cleanup_events();
+    cudaEventElapsedTime(&ms, bs.ev0, bs.ev1);
     wq_status s2 = status_to_error(ctx, hstat);
-    if (s2 != WQ_OK) return bail(s2);
+    if (s2 != WQ_OK) return s2;
     R->info.n_points = R->Q;
     R->info.n_gauss = R->G;
     R->info.sum_r = R->sum_r;
     R->info.max_r = R->max_r;
     R->info.setup_ms = ms;
+    return WQ_OK;
+}
+
+static wq_status rule_build_impl(wq_basis* basis, const wq_rule_opts* opts, const SavedRule* saved, wq_rule** out) {
+    BuildState bs;
+    wq_rule* R = nullptr;
+    wq_status s = rule_prepare(basis, opts, saved, &R, bs);
+    if (s != WQ_OK) return s;
+    if (!saved) s = rule_weights_single(R, bs);
+    if (s == WQ_OK) s = rule_finish(R, bs);
+    if (s != WQ_OK) {
+        delete R;
+        return s;
+    }
     *out = R;
     return WQ_OK;
 }
 
 wq_status wq_rule_build(wq_basis* basis, const wq_rule_opts* opts, wq_rule** out) {
     return rule_build_impl(basis, opts, nullptr, out);
+}
+
+wq_status wq_rule_build_batched(int32_t k, wq_basis* const* bases, const wq_rule_opts* opts, wq_rule** out) {
+    drop_stale_error();
+    if (!bases || !opts || !out || k < 1) return WQ_ERR_ARG;
+    for (int r = 0; r < k; ++r) out[r] = nullptr;
+    for (int r = 0; r < k; ++r)
+        if (!bases[r]) return WQ_ERR_ARG;
+    wq_ctx* ctx = bases[0]->ctx;
+    for (int r = 0; r < k; ++r)
+        if (bases[r]->ctx->device != ctx->device)
+            return fail(ctx, WQ_ERR_ARG, "batched rule build: the bases must share the device");
+    std::vector<BuildState> bs(k);
+    std::vector<wq_rule*> R(k, nullptr);
+    auto release = [&](wq_status s) {
+        for (wq_rule*& x : R) {
+            delete x;
+            x = nullptr;
+        }
+        return s;
+    };
+    for (int r = 0; r < k; ++r) {
+        wq_status s = rule_prepare(bases[r], opts, nullptr, &R[r], bs[r]);
+        if (s != WQ_OK) return release(s);
+    }
+    // one job per (rule, built component, row), the rows with the most Jacobi work first
+    std::vector<wqd::TsvdSet> sets;
+    std::vector<int2> jobs;
+    std::vector<double> cost;
+    int64_t per_cta = 1;
+    for (int r = 0; r < k; ++r) {
+        wq_rule* Q = R[r];
+        if (Q->n > INT32_MAX) return release(fail(ctx, WQ_ERR_ARG, "batched rule build: too many rows in one rule"));
+        per_cta = std::max(per_cta, bs[r].per_cta);
+        for (int c = 0; c < 5; ++c) {
+            if (Q->wcidx[c] < 0) continue;
+            const int64_t kk = Q->wcidx[c];
+            const int set = (int)sets.size();
+            sets.push_back({Q->el, Q->rw, Q->d_table, table_comp(Q, c), Q->d_mom[c], Q->d_W, Q->nwc, (int)kk,
+                            bs[r].d_rank + kk * Q->n, bs[r].d_zid + kk * Q->n, Q->d_status});
+            for (int64_t i = 0; i < Q->n; ++i) {
+                jobs.push_back(make_int2(set, (int)i));
+                cost.push_back(bs[r].row_cost[i]);
+            }
+        }
+    }
+    {
+        std::vector<int64_t> ord(jobs.size());
+        for (size_t j = 0; j < ord.size(); ++j) ord[j] = (int64_t)j;
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+        std::vector<int2> sorted(jobs.size());
+        for (size_t j = 0; j < ord.size(); ++j) sorted[j] = jobs[ord[j]];
+        jobs.swap(sorted);
+    }
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    const int n_sm = R[0]->n_sm;
+    const int n_cta = (int)std::min<int64_t>((int64_t)jobs.size(), (int64_t)n_sm * 8);
+    wqd::TsvdSet* d_sets = nullptr;
+    int2* d_jobs = nullptr;
+    unsigned long long* d_next = nullptr;
+    double *d_flops = nullptr, *d_scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto free_tmp = [&]() {
+        if (d_sets) cudaFree(d_sets);
+        if (d_jobs) cudaFree(d_jobs);
+        if (d_next) cudaFree(d_next);
+        if (d_flops) cudaFree(d_flops);
+        if (d_scratch) cudaFree(d_scratch);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&d_sets, std::max<size_t>(sets.size(), 1) * sizeof(wqd::TsvdSet)) != cudaSuccess ||
+        cudaMalloc(&d_jobs, std::max<size_t>(jobs.size(), 1) * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&d_next, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&d_flops, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&d_scratch, (size_t)per_cta * std::max(n_cta, 1) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        free_tmp();
+        return release(fail(ctx, WQ_ERR_OOM, "batched rule build: weight-solve buffers"));
+    }
+    double fl = 0.0;
+    float tms = 0.0f;
+    cudaError_t ce = cudaMemcpyAsync(d_sets, sets.data(), sets.size() * sizeof(wqd::TsvdSet), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess && !jobs.empty())
+        ce = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d_flops, 0, sizeof(double), st);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+    if (ce == cudaSuccess)
+        ce = wqd::launch_tsvd_batch(d_sets, d_jobs, (int64_t)jobs.size(), d_next, bs[0].tol, bs[0].sweeps, d_scratch,
+                                    per_cta, n_cta, d_flops, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&fl, d_flops, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tms, e0, e1);
+    free_tmp();
+    if (ce != cudaSuccess)
+        return release(fail(ctx, WQ_ERR_CUDA, std::string("batched weight solves: ") + cudaGetErrorString(ce)));
+    for (int r = 0; r < k; ++r) {
+        R[r]->info.tsvd_ms = tms;
+        R[r]->info.tsvd_gflop = fl * 1e-9;
+        ce = weight_stats(R[r], bs[r]);
+        if (ce != cudaSuccess)
+            return release(fail(ctx, WQ_ERR_CUDA, std::string("batched weight solves: ") + cudaGetErrorString(ce)));
+        wq_status s = rule_finish(R[r], bs[r]);
+        if (s != WQ_OK) return release(s);
+    }
+    for (int r = 0; r < k; ++r) out[r] = R[r];
+    return WQ_OK;
 }
 
 wq_status wq_rule_save(const wq_rule* rule, const char* path) {
@@ -1086,7 +1287,7 @@ wq_status wq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, doubl
     if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST && prec != WQ_PREC_TC)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     if (prec == WQ_PREC_TC && !rule->tc_ok)
-        return fail(rule->ctx, WQ_ERR_ARG, "WQ_PREC_TC needs at most 64 points per element");
+        return fail(rule->ctx, WQ_ERR_ARG, "WQ_PREC_TC: this rule has no tensor-core plan (an element with more than 64 points, or WQ_PLAN_NO_TC)");
     cudaEvent_t* evs = rule->next_timing_events();
     if (prec == WQ_PREC_F64)
         e = wqd::launch_elem_f64(rule->it_wq, rule->src64_wq, tm, 0, (const double*)d_coef, (double*)d_vals, st, evs);
@@ -1115,7 +1316,7 @@ wq_status wq_gq_assemble(const wq_rule* rule, int32_t op, const void* d_coef, do
     if (prec != WQ_PREC_F64 && prec != WQ_PREC_F32 && prec != WQ_PREC_F32_FAST && prec != WQ_PREC_TC)
         return fail(rule->ctx, WQ_ERR_ARG, "unknown precision");
     if (prec == WQ_PREC_TC && !rule->tc_ok)
-        return fail(rule->ctx, WQ_ERR_ARG, "WQ_PREC_TC needs at most 64 points per element");
+        return fail(rule->ctx, WQ_ERR_ARG, "WQ_PREC_TC: this rule has no tensor-core plan (an element with more than 64 points, or WQ_PLAN_NO_TC)");
     cudaEvent_t* evs = rule->next_timing_events();
     if (prec == WQ_PREC_F64)
         e = wqd::launch_elem_f64(rule->it_gq, rule->src64_gq, tm, 1, (const double*)d_coef, (double*)d_vals, st, evs);

@@ -50,6 +50,22 @@ struct Rows {
     const int32_t* order;     // [n] processing order of the rows (spatially sorted), or null
 };
 
+// One weight component of one rule for the batched truncated-SVD launch: the rule's
+// element and row plans, its point table (component tc gives A, component 0 gives Z),
+// moments [nnz], weights W (column wc of nwc), per-row rank / Z = I flags and status.
+struct TsvdSet {
+    Elems el;
+    Rows rw;
+    const double* table;
+    int tc;
+    const double* mom;
+    double* W;
+    int nwc, wc;
+    int32_t* rank;
+    uint8_t* zid;
+    unsigned* status;
+};
+
 // Element-major FP32 assembly.  Work items are 16 x 16 tiles of element blocks:
 // item[k] = {table offset, first point, m | P << 8 | (a0/16) << 16 | (b0/16) << 20,
 // first row of the element in the element-major weights}, kb[k] = start of the

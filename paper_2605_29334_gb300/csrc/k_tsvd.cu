@@ -25,21 +25,21 @@ __device__ __forceinline__ double warp_sum(double v) {
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
-__global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* __restrict__ table, int tc,
-                                              const double* __restrict__ mom, double* __restrict__ W, int nwc,
-                                              int wc, double tol, int max_sweeps, double* __restrict__ scratch,
-                                              int64_t per_cta, int32_t* __restrict__ rank_out,
-                                              uint8_t* __restrict__ zid_out, unsigned* status,
-                                              double* __restrict__ flops) {
+// One system (row i of one component), solved by the whole CTA in the scratch slice S.
+// Returns this thread's share of the FP64 operation count: 6 r per pair check,
+// 6 (r + n) + 20 per rotation in the Jacobi phase, ~2 r t^2 + 8 r t for the QR and
+// solves.  Every row's result depends on its own data only, so the weights do not
+// depend on which CTA solves which row or in what order.
+__device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, const double* __restrict__ table,
+                                              int tc, const double* __restrict__ mom, double* __restrict__ W,
+                                              int nwc, int wc, double tol, int max_sweeps, int64_t i,
+                                              double* __restrict__ S, int32_t* __restrict__ rank_out,
+                                              uint8_t* __restrict__ zid_out, unsigned* status, int* sh_t_ptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5, bd = blockDim.x;
-    __shared__ int sh_t;
-    __shared__ double sh_fl[4];
-    // FP64 operations of the Jacobi phase (6 r per pair check, 6 (r + n) + 20 per rotation)
-    // and of the QR and solves (~2 r t^2 + 8 r t), for the set-up roofline
+    int& sh_t = *sh_t_ptr;
     double fl = 0.0;
-    double* S = scratch + (int64_t)blockIdx.x * per_cta;
     const int nc = el.nc;
-    for (int64_t i = blockIdx.x; i < rw.n; i += gridDim.x) {
+    {
         const int n = rw.row_ptr[i + 1] - rw.row_ptr[i];
         const int r = (int)(rw.w_ptr[i + 1] - rw.w_ptr[i]);
         double* At = S;                      // [n][r]
@@ -269,6 +269,12 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
         }
         __syncthreads();
     }
+    return fl;
+}
+
+__device__ __forceinline__ void add_flops(double fl, double* flops) {
+    __shared__ double sh_fl[4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     if (flops) {
         for (int o = 16; o >= 1; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
         if (lane == 0) sh_fl[warp] = fl;
@@ -279,6 +285,61 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
             atomicAdd(flops, f);
         }
     }
+}
+
+__global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* __restrict__ table, int tc,
+                                              const double* __restrict__ mom, double* __restrict__ W, int nwc,
+                                              int wc, double tol, int max_sweeps, double* __restrict__ scratch,
+                                              int64_t per_cta, int32_t* __restrict__ rank_out,
+                                              uint8_t* __restrict__ zid_out, unsigned* status,
+                                              double* __restrict__ flops) {
+    __shared__ int sh_t;
+    double fl = 0.0;
+    double* S = scratch + (int64_t)blockIdx.x * per_cta;
+    for (int64_t i = blockIdx.x; i < rw.n; i += gridDim.x)
+        fl += tsvd_system(el, rw, table, tc, mom, W, nwc, wc, tol, max_sweeps, i, S, rank_out, zid_out, status, &sh_t);
+    add_flops(fl, flops);
+}
+
+// Every system of several rules and components in one persistent launch: CTAs take
+// jobs {system set, row} from a queue ordered by estimated cost (largest first), so
+// that the uneven systems near extraordinary points spread over the grid.
+__global__ void __launch_bounds__(128) k_tsvd_batch(const TsvdSet* __restrict__ sets, const int2* __restrict__ jobs,
+                                                    int64_t n_jobs, unsigned long long* __restrict__ next,
+                                                    double tol, int max_sweeps, double* __restrict__ scratch,
+                                                    int64_t per_cta, double* __restrict__ flops) {
+    __shared__ int sh_t, sh_row;
+    __shared__ long long sh_job;
+    __shared__ TsvdSet ts;   // the job's rule and component, read from shared memory by every loop
+    double fl = 0.0;
+    double* S = scratch + (int64_t)blockIdx.x * per_cta;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            sh_job = (long long)atomicAdd(next, 1ull);
+            if (sh_job < n_jobs) {
+                const int2 jb = jobs[sh_job];
+                sh_row = jb.y;
+                ts = sets[jb.x];
+            }
+        }
+        __syncthreads();
+        if (sh_job >= n_jobs) break;
+        // tsvd_system ends with a barrier, so thread 0 refills sh_job / ts only after
+        // every thread is done with them
+        fl += tsvd_system(ts.el, ts.rw, ts.table, ts.tc, ts.mom, ts.W, ts.nwc, ts.wc, tol, max_sweeps, sh_row, S,
+                          ts.rank, ts.zid, ts.status, &sh_t);
+    }
+    add_flops(fl, flops);
+}
+
+cudaError_t launch_tsvd_batch(const TsvdSet* sets, const int2* jobs, int64_t n_jobs, unsigned long long* next,
+                              double tol, int max_sweeps, double* scratch, int64_t per_cta, int n_cta, double* flops,
+                              cudaStream_t st) {
+    if (n_jobs == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_tsvd_batch<<<n_cta, 128, 0, st>>>(sets, jobs, n_jobs, next, tol, max_sweeps, scratch, per_cta, flops);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, int tc, const double* mom, double* W,

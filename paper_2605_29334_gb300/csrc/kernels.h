@@ -111,6 +111,13 @@ cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, in
                         double* scratch, int64_t per_cta, int n_cta, int32_t* rank, uint8_t* zid,
                         unsigned* status, double* flops, cudaStream_t st);
 
+// The same solves for many rules and components in one persistent launch (n_cta CTAs,
+// per_cta doubles of scratch each): jobs[j] = {index into sets, row}, taken in order
+// through the counter *next (zeroed on `st` before the launch).
+cudaError_t launch_tsvd_batch(const TsvdSet* sets, const int2* jobs, int64_t n_jobs, unsigned long long* next,
+                              double tol, int max_sweeps, double* scratch, int64_t per_cta, int n_cta, double* flops,
+                              cudaStream_t st);
+
 // u_h and grad u_h at WQ points (Sec. 5 interpolation).
 cudaError_t launch_interp(const Elems& el, const int32_t* pt_elem, const int32_t* fns,
                           const int64_t* fn_ptr, int64_t Q, const double* table, const double* u,

@@ -22,6 +22,7 @@ OP_MASS, OP_STIFF, OP_BIHARM, OP_HEAT_S, OP_HEAT_J = range(5)
 COMP_N, COMP_X, COMP_Y, COMP_Z, COMP_LAP = range(5)
 PREC_F64, PREC_F32, PREC_F32_FAST, PREC_TC, PREC_AUTO = 0, 1, 2, 3, 4
 VARIANT_TILE12, VARIANT_TILE16, VARIANT_SLOTMAP = 0, 1, 2
+PLAN_NO_TC, PLAN_NO_TILE = 1, 2
 TYPE_NAMES = ["passive", "boundary", "irregular", "enriched_transition", "transition", "enriched_regular", "regular"]
 
 
@@ -44,7 +45,7 @@ class BasisInfo(C.Structure):
 
 class RuleOpts(C.Structure):
     _fields_ = [("comps", C.c_uint32), ("count_mode", C.c_int32), ("tsvd_rel_tol", C.c_double),
-                ("max_sweeps", C.c_int32), ("stream", C.c_void_p)]
+                ("max_sweeps", C.c_int32), ("stream", C.c_void_p), ("skip_plans", C.c_uint32)]
 
 
 class RuleInfo(C.Structure):
@@ -72,6 +73,8 @@ EXPORTS = {
     "wq_basis_pattern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "wq_point_counts": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "wq_rule_build": (C.c_int, [C.c_void_p, C.POINTER(RuleOpts), C.POINTER(C.c_void_p)]),
+    "wq_rule_build_batched": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(RuleOpts),
+                                        C.POINTER(C.c_void_p)]),
     "wq_rule_destroy": (None, [C.c_void_p]),
     "wq_rule_info_get": (C.c_int, [C.c_void_p, C.POINTER(RuleInfo)]),
     "wq_rule_points": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
@@ -342,23 +345,44 @@ def refine_mesh(ctx, mesh, levels=1):
     return mesh
 
 
+def _rule_opts(comps, count_mode, tol, max_sweeps, stream, skip_plans):
+    mask = 0
+    for c in comps:
+        mask |= 1 << int(c)
+    return RuleOpts(mask, int(count_mode), float(tol), int(max_sweeps), _stream_handle(stream), int(skip_plans))
+
+
+def build_rules(bases, comps=(COMP_N, COMP_X, COMP_Y), tol=1e-12, max_sweeps=0, stream=None, count_mode=0,
+                skip_plans=0):
+    """wq_rule_build_batched: the rules of several bases (one device), with every
+    truncated-SVD system of all of them solved in one persistent launch."""
+    bases = list(bases)
+    k = len(bases)
+    hb = (C.c_void_p * k)(*[b.h.value if isinstance(b.h, C.c_void_p) else b.h for b in bases])
+    out = (C.c_void_p * k)()
+    opts = _rule_opts(comps, count_mode, tol, max_sweeps, stream, skip_plans)
+    bases[0].ctx.check(lib().wq_rule_build_batched(k, hb, C.byref(opts), out))
+    return [Rule(b, comps=comps, _handle=C.c_void_p(out[i])) for i, b in enumerate(bases)]
+
+
 class Rule:
     """wq_rule_build: placement, basis tables, Gauss moments and TSVD weights on the device."""
 
     def __init__(self, basis, comps=(COMP_N, COMP_X, COMP_Y), tol=1e-12, max_sweeps=0, stream=None, path=None,
-                 count_mode=0):
-        """Build the rule, or (path given) load weights and moments saved by save()."""
+                 count_mode=0, skip_plans=0, _handle=None):
+        """Build the rule, or (path given) load weights and moments saved by save().
+        skip_plans: PLAN_NO_TC | PLAN_NO_TILE leave those assembly plans out."""
         self.basis = basis
         self.ctx = basis.ctx
         h = C.c_void_p()
-        if path is not None:
+        if _handle is not None:                 # built by build_rules
+            h = _handle
+            self.h = h
+        elif path is not None:
             self.ctx.check(lib().wq_rule_load(basis.h, os.fsencode(path), C.byref(h)))
             self.h = h
         else:
-            mask = 0
-            for c in comps:
-                mask |= 1 << int(c)
-            opts = RuleOpts(mask, int(count_mode), float(tol), int(max_sweeps), _stream_handle(stream))
+            opts = _rule_opts(comps, count_mode, tol, max_sweeps, stream, skip_plans)
             self.ctx.check(lib().wq_rule_build(basis.h, C.byref(opts), C.byref(h)))
             self.h = h
         info = RuleInfo()

@@ -6,6 +6,8 @@
   bitwise equal to its own wq_assemble (same arithmetic, same summation order),
   the FP64 mode falls back to per-rule calls, the batched call replays from a
   CUDA graph, and one instance is anchored to the oracle.
+* wq_rule_build_batched: the same instances' weight systems in one launch, bitwise
+  equal to separate builds; rules built without the optional assembly plans.
 * wq_rule_save / wq_rule_load: a loaded rule reproduces weights, moments and
   assembled matrices bitwise; a file saved for another mesh, or cut short, is
   refused with WQ_ERR_ARG.
@@ -67,6 +69,50 @@ def test_batched_against_oracle(W, batch_case):
     # here the oracle anchors the batched instance to the method
     assert np.max(np.abs(f64 - ref)) / scale < 1e-8
     assert np.max(np.abs(got - f64)) / scale < 1e-6
+
+
+def test_batched_rule_build_equals_separate_builds(W, batch_case):
+    """wq_rule_build_batched: the weight systems of all eight instances and three
+    components, solved in one persistent launch in order of estimated work, give the
+    weights, moments, weight statistics and matrices of eight separate builds, bit for
+    bit (each system is solved by the same code, whatever CTA takes it)."""
+    import torch
+    rules, coefs = batch_case["rules"], batch_case["coefs"]
+    built = W.build_rules(batch_case["bases"], comps=[W.COMP_N, W.COMP_X, W.COMP_Y])
+    assert len(built) == len(rules)
+    for r, b, c in zip(rules, built, coefs):
+        for comp in (W.COMP_N, W.COMP_X, W.COMP_Y):
+            assert torch.equal(r.weights(comp)[0], b.weights(comp)[0]), comp
+            assert torch.equal(r.moments(comp), b.moments(comp)), comp
+        assert list(r.info.n_truncated) == list(b.info.n_truncated)
+        assert list(r.info.n_z_identity) == list(b.info.n_z_identity)
+        assert b.info.tsvd_ms > 0.0 and b.info.tsvd_gflop > 0.0
+        for op in (W.OP_MASS, W.OP_STIFF):
+            for prec in (W.PREC_F32, W.PREC_F64):
+                assert torch.equal(r.assemble(op, c, prec=prec), b.assemble(op, c, prec=prec)), (op, prec)
+    # one instance alone through the batched call
+    one = W.build_rules(batch_case["bases"][:1], comps=[W.COMP_N, W.COMP_X, W.COMP_Y])[0]
+    assert torch.equal(one.weights(W.COMP_X)[0], rules[0].weights(W.COMP_X)[0])
+
+
+def test_rule_without_tensor_core_and_tile_plans(W, batch_case):
+    """skip_plans: a rule without the tensor-core and tile-engine plans assembles the
+    same FP32 and FP64 matrices, refuses WQ_PREC_TC and the tile variants with
+    WQ_ERR_ARG, and the autotuner picks among the modes it has."""
+    import torch
+    b, r, c = batch_case["bases"][0], batch_case["rules"][0], batch_case["coefs"][0]
+    lean = W.Rule(b, comps=[W.COMP_N, W.COMP_X, W.COMP_Y], skip_plans=W.PLAN_NO_TC | W.PLAN_NO_TILE)
+    for op in (W.OP_MASS, W.OP_STIFF):
+        for prec in (W.PREC_F32, W.PREC_F64):
+            assert torch.equal(lean.assemble(op, c, prec=prec), r.assemble(op, c, prec=prec)), (op, prec)
+    with pytest.raises(W.WQError) as e:
+        lean.assemble(W.OP_STIFF, c, prec=W.PREC_TC)
+    assert e.value.code == 1
+    with pytest.raises(W.WQError):
+        lean.set_variant(W.OP_STIFF, W.VARIANT_TILE12)
+    res = lean.autotune(W.OP_STIFF, c, tol=1e-6, reps=3)
+    assert res["chosen"] in (W.PREC_F32, W.PREC_F32_FAST)
+    assert res["err"][0] < 0.0                          # no tensor-core candidate
 
 
 def test_batched_graph_replay(W, batch_case):

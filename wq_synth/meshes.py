@@ -343,6 +343,7 @@ def rotated(nx=8, ny=5, n_ep=12, valences=(3, 5, 6), levels=4, seed=2001, jitter
                 if i in (0, nx) or j in (0, ny)}
     fixed = {vid(i, j): np.array([float(i), float(j)]) for i in range(nx + 1) for j in range(ny + 1)
              if vid(i, j) in core_bnd}
+    base_val = _valences(base, nv)
     for _ in range(max_tries):
         quads = [list(q) for q in base]
         for _step in range(400):
@@ -362,7 +363,7 @@ def rotated(nx=8, ny=5, n_ep=12, valences=(3, 5, 6), levels=4, seed=2001, jitter
             val = _valences(trial, nv)
             bad = False
             for v in core_bnd:
-                if val[v] != _valences(base, nv)[v]:
+                if val[v] != base_val[v]:
                     bad = True
                     break
             if bad or any(val[v] < 3 or val[v] > max(valences) for v in range(nv) if v not in core_bnd):
@@ -505,37 +506,57 @@ def gaussian_bumps(seed, lo, hi, n=8, amp=0.5, width=0.1):
     return f
 
 
-def instances(seed, count, e_min=500, e_max=50000):
-    """Independent planar instances of uneven size for batched assembly.
-
-    Element counts are drawn log-uniform in [e_min, e_max].  Each instance is
-    either a rotated-core mesh (nx, ny in 3..10, an even number of EPs of valence
-    3/5/6 up to 20) or a disk around one EP of valence 3..8, refined until its
-    size is nearest to the drawn count.  Returns a list of mesh dicts.
-    """
+def instance_specs(seed, count, e_min=500, e_max=50000):
+    """The drawn parameters of ``instances`` (all random draws happen here, in order):
+    a list of ("rotated", nx, ny, n_ep, levels, sub) or ("disk", mu, n, levels, sub)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for k in range(count):
         target = float(np.exp(rng.uniform(np.log(e_min), np.log(e_max))))
         sub = int(rng.integers(1 << 30))
         if rng.uniform() < 0.6:
-            nx, ny = int(rng.integers(3, 11)), int(rng.integers(3, 11))
+            nx, ny = int(rng.integers(4, 11)), int(rng.integers(4, 11))
             interior = (nx - 1) * (ny - 1)
             n_ep = int(min(20, max(2, 2 * int(rng.integers(1, max(2, interior // 3) + 1)))))
             n_ep = min(n_ep, 2 * (interior // 3)) if interior >= 6 else 0
-            base = nx * ny
-            levels = int(np.clip(np.round(np.log(target / base) / np.log(4.0)), 0, 6))
-            mesh = None
-            while mesh is None and n_ep >= 2:
-                try:
-                    mesh = rotated(nx=nx, ny=ny, n_ep=n_ep, levels=levels, seed=sub, max_tries=300)
-                except RuntimeError:
-                    n_ep -= 2                       # fewer EPs when none can be drawn
-            out.append(mesh if mesh is not None else grid(nx, ny, seed=sub, jitter=0.02, levels=levels))
+            levels = int(np.clip(np.round(np.log(target / (nx * ny)) / np.log(4.0)), 0, 6))
+            out.append(("rotated", nx, ny, n_ep, levels, sub))
         else:
             mu = int(rng.integers(3, 9))
             n = int(rng.integers(3, 7))
-            base = mu * n * n
-            levels = int(np.clip(np.round(np.log(target / base) / np.log(4.0)), 0, 6))
-            out.append(disk(mu=mu, n=n, seed=sub, levels=levels))
+            levels = int(np.clip(np.round(np.log(target / (mu * n * n)) / np.log(4.0)), 0, 6))
+            out.append(("disk", mu, n, levels, sub))
     return out
+
+
+def make_instance(spec):
+    """The mesh of one entry of ``instance_specs`` (no random draws beyond its seed)."""
+    if spec[0] == "disk":
+        _, mu, n, levels, sub = spec
+        return disk(mu=mu, n=n, seed=sub, levels=levels)
+    _, nx, ny, n_ep, levels, sub = spec
+    mesh = None
+    while mesh is None and n_ep >= 2:
+        try:
+            mesh = rotated(nx=nx, ny=ny, n_ep=n_ep, levels=levels, seed=sub, max_tries=40)
+        except RuntimeError:
+            n_ep -= 2                       # fewer EPs when none can be drawn
+    return mesh if mesh is not None else grid(nx, ny, seed=sub, jitter=0.02, levels=levels)
+
+
+def instances(seed, count, e_min=500, e_max=50000, workers=1):
+    """Independent planar instances of uneven size for batched assembly.
+
+    Element counts are drawn log-uniform in [e_min, e_max].  Each instance is
+    either a rotated-core mesh (nx, ny in 4..10, an even number of EPs of valence
+    3/5/6 up to 20) or a disk around one EP of valence 3..8, refined until its
+    size is nearest to the drawn count.  Returns a list of mesh dicts.  workers > 1
+    builds the meshes in that many spawned processes (the same meshes).
+    """
+    specs = instance_specs(seed, count, e_min, e_max)
+    if workers <= 1:
+        return [make_instance(sp) for sp in specs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(make_instance, specs))
