@@ -281,6 +281,10 @@ def bench_ours(args, rank, world):
                    "n_points": rule.Q, "n_gauss": rule.G, "op": "stiffness", "l2": "flushed (256 MB write) before "
                    "every timed step; timed = the assembly call only", "parallelism": "independent instance per GPU"},
         "rel_err_vs_f64": rel,
+        "precision_note": "value: the mixed mode wq_rule_autotune picks within 1e-6 of the same rule's GPU FP64 "
+                          "result (rel_err_vs_f64); the GPU FP64 path is pinned to the FP64 oracle by "
+                          "tests/test_gpu_fullsize.py at max(1e-11, 4x the oracle's LAPACK-driver spread); the "
+                          "like-for-like FP64 WQ and GQ figures are comparators.wq_f64_* / gq_f64_*",
         "autotune_ms": dict(zip(("tc", "f32", "f32_fast"), tune["ms"])),
         "autotune_candidates": tune["candidates"], "kernel_variant": variant,
         "gpu_launches": args.steps * 2,
@@ -304,7 +308,8 @@ def bench_ours(args, rank, world):
                 "d2h_bytes_per_step": int(nnz * (8 if prec == wq.PREC_F64 else 4))},
         "clocks": clocks,
     }
-    res["refine"] = refine_measure(wq, basis, mesh, flush, max(args.steps // 20, 20), args.warmup, hbm)
+    res["refine"] = refine_measure(wq, basis, mesh, flush, max(args.steps // 20, 20), args.warmup, hbm,
+                                   n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12)
     if not args.no_cpu_baseline:
         a64 = rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F64).cpu().numpy()
         g64 = rule.gq_assemble(wq.OP_STIFF, coef_g, prec=wq.PREC_F64).cpu().numpy()
@@ -529,12 +534,14 @@ def _kernel_source_sha1(kname):
     return hashlib.sha1(s.encode()).hexdigest()
 
 
-def refine_measure(wq, basis, mesh, flush, steps, warmup, hbm):
+def refine_measure(wq, basis, mesh, flush, steps, warmup, hbm, fp64_tflops):
     """One global refinement of the workload's control mesh (Sec. 3) on the device:
     knot-insertion stencils for the vertex-based control points, de Casteljau splits of
     the enriched faces' nets for the face-based ones.  Algorithmic bytes: every coarse
-    control point, stencil entry (4 B index + 8 B weight, 8 B row pointer), job, function
-    id and Bezier coefficient read once, every fine control point written once."""
+    control point, stencil entry (4 B index + 8 B weight, 8 B row pointer), face job and
+    non-zero term of a fine face-based point (the de Casteljau split folded into the
+    Bezier coefficients; 4 B function id + 8 B value) read once, every fine control point
+    written once.  FP64 work: 3 FMAs per stencil entry and per term."""
     import torch
     r = wq.Refine(basis)
     I = r.info
@@ -552,11 +559,15 @@ def refine_measure(wq, basis, mesh, flush, steps, warmup, hbm):
     ms = time_steps(graph.replay, steps, warmup, flush)
     t = float(np.mean(ms)) / 1e3
     byts = (24 * (I.n_coarse_vertices + I.n_coarse_face_xyz + I.n_vertices + I.n_face_xyz)
-            + 12 * I.n_stencil + 8 * (I.n_vertices + 1) + 24 * I.n_face_jobs + 4 * I.n_face_fns + 8 * I.n_face_coef)
+            + 12 * I.n_stencil + 8 * (I.n_vertices + 1) + 24 * I.n_face_jobs + 12 * I.n_face_terms)
+    flops = 6 * (I.n_stencil + I.n_face_terms)
     return {"ms": t * 1e3, "coarse_vertices": I.n_coarse_vertices, "fine_vertices": I.n_vertices,
             "fine_faces": I.n_faces, "fine_face_points": I.n_face_xyz, "face_jobs": I.n_face_jobs,
+            "face_coefficients_dense": I.n_face_coef, "face_terms_nonzero": I.n_face_terms,
             "algorithmic_bytes": byts, "achieved_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm,
-            "launches": 2, "timing": "CUDA-graph replay, L2 flushed before each"}
+            "fp64_gflop": flops / 1e9, "fp64_frac": flops / t / 1e12 / fp64_tflops,
+            "fp64_peak_source": "derived (not measured): SMs x 2 FP64 FMA/cycle x 2 x max SM clock",
+            "launches": 1, "timing": "CUDA-graph replay, L2 flushed before each"}
 
 
 def assembly_work(rule, basis, n_terms, n_coef_rows=1, value_bytes=4):

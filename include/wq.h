@@ -460,6 +460,9 @@ typedef struct {
     int64_t n_face_jobs;         /* coarse enriched faces (one de Casteljau split each) */
     int64_t n_face_fns;          /* functions over all of them (control points each job reads) */
     int64_t n_face_coef;         /* their Bezier coefficients (16 or 64 per function) */
+    int64_t n_face_terms;        /* non-zero (function, fine point) terms: the de Casteljau split
+                                    folded into the coefficients, 16 fine points per face */
+    int64_t n_face_ell;          /* their padded device copy (16 points x an even count per face) */
 } wq_refine_info;
 
 /* Plan one global refinement of the basis's control mesh (Sec. 3: the enriched
@@ -510,8 +513,9 @@ wq_status wq_refine_mesh(const wq_refine* r, int32_t* h_quads, int32_t* h_level0
  * skipped.  Errors: WQ_ERR_ARG (null plan). */
 wq_status wq_refine_stencils(const wq_refine* r, int64_t* h_ptr, int32_t* h_src, double* h_w);
 
-/* Apply the refinement on the device (two kernels on stream, no allocation, no
- * synchronisation): d_xyz [n_coarse_vertices][3] and d_face_xyz
+/* Apply the refinement on the device (one kernel on stream, no allocation, no
+ * synchronisation; each fine face-based point is a short sum over the non-zero
+ * terms listed at plan creation): d_xyz [n_coarse_vertices][3] and d_face_xyz
  * [n_coarse_face_xyz][3] are the coarse control points (the basis's own, or any
  * other values: the map is linear), d_xyz_fine [n_vertices][3] and
  * d_face_xyz_fine [n_face_xyz][3] receive the fine ones, ready for

@@ -4,33 +4,46 @@
 // The plan (fine topology, stencils, element coefficients) is built on the host
 // (refine_host.cpp); this file holds the kernels and the wq_refine_* C ABI.
 //
-// k_refine_vertices: one thread per fine vertex, x_w = sum_k w_k x_{src_k} over
-//   its stencil (at most 9 coarse vertices, padded to 9 and stored slot-major so
-//   that all of a thread's loads are in flight together; gathers of 24-byte points).
-// k_refine_faces: one block of 64 threads per coarse enriched face.  The block
-//   gathers the coarse control points of the element's functions into shared
-//   memory (64 at a time, all loads in flight together); thread p then contracts
-//   Bezier coefficient p of every function with them into net point p (16 points,
-//   or 4 x 16 for a 2 x 2-split irregular element); a plain face's net is split at 1/2 along
-//   u and v by de Casteljau's algorithm in shared memory (4 x 4 -> 7 x 7), and
-//   16 threads write the inner points of the four children (for a split element
-//   the sub-nets are the children's nets).
+// k_refine: one launch, one warp per work item.  The de Casteljau split is linear, so
+//   at set-up it is folded into the element's Bezier coefficients: every inner point of
+//   the four children of a coarse enriched face is a fixed combination of the coarse
+//   control points, of which only the non-zero terms are kept (about a seventh of the
+//   dense m x 16 coefficients on the benchmark mesh).  A face is then 16 short dot
+//   products, a group of 32 fine vertices 32 knot-insertion stencils (at most 9 coarse
+//   vertices each).
+#include <algorithm>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "rule.h"
 #include "wq_internal.h"
 
+// A coarse enriched face on the device: the 16 inner points of its children as a padded
+// (ELL) list of non-zero terms, K per point, stored term-major ([k][16]) at ell_off,
+// each a coefficient and the raw control-variable id of its function.
+struct FaceJobDev {
+    int64_t ell_off;
+    int32_t K;       // terms per point (even: the two half-warps take alternate terms)
+    int32_t nsub;    // 1 or 4 (2 x 2-split irregular element)
+    int32_t out;     // first fine face-based point written (16 per job)
+    int32_t pad;
+};
+
 struct wq_refine {
     wq_ctx* ctx = nullptr;
     int device = -1;
     wqi::RefinePlan plan;
+    int64_t n_terms = 0;                   // non-zero coefficients over all face jobs
+    int64_t n_ell = 0;                     // their padded (ELL) entries
     std::vector<wqi::DevBuf> bufs;
-    int32_t* d_st_src = nullptr;           // stencils padded to RF_SLOTS, slot-major [RF_SLOTS][Vf]
+    int32_t* d_st_src = nullptr;           // stencils per group of 32 fine vertices, [group][RF_SLOTS][32]
     double* d_st_w = nullptr;
-    wqi::RefineJob* d_jobs = nullptr;
-    int32_t* d_fn_raw = nullptr;
-    double* d_coef = nullptr;
+    uint8_t* d_st_K = nullptr;             // the group's longest stencil
+    FaceJobDev* d_jobs = nullptr;
+    int32_t* d_ell_id = nullptr;           // raw control-variable id of every (padded) term
+    double* d_ell_c = nullptr;             // its coefficient (0 for padding)
+    int n_sm = 1;
     ~wq_refine() {
         for (auto& b : bufs)
             if (b.p) cudaFree(b.p);
@@ -41,120 +54,95 @@ namespace {
 
 constexpr int RF_SLOTS = 9;   // longest stencil: the 3 x 3 vertex rule
 
-// Stencils padded to RF_SLOTS entries (weight 0, source 0), slot-major: entry k of
-// vertex v at k * nv + v, so that a warp reads each slot contiguously and every
-// load of a thread is issued before the first one is used.
-__global__ void __launch_bounds__(256) k_refine_vertices(int64_t nv, const int32_t* __restrict__ src,
-                                                         const double* __restrict__ w,
-                                                         const double* __restrict__ xyz, double* __restrict__ out) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    int32_t s[RF_SLOTS];
-    double c[RF_SLOTS];
-#pragma unroll
-    for (int k = 0; k < RF_SLOTS; ++k) {
-        s[k] = src[k * nv + v];
-        c[k] = w[k * nv + v];
-    }
-    double x = 0.0, y = 0.0, z = 0.0;
-#pragma unroll
-    for (int k = 0; k < RF_SLOTS; ++k) {
-        const double* p = xyz + 3 * (int64_t)s[k];
-        x = fma(c[k], p[0], x);
-        y = fma(c[k], p[1], y);
-        z = fma(c[k], p[2], z);
-    }
-    out[3 * v] = x;
-    out[3 * v + 1] = y;
-    out[3 * v + 2] = z;
-}
+constexpr int RF_WARPS = 8;   // warps per block of the refinement kernel
 
-__device__ __forceinline__ void split_half(const double* b, int stride_in, double* o, int stride_out) {
-    // de Casteljau at 1/2: 4 control points -> the 7 of the two halves
-    const double b0 = b[0], b1 = b[stride_in], b2 = b[2 * stride_in], b3 = b[3 * stride_in];
-    const double b01 = 0.5 * (b0 + b1), b12 = 0.5 * (b1 + b2), b23 = 0.5 * (b2 + b3);
-    const double b012 = 0.5 * (b01 + b12), b123 = 0.5 * (b12 + b23);
-    o[0] = b0;
-    o[stride_out] = b01;
-    o[2 * stride_out] = b012;
-    o[3 * stride_out] = 0.5 * (b012 + b123);
-    o[4 * stride_out] = b123;
-    o[5 * stride_out] = b23;
-    o[6 * stride_out] = b3;
-}
+// de Casteljau at 1/2 of a cubic: control point x of the two halves (x = 0..6) as a
+// combination of the four of the whole (rows 1/2^k binomial weights, exact in FP64).
+constexpr double kHalfSplit[7][4] = {{1.0, 0.0, 0.0, 0.0},       {0.5, 0.5, 0.0, 0.0},
+                                     {0.25, 0.5, 0.25, 0.0},     {0.125, 0.375, 0.375, 0.125},
+                                     {0.0, 0.25, 0.5, 0.25},     {0.0, 0.0, 0.5, 0.5},
+                                     {0.0, 0.0, 0.0, 1.0}};
 
-__global__ void __launch_bounds__(64) k_refine_faces(int64_t n_jobs, const wqi::RefineJob* __restrict__ jobs,
-                                                     const int32_t* __restrict__ fn_raw,
-                                                     const double* __restrict__ coef, int64_t Vc,
-                                                     const double* __restrict__ xyz,
-                                                     const double* __restrict__ fxyz, double* __restrict__ out) {
-    __shared__ double sP[3][64];         // control points of the functions being contracted
-    __shared__ double net[3][64];        // [coord][sub*16 + i*4 + j]
-    __shared__ double half[3][7 * 4];    // u-split rows: [coord][x*4 + j]
-    __shared__ double full[3][7 * 7];    // [coord][x*7 + y]
-    const int64_t b = blockIdx.x;
-    if (b >= n_jobs) return;
-    const wqi::RefineJob jb = jobs[b];
-    const int t = threadIdx.x;
-    const int np = 16 * jb.nsub;
-    double x = 0.0, y = 0.0, z = 0.0;
-    const double* c = coef + jb.coef_off + t;
-    for (int a0 = 0; a0 < jb.m; a0 += 64) {
-        // the control points of up to 64 functions, gathered by all threads at once
-        const int na = min(64, jb.m - a0);
-        if (t < na) {
-            const int64_t r = fn_raw[jb.fn_off + a0 + t];
-            const double* p = r < Vc ? xyz + 3 * r : fxyz + 3 * (r - Vc);
-            sP[0][t] = p[0];
-            sP[1][t] = p[1];
-            sP[2][t] = p[2];
-        }
-        __syncthreads();
-        if (t < np) {
-#pragma unroll 8
-            for (int a = 0; a < na; ++a) {
-                const double w = c[(int64_t)(a0 + a) * np];
-                x = fma(w, sP[0][a], x);
-                y = fma(w, sP[1][a], y);
-                z = fma(w, sP[2][a], z);
+// Both parts of one refinement in one launch, one warp per work item, taken in a
+// grid-stride loop: first the coarse enriched faces, then the fine vertices in groups
+// of 32.  No shared memory and no barrier: every item is a padded (ELL) list of
+// (control point, coefficient) terms per output point.
+//   Face: slot t = lane & 15 is inner point t of the four children (child t / 4 at
+//   coarse corner t / 4, its corner t % 4); its terms are the non-zero coefficients of
+//   the element's functions in that point -- for a plain face the de Casteljau split at
+//   1/2 folded into the Bezier coefficients at set-up, for a 2 x 2-split irregular
+//   element the coefficients of the sub-net point itself.  The two half-warps take
+//   alternate terms, then add.
+//   Vertex group: lane l is fine vertex 32 g + l; its knot-insertion stencil, padded to
+//   the group's longest (K_g <= RF_SLOTS) and stored [g][k][32], so that the loads of a
+//   lane are in flight together.
+__global__ void __launch_bounds__(RF_WARPS * 32) k_refine(int64_t n_jobs, const FaceJobDev* __restrict__ jobs,
+                                                          const int32_t* __restrict__ ell_id,
+                                                          const double* __restrict__ ell_c, int64_t Vc,
+                                                          const double* __restrict__ xyz,
+                                                          const double* __restrict__ fxyz,
+                                                          double* __restrict__ out_f, int64_t nv,
+                                                          const uint8_t* __restrict__ vK,
+                                                          const int32_t* __restrict__ src,
+                                                          const double* __restrict__ w,
+                                                          double* __restrict__ out_v) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t n_vchunks = (nv + 31) / 32;
+    const int64_t total = n_jobs + n_vchunks;
+    const int64_t stride = (int64_t)gridDim.x * RF_WARPS;
+    for (int64_t item = (int64_t)blockIdx.x * RF_WARPS + wib; item < total; item += stride) {
+        if (item >= n_jobs) {
+            const int64_t g = item - n_jobs, v = g * 32 + lane;
+            const int K = vK[g];
+            const int32_t* sg = src + g * (RF_SLOTS * 32) + lane;
+            const double* wg = w + g * (RF_SLOTS * 32) + lane;
+            int32_t sidx[RF_SLOTS];
+            double c[RF_SLOTS];
+#pragma unroll
+            for (int k = 0; k < RF_SLOTS; ++k)
+                if (k < K) {
+                    sidx[k] = sg[k * 32];
+                    c[k] = wg[k * 32];
+                }
+            double x = 0.0, y = 0.0, z = 0.0;
+#pragma unroll
+            for (int k = 0; k < RF_SLOTS; ++k)
+                if (k < K) {
+                    const double* p = xyz + 3 * (int64_t)sidx[k];
+                    x = fma(c[k], p[0], x);
+                    y = fma(c[k], p[1], y);
+                    z = fma(c[k], p[2], z);
+                }
+            if (v < nv) {
+                out_v[3 * v] = x;
+                out_v[3 * v + 1] = y;
+                out_v[3 * v + 2] = z;
             }
+            continue;
         }
-        __syncthreads();
-    }
-    if (t < np) {
-        net[0][t] = x;
-        net[1][t] = y;
-        net[2][t] = z;
-    }
-    __syncthreads();
-    const int k = t >> 2, c2 = t & 3;                       // child (coarse corner), its corner
-    const int cu = (k == 1 || k == 2), cv = (k >= 2);
-    const int du = (c2 == 1 || c2 == 2), dv = (c2 >= 2);
-    if (jb.nsub == 1) {
-        if (t < 12) {                                       // 4 rows j x 3 coordinates, along u
-            const int j = t / 3, d = t % 3;
-            split_half(&net[d][j], 4, &half[d][j], 4);
+        const FaceJobDev jb = jobs[item];
+        const int t = lane & 15, half = lane >> 4;
+        const int32_t* ids = ell_id + jb.ell_off;
+        const double* cs = ell_c + jb.ell_off;
+        double x = 0.0, y = 0.0, z = 0.0;
+#pragma unroll 4
+        for (int k = half; k < jb.K; k += 2) {
+            const int64_t r = ids[k * 16 + t];
+            const double c = cs[k * 16 + t];
+            const double* q = r < Vc ? xyz + 3 * r : fxyz + 3 * (r - Vc);
+            x = fma(c, q[0], x);
+            y = fma(c, q[1], y);
+            z = fma(c, q[2], z);
         }
-        __syncthreads();
-        if (t < 21) {                                       // 7 columns x 3 coordinates, along v
-            const int x = t / 3, d = t % 3;
-            split_half(&half[d][x * 4], 1, &full[d][x * 7], 1);
+        x += __shfl_down_sync(0xffffffffu, x, 16);
+        y += __shfl_down_sync(0xffffffffu, y, 16);
+        z += __shfl_down_sync(0xffffffffu, z, 16);
+        if (lane < 16) {
+            double* o = out_f + 3 * ((int64_t)jb.out + t);
+            o[0] = x;
+            o[1] = y;
+            o[2] = z;
         }
-        __syncthreads();
-        if (t < 16) {
-            const int x = 3 * cu + 1 + du, y = 3 * cv + 1 + dv;
-            double* o = out + 3 * ((int64_t)jb.out + t);
-            o[0] = full[0][x * 7 + y];
-            o[1] = full[1][x * 7 + y];
-            o[2] = full[2][x * 7 + y];
-        }
-    } else if (t < 16) {
-        const int s = cu + 2 * cv;                          // the child is sub-element s
-        const int p = s * 16 + (1 + du) * 4 + (1 + dv);
-        double* o = out + 3 * ((int64_t)jb.out + t);
-        o[0] = net[0][p];
-        o[1] = net[1][p];
-        o[2] = net[2][p];
     }
 }
 
@@ -204,31 +192,92 @@ wq_status wq_refine_create(const wq_basis* basis, wq_refine** out) {
         delete R;
         return rfail(basis->ctx, err.code, err.msg);
     }
+    // face jobs: for each of the 16 children's inner points the non-zero coefficients of
+    // the element's functions in it (zero terms would add exactly nothing), in function
+    // order, padded to an even count K per job with zero terms on the job's first function
+    std::vector<FaceJobDev> fj;
+    std::vector<int32_t> ell_id;
+    std::vector<double> ell_c;
+    try {
+        fj.resize(R->plan.jobs.size());
+        std::vector<std::vector<std::pair<int32_t, double>>> terms(16);
+        for (size_t x = 0; x < R->plan.jobs.size(); ++x) {
+            const wqi::RefineJob& J = R->plan.jobs[x];
+            const int np = 16 * J.nsub;
+            int K = 0;
+            for (int t = 0; t < 16; ++t) {
+                    const int k = t >> 2, c2 = t & 3;            // child (coarse corner), its corner
+                const int cu = (k == 1 || k == 2), cv = (k >= 2), du = (c2 == 1 || c2 == 2), dv = (c2 >= 2);
+                terms[t].clear();
+                for (int a = 0; a < J.m; ++a) {
+                    const double* ca = R->plan.coef.data() + J.coef_off + (int64_t)a * np;
+                    double c = 0.0;
+                    if (J.nsub != 1) {
+                        c = ca[(cu + 2 * cv) * 16 + (1 + du) * 4 + (1 + dv)];   // the sub-net's point
+                    } else {
+                        // de Casteljau at 1/2 folded in: row xx of the u-split, column yy of
+                        // the v-split of the 4 x 4 net
+                        const int xx = 3 * cu + 1 + du, yy = 3 * cv + 1 + dv;
+                        for (int i = 0; i < 4; ++i)
+                            for (int j = 0; j < 4; ++j) c += kHalfSplit[xx][i] * kHalfSplit[yy][j] * ca[i * 4 + j];
+                    }
+                    if (c != 0.0) terms[t].push_back({R->plan.fn_raw[(size_t)J.fn_off + a], c});
+                }
+                K = std::max(K, (int)terms[t].size());
+                R->n_terms += (int64_t)terms[t].size();
+            }
+            K = (K + 1) & ~1;
+            fj[x] = {(int64_t)ell_id.size(), K, J.nsub, J.out, 0};
+            const int32_t pad_id = J.m > 0 ? R->plan.fn_raw[(size_t)J.fn_off] : 0;
+            for (int k = 0; k < K; ++k)
+                for (int t = 0; t < 16; ++t) {
+                    const bool real = k < (int)terms[t].size();
+                    ell_id.push_back(real ? terms[t][k].first : pad_id);
+                    ell_c.push_back(real ? terms[t][k].second : 0.0);
+                }
+        }
+    } catch (const std::bad_alloc&) {
+        delete R;
+        return rfail(basis->ctx, WQ_ERR_OOM, "host allocation failed");
+    }
+    R->n_ell = (int64_t)ell_id.size();
     if (R->device >= 0) {
         if (cudaSetDevice(R->device) != cudaSuccess) {
             cudaGetLastError();
             delete R;
             return rfail(basis->ctx, WQ_ERR_CUDA, "cudaSetDevice failed");
         }
+        int n_sm = 0;
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, R->device) == cudaSuccess && n_sm > 0)
+            R->n_sm = n_sm;
+        cudaGetLastError();
         const wqi::RefinePlan& P = R->plan;
-        std::vector<int32_t> ell_src((size_t)RF_SLOTS * P.Vf, 0);
-        std::vector<double> ell_w((size_t)RF_SLOTS * P.Vf, 0.0);
+        // stencils per group of 32 fine vertices, padded to the group's longest (weight 0,
+        // source 0), [group][RF_SLOTS][32]
+        const int64_t ng = (P.Vf + 31) / 32;
+        std::vector<int32_t> ell_src((size_t)ng * RF_SLOTS * 32, 0);
+        std::vector<double> ell_w((size_t)ng * RF_SLOTS * 32, 0.0);
+        std::vector<uint8_t> gK((size_t)std::max<int64_t>(ng, 1), 0);
         for (int64_t v = 0; v < P.Vf; ++v) {
-            if (P.st_ptr[v + 1] - P.st_ptr[v] > RF_SLOTS) {
+            const int64_t len = P.st_ptr[v + 1] - P.st_ptr[v];
+            if (len > RF_SLOTS) {
                 delete R;
                 return rfail(basis->ctx, WQ_ERR_MESH, "refinement stencil longer than 9 entries");
             }
-            for (int64_t k = P.st_ptr[v]; k < P.st_ptr[v + 1]; ++k) {
-                ell_src[(size_t)(k - P.st_ptr[v]) * P.Vf + v] = P.st_src[k];
-                ell_w[(size_t)(k - P.st_ptr[v]) * P.Vf + v] = P.st_w[k];
+            const int64_t g = v / 32, l = v % 32;
+            gK[g] = (uint8_t)std::max<int64_t>(gK[g], len);
+            for (int64_t k = 0; k < len; ++k) {
+                ell_src[(size_t)((g * RF_SLOTS + k) * 32 + l)] = P.st_src[P.st_ptr[v] + k];
+                ell_w[(size_t)((g * RF_SLOTS + k) * 32 + l)] = P.st_w[P.st_ptr[v] + k];
             }
         }
         wq_status s = WQ_OK;
         if (s == WQ_OK) s = rupload(R, R->d_st_src, ell_src);
         if (s == WQ_OK) s = rupload(R, R->d_st_w, ell_w);
-        if (s == WQ_OK) s = rupload(R, R->d_jobs, P.jobs);
-        if (s == WQ_OK) s = rupload(R, R->d_fn_raw, P.fn_raw);
-        if (s == WQ_OK) s = rupload(R, R->d_coef, P.coef);
+        if (s == WQ_OK) s = rupload(R, R->d_st_K, gK);
+        if (s == WQ_OK) s = rupload(R, R->d_jobs, fj);
+        if (s == WQ_OK) s = rupload(R, R->d_ell_id, ell_id);
+        if (s == WQ_OK) s = rupload(R, R->d_ell_c, ell_c);
         if (s != WQ_OK) {
             delete R;
             return s;
@@ -256,6 +305,8 @@ wq_status wq_refine_info_get(const wq_refine* r, wq_refine_info* info) {
     info->n_face_jobs = (int64_t)P.jobs.size();
     info->n_face_fns = (int64_t)P.fn_raw.size();
     info->n_face_coef = (int64_t)P.coef.size();
+    info->n_face_terms = r->n_terms;
+    info->n_face_ell = r->n_ell;
     return WQ_OK;
 }
 
@@ -287,14 +338,15 @@ wq_status wq_refine_apply(const wq_refine* r, const double* d_xyz, const double*
     if (e == cudaSuccess && cur != r->device) e = cudaSetDevice(r->device);   // no call when already current
     if (e != cudaSuccess) return rfail(r->ctx, WQ_ERR_CUDA, std::string("device selection: ") + cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
-    if (P.Vf > 0) {
-        const unsigned g = (unsigned)((P.Vf + 255) / 256);
-        k_refine_vertices<<<g, 256, 0, st>>>(P.Vf, r->d_st_src, r->d_st_w, d_xyz, d_xyz_fine);
-    }
     const int64_t nj = (int64_t)P.jobs.size();
-    if (nj > 0)
-        k_refine_faces<<<(unsigned)nj, 64, 0, st>>>(nj, r->d_jobs, r->d_fn_raw, r->d_coef, P.Vc, d_xyz, d_face_xyz,
-                                                    d_face_xyz_fine);
+    const int64_t items = nj + (P.Vf + 31) / 32;
+    if (items > 0) {
+        // one warp per item, up to eight resident blocks of eight warps per SM
+        const int64_t blocks = std::min<int64_t>((items + RF_WARPS - 1) / RF_WARPS, (int64_t)r->n_sm * 8);
+        k_refine<<<(unsigned)blocks, RF_WARPS * 32, 0, st>>>(nj, r->d_jobs, r->d_ell_id, r->d_ell_c, P.Vc, d_xyz,
+                                                             d_face_xyz, d_face_xyz_fine, P.Vf, r->d_st_K,
+                                                             r->d_st_src, r->d_st_w, d_xyz_fine);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return rfail(r->ctx, WQ_ERR_CUDA, std::string("refine launch: ") + cudaGetErrorString(e));
     return WQ_OK;

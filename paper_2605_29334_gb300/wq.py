@@ -57,7 +57,8 @@ class RuleInfo(C.Structure):
 class RefineInfo(C.Structure):
     _fields_ = [("n_vertices", C.c_int64), ("n_faces", C.c_int64), ("n_face_xyz", C.c_int64),
                 ("n_coarse_vertices", C.c_int64), ("n_coarse_face_xyz", C.c_int64), ("n_stencil", C.c_int64),
-                ("n_face_jobs", C.c_int64), ("n_face_fns", C.c_int64), ("n_face_coef", C.c_int64)]
+                ("n_face_jobs", C.c_int64), ("n_face_fns", C.c_int64), ("n_face_coef", C.c_int64),
+                ("n_face_terms", C.c_int64), ("n_face_ell", C.c_int64)]
 
 
 EXPORTS = {
