@@ -710,7 +710,7 @@ static wq_status rule_prepare(wq_basis* basis, const wq_rule_opts* opts, const S
         return bail(sst);
     // weight-solve scratch per CTA (allocated by the solve, freed after it)
     const int64_t mn = R->max_n_i, mr = R->max_r;
-    bs.per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
+    bs.per_cta = wqd::tsvd_scratch_doubles(mn, mr);
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
     R->n_sm = std::max(n_sm, 1);
@@ -854,7 +854,7 @@ static cudaError_t weight_stats(wq_rule* R, BuildState& bs) {
 // component (timed, FP64 operations counted); the scratch lives for the solves only.
 static wq_status rule_weights_single(wq_rule* R, BuildState& bs) {
     wq_ctx* ctx = R->ctx;
-    const int n_cta = (int)std::min<int64_t>(R->n, (int64_t)R->n_sm * 8);
+    const int n_cta = (int)std::min<int64_t>(R->n, (int64_t)R->n_sm * wqd::TSVD_CTAS_PER_SM);
     double* d_scratch = nullptr;
     if (n_cta > 0 && cudaMalloc(&d_scratch, (size_t)bs.per_cta * n_cta * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -1057,7 +1057,7 @@ wq_status wq_rule_build_batched(int32_t k, wq_basis* const* bases, const wq_rule
     }
     cudaStream_t st = (cudaStream_t)opts->stream;
     const int n_sm = R[0]->n_sm;
-    const int n_cta = (int)std::min<int64_t>((int64_t)jobs.size(), (int64_t)n_sm * 8);
+    const int n_cta = (int)std::min<int64_t>((int64_t)jobs.size(), (int64_t)n_sm * wqd::TSVD_CTAS_PER_SM);
     wqd::TsvdSet* d_sets = nullptr;
     int2* d_jobs = nullptr;
     unsigned long long* d_next = nullptr;

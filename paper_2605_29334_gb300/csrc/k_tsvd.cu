@@ -5,14 +5,17 @@
 //
 // One CTA per system (persistent grid over rows), FP64, matrices in a per-CTA
 // global scratch slice:
-//  1. gather A^T row-major by function (At[a][q]) and z from the point tables;
-//  2. one-sided (Hestenes) Jacobi on the n_i vectors At[a] (length r_i), round-
-//     robin pairs, four lanes per pair, accumulating the rotations in Jt (so that
-//     A^T J = [s_k v_k], U = J);  a sweep cap ends it with a status flag;
-//  3. s_k = |At[k]|, keep s_k >= tol s_max;  g = S_t^{-1} U_t^T b;
-//  4. G = Z V_t (columns z * At[k] / s_k), Householder QR G = Q R, then
-//     w = Z Q R^{-T} g  -- the inverse of G^T G = V_t^T Z^2 V_t applied through
+//  1. gather A row-major by function (At[a][q]) and z from the point tables;
+//  2. Householder QR with column pivoting of A^T (r_i x n_i): A^T P = Q R;
+//  3. one-sided (Hestenes) Jacobi on the n_i rows of R (length n_i), round-robin
+//     pairs, four lanes per pair, accumulating the rotations in Jt (J^T R = S Y^T,
+//     so A = (P Y) S (Q J)^T);  a sweep cap ends it with a status flag;
+//  4. s_k = |row k of the rotated R|, keep s_k >= tol s_max;  g = S_t^{-1} U_t^T b;
+//  5. G = Z V_t (columns z * Q j_k), Householder QR G = Q' R', then
+//     w = Z Q' R'^{-T} g  -- the inverse of G^T G = V_t^T Z^2 V_t applied through
 //     the QR factor, as the paper does for the full-rank case (Sec. 2, Eq. QR).
+//  The pivoted QR is Drmac and Veselic's preconditioning of one-sided Jacobi (SIAM J.
+//  Matrix Anal. Appl. 29, 2008): the same SVD, in about half the sweeps.
 //  If N_i vanishes at one of its points (z_q == 0, V_t^T Z^2 V_t singular) the
 //  row uses Z = I and is flagged.  rank_out / zid_out may be null.
 #include "kernels.h"
@@ -25,10 +28,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
-// One system (row i of one component), solved by the whole CTA in the scratch slice S.
-// Returns this thread's share of the FP64 operation count: 6 r per pair check,
-// 6 (r + n) + 20 per rotation in the Jacobi phase, ~2 r t^2 + 8 r t for the QR and
-// solves.  Every row's result depends on its own data only, so the weights do not
+// One system (row i of one component), solved by the whole CTA in the scratch slice S
+// (2 n r + 2 n^2 + 2 r + 7 n doubles).  Returns this thread's share of the FP64
+// operation count: ~4 (n - k)(r - k) per pivoted-QR step, 6 n per pair check and
+// 12 n + 20 per rotation in the Jacobi phase, ~2 r t^2 + 8 r t + 4 r n t for V_t, the
+// QR of G and the solves.  Every row's result depends on its own data only, so the weights do not
 // depend on which CTA solves which row or in what order.
 __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, const double* __restrict__ table,
                                               int tc, const double* __restrict__ mom, double* __restrict__ W,
@@ -42,19 +46,25 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
     {
         const int n = rw.row_ptr[i + 1] - rw.row_ptr[i];
         const int r = (int)(rw.w_ptr[i + 1] - rw.w_ptr[i]);
-        double* At = S;                      // [n][r]
+        double* At = S;                      // [n][r]  A by rows, then the reflectors and R of A^T P = Q R
         double* G = At + (int64_t)n * r;     // [n][r]  (t columns of Z V_t, then Householder data)
         double* Jt = G + (int64_t)n * r;     // [n][n]
-        double* z = Jt + (int64_t)n * n;     // [r]
+        double* Rb = Jt + (int64_t)n * n;    // [n][n]  R by rows, rotated by the Jacobi sweeps
+        double* z = Rb + (int64_t)n * n;     // [r]
         double* v = z + r;                   // [r]
         double* b = v + r;                   // [n]
         double* sig = b + n;                 // [n]
         double* g = sig + n;                 // [n]
-        double* tau = g + n;                 // [n]
-        int* keep = (int*)(tau + n);         // [n]
+        double* tau = g + n;                 // [n]  reflectors of G
+        double* htau = tau + n;              // [n]  reflectors of A^T
+        int* keep = (int*)(htau + n);        // [n]
+        int* perm = keep + n;                // [n]  column pivots of A^T (function order)
         for (int64_t k = tid; k < (int64_t)n * r; k += bd) At[k] = 0.0;
         for (int64_t k = tid; k < (int64_t)n * n; k += bd) Jt[k] = (k / n == k % n) ? 1.0 : 0.0;
-        for (int k = tid; k < n; k += bd) b[k] = mom[rw.row_ptr[i] + k];
+        for (int k = tid; k < n; k += bd) {
+            b[k] = mom[rw.row_ptr[i] + k];
+            perm[k] = k;
+        }
         __syncthreads();
         // 1. gather
         int qoff = 0;
@@ -77,13 +87,97 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
         zero_z = __syncthreads_or(zero_z);
         if (zero_z)
             for (int q = tid; q < r; q += bd) z[q] = 1.0;
-        // 2. one-sided Jacobi: groups of JG lanes per rotation pair (8 pairs per warp);
+        // 2. Householder QR with column pivoting of A^T (r x n; its columns are the rows
+        //    of At): A^T P = Q R, the reflectors kept below R in At (At[k][k+1..r) is
+        //    reflector k, At[j][k] = R[k][j] for j >= k).  The one-sided Jacobi then runs
+        //    on the rows of the n x n factor R: pivoting grades R so that its rows are far
+        //    closer to orthogonal than those of A (about half the sweeps, each on rows of
+        //    length n instead of r), and A = (P Y) S (Q J)^T with R = J S Y^T.
+        // squared norms of the columns of A^T (the pivot choice), downdated after every
+        // step by the entry that moves into R; the pivots only steer the convergence,
+        // every choice gives the same factorisation A^T P = Q R of its own P
+        for (int j = warp; j < n; j += nwarp) {
+            double s2 = 0.0;
+            for (int x = lane; x < r; x += 32) s2 = fma(At[(int64_t)j * r + x], At[(int64_t)j * r + x], s2);
+            s2 = warp_sum(s2);
+            if (lane == 0) sig[j] = s2;
+        }
+        __syncthreads();
+        for (int k = 0; k < n; ++k) {
+            if (tid == 0) {
+                int pv = k;
+                for (int j = k + 1; j < n; ++j)
+                    if (sig[j] > sig[pv]) pv = j;
+                sh_t = pv;
+                fl += 4.0 * (double)(n - k) * (double)(r - k);
+            }
+            __syncthreads();
+            const int pv = sh_t;
+            if (pv != k) {
+                for (int x = tid; x < r; x += bd) {
+                    const double t0 = At[(int64_t)k * r + x];
+                    At[(int64_t)k * r + x] = At[(int64_t)pv * r + x];
+                    At[(int64_t)pv * r + x] = t0;
+                }
+                if (tid == 0) {
+                    const int t1 = perm[k];
+                    perm[k] = perm[pv];
+                    perm[pv] = t1;
+                    const double t2 = sig[k];
+                    sig[k] = sig[pv];
+                    sig[pv] = t2;
+                }
+            }
+            __syncthreads();
+            double* hk = At + (int64_t)k * r;
+            if (warp == 0) {
+                double xn2 = 0.0;
+                for (int x = k + 1 + lane; x < r; x += 32) xn2 = fma(hk[x], hk[x], xn2);
+                xn2 = warp_sum(xn2);
+                const double alpha = hk[k];
+                double tk = 0.0, beta = alpha, scale = 0.0;
+                if (xn2 > 0.0) {
+                    beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+                    tk = (beta - alpha) / beta;
+                    scale = 1.0 / (alpha - beta);
+                }
+                __syncwarp();
+                if (xn2 > 0.0)
+                    for (int x = k + 1 + lane; x < r; x += 32) hk[x] *= scale;
+                if (lane == 0) {
+                    hk[k] = beta;
+                    htau[k] = tk;
+                }
+            }
+            __syncthreads();
+            const double tk = htau[k];
+            for (int j = k + 1 + warp; j < n; j += nwarp) {
+                double* aj = At + (int64_t)j * r;
+                double d = 0.0;
+                for (int x = k + 1 + lane; x < r; x += 32) d = fma(hk[x], aj[x], d);
+                d = warp_sum(d);
+                d = tk * (aj[k] + d);
+                for (int x = k + 1 + lane; x < r; x += 32) aj[x] -= d * hk[x];
+                __syncwarp();
+                if (lane == 0) {
+                    aj[k] -= d;
+                    sig[j] = fmax(sig[j] - aj[k] * aj[k], 0.0);
+                }
+            }
+            __syncthreads();
+        }
+        for (int64_t k = tid; k < (int64_t)n * n; k += bd) {
+            const int rr = (int)(k / n), cc = (int)(k - (int64_t)rr * n);
+            Rb[k] = cc >= rr ? At[(int64_t)cc * r + rr] : 0.0;
+        }
+        __syncthreads();
+        // 3. one-sided Jacobi on the rows of R: groups of JG lanes per rotation pair (8 pairs per warp);
         //    zeta = (be - al) / (2 ga) in FP64, the tangent from it in FP32 (hypotf; t =
         //    1/(2 zeta) beyond 1e30), cos/sin in FP64 from that tangent (c = (1 + t^2)^-1/2
         //    by two Newton steps from an FP32 seed, s = c t): every applied rotation is
         //    orthogonal to FP64 rounding; the FP32 angle only costs convergence speed.
         const int np = (n + 1) & ~1;
-        const double tolJ = fmax(2.220446049250313e-16 * sqrt((double)r), 1e-15);
+        const double tolJ = fmax(2.220446049250313e-16 * sqrt((double)n), 1e-15);
         const double tol2 = tolJ * tolJ;
         constexpr int JG = 4;
         const int gl = lane & (JG - 1), grp = lane / JG;
@@ -105,11 +199,11 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
                         q = (rnd - k + (np - 1)) % (np - 1);
                     }
                     const bool valid = k < npairs && p < n && q < n;
-                    double* ap = At + (int64_t)(valid ? p : 0) * r;
-                    double* aq = At + (int64_t)(valid ? q : 0) * r;
+                    double* ap = Rb + (int64_t)(valid ? p : 0) * n;
+                    double* aq = Rb + (int64_t)(valid ? q : 0) * n;
                     double al = 0.0, be = 0.0, ga = 0.0;
                     if (valid)
-                        for (int x = gl; x < r; x += JG) {
+                        for (int x = gl; x < n; x += JG) {
                             const double u = ap[x], w = aq[x];
                             al = fma(u, u, al);
                             be = fma(w, w, be);
@@ -137,7 +231,7 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
                         c = c * fma(-0.5 * qq, c * c, 1.5);
                         c = c * fma(-0.5 * qq, c * c, 1.5);
                         const double sn = c * t;
-                        for (int x = gl; x < r; x += JG) {
+                        for (int x = gl; x < n; x += JG) {
                             const double u = ap[x], w = aq[x];
                             ap[x] = fma(c, u, -sn * w);
                             aq[x] = fma(sn, u, c * w);
@@ -157,11 +251,12 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
             converged = !__syncthreads_or(rotated);
         }
         if (!converged && tid == 0) atomicOr(status, ST_NOT_CONVERGED);
-        fl += 6.0 * r * nchk + (6.0 * (r + n) + 20.0) * nrot;
-        // 3. singular values, kept set, g = S_t^-1 U_t^T b
+        fl += 6.0 * n * nchk + (12.0 * n + 20.0) * nrot;
+        // 4. singular values, kept set, g = S_t^-1 U_t^T b with U = P Y (row a of the
+        //    rotated R is s_a y_a^T, and (P y)[perm[j]] = y[j])
         for (int a = warp; a < n; a += nwarp) {
             double s2 = 0.0;
-            for (int x = lane; x < r; x += 32) s2 += At[(int64_t)a * r + x] * At[(int64_t)a * r + x];
+            for (int x = lane; x < n; x += 32) s2 += Rb[(int64_t)a * n + x] * Rb[(int64_t)a * n + x];
             s2 = warp_sum(s2);
             if (lane == 0) sig[a] = sqrt(s2);
         }
@@ -177,19 +272,33 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
         }
         __syncthreads();
         const int t = sh_t;
-        if (tid == 0) fl += 2.0 * r * (double)t * t + 8.0 * r * t;
+        if (tid == 0) fl += 2.0 * r * (double)t * t + 8.0 * r * t + 4.0 * (double)r * n * t;
         for (int k = warp; k < t; k += nwarp) {
             const int a = keep[k];
             double d = 0.0;
-            for (int x = lane; x < n; x += 32) d += Jt[(int64_t)a * n + x] * b[x];
+            for (int x = lane; x < n; x += 32) d += Rb[(int64_t)a * n + x] * b[perm[x]];
             d = warp_sum(d);
-            if (lane == 0) g[k] = d / sig[a];
+            if (lane == 0) g[k] = d / (sig[a] * sig[a]);
         }
-        // 4. G = Z V_t
-        for (int64_t k = tid; k < (int64_t)t * r; k += bd) {
-            const int c = (int)(k / r), q = (int)(k - (int64_t)c * r);
+        // 5. G = Z V_t with V = Q J: column c = Z Q [j_a; 0] (j_a = row a of Jt), the
+        //    reflectors of A^T applied last to first
+        for (int c = warp; c < t; c += nwarp) {
             const int a = keep[c];
-            G[k] = z[q] * At[(int64_t)a * r + q] / sig[a];
+            double* gc = G + (int64_t)c * r;
+            for (int x = lane; x < r; x += 32) gc[x] = x < n ? Jt[(int64_t)a * n + x] : 0.0;
+            __syncwarp();
+            for (int kk = n - 1; kk >= 0; --kk) {
+                const double* hk = At + (int64_t)kk * r;
+                double d = 0.0;
+                for (int x = kk + 1 + lane; x < r; x += 32) d = fma(hk[x], gc[x], d);
+                d = warp_sum(d);
+                d = htau[kk] * (gc[kk] + d);
+                for (int x = kk + 1 + lane; x < r; x += 32) gc[x] -= d * hk[x];
+                __syncwarp();
+                if (lane == 0) gc[kk] -= d;
+                __syncwarp();
+            }
+            for (int x = lane; x < r; x += 32) gc[x] *= z[x];
         }
         __syncthreads();
         // Householder QR of G (r x t, column c stored at G + c*r)
@@ -287,7 +396,7 @@ __device__ __forceinline__ void add_flops(double fl, double* flops) {
     }
 }
 
-__global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* __restrict__ table, int tc,
+__global__ void __launch_bounds__(128, 6) k_tsvd(Elems el, Rows rw, const double* __restrict__ table, int tc,
                                               const double* __restrict__ mom, double* __restrict__ W, int nwc,
                                               int wc, double tol, int max_sweeps, double* __restrict__ scratch,
                                               int64_t per_cta, int32_t* __restrict__ rank_out,
@@ -304,7 +413,7 @@ __global__ void __launch_bounds__(128) k_tsvd(Elems el, Rows rw, const double* _
 // Every system of several rules and components in one persistent launch: CTAs take
 // jobs {system set, row} from a queue ordered by estimated cost (largest first), so
 // that the uneven systems near extraordinary points spread over the grid.
-__global__ void __launch_bounds__(128) k_tsvd_batch(const TsvdSet* __restrict__ sets, const int2* __restrict__ jobs,
+__global__ void __launch_bounds__(128, 6) k_tsvd_batch(const TsvdSet* __restrict__ sets, const int2* __restrict__ jobs,
                                                     int64_t n_jobs, unsigned long long* __restrict__ next,
                                                     double tol, int max_sweeps, double* __restrict__ scratch,
                                                     int64_t per_cta, double* __restrict__ flops) {

@@ -106,6 +106,12 @@ cudaError_t launch_split_rows(const double* W, const int32_t* dst, float2* W2e, 
 //   writes W[(w_ptr[i] + q) * nwc + wc].  scratch holds `per_cta` doubles per CTA.
 //   Per-row rank written to rank[i], Z = I fallback flagged in zid[i]; the FP64
 //   operation count is added to *flops (may be null).
+// Scratch of one truncated-SVD system (doubles) for rows of at most max_n functions and
+// max_r points, and the CTAs per SM the solver kernels are built for.
+inline int64_t tsvd_scratch_doubles(int64_t max_n, int64_t max_r) {
+    return 2 * max_n * max_r + 2 * max_n * max_n + 2 * max_r + 7 * max_n + 8;
+}
+constexpr int TSVD_CTAS_PER_SM = 6;
 cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, int tc,
                         const double* mom, double* W, int nwc, int wc, double tol, int max_sweeps,
                         double* scratch, int64_t per_cta, int n_cta, int32_t* rank, uint8_t* zid,

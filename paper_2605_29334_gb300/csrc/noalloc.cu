@@ -6,7 +6,7 @@
 // for instance a host application that has handed all free device memory to
 // its own pool allocator, or a time-critical loop in which the implicit device
 // synchronisation of cudaMalloc/cudaFree is not acceptable.  The weight solve
-// of wq_rule_build needs a per-CTA workspace of 2 n r + n^2 + 2 r + 5 n doubles
+// of wq_rule_build needs a per-CTA workspace of 2 n r + 2 n^2 + 2 r + 7 n doubles
 // (n = #S_i, r = #points of N_i); here it comes from the fixed array below.
 //
 // The array g_noalloc_scratch is a file-scope __device__ object: every device
@@ -88,7 +88,7 @@ extern "C" wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, 
     double* scratch = g_scratch_ptr[dev];
     unsigned* status = g_status_ptr[dev];
     const int64_t mn = rule->max_n_i, mr = rule->max_r;
-    const int64_t per_cta = 2 * mn * mr + mn * mn + 2 * mr + 5 * mn + 8;
+    const int64_t per_cta = wqd::tsvd_scratch_doubles(mn, mr);
     if (per_cta > kScratchDoubles)
         return set_err(ctx, WQ_ERR_ARG,
                        "weight system too large for the fixed scratch: needs " + std::to_string(per_cta * 8) +
@@ -96,7 +96,7 @@ extern "C" wq_status wq_rule_weights_noalloc(const wq_rule* rule, int32_t comp, 
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     int64_t n_cta = kScratchDoubles / per_cta;
-    n_cta = std::min<int64_t>(n_cta, (int64_t)std::max(n_sm, 1) * 8);
+    n_cta = std::min<int64_t>(n_cta, (int64_t)std::max(n_sm, 1) * wqd::TSVD_CTAS_PER_SM);
     n_cta = std::min<int64_t>(n_cta, std::max<int64_t>(rule->n, 1));
     e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
