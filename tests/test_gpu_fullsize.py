@@ -162,3 +162,46 @@ def test_fullsize_heat_tangent(W, record_property):
     dt = 1e-2
     _run(W, mesh, ["N", "x", "y"], W.OP_HEAT_S, [("N", 1.0 / dt), ("x", None), ("y", None)], kap, 1.0 / dt,
          [W.PREC_F64, W.PREC_F32], seed=14, record=record_property, variants=True)
+
+
+def test_fullsize_every_row_properties(W, record_property):
+    """Every row of the benchmark workload (28,619 rows, 1.09 M entries), against what
+    the method fixes at any size (Sec. 4.1, partition of unity and linear reproduction
+    of the spline space):
+      * stiffness with the log-normal kappa: sum_j K_ij = 0 (sum_j grad N_j = 0 at every
+        point, whatever the weights and the coefficient);
+      * mass with c = 1: sum_j M_ij = sum_q w^N_iq (sum_j N_j = 1);
+      * stiffness with c = 1 applied to the control points' x-coordinates:
+        sum_j K_ij x_j = sum_q w^x_iq (x = sum_j x_j N_j, so d_x x = 1, d_y x = 0).
+    FP64 within 1e-11 of each row's scale, the float modes within 1e-6."""
+    import torch
+    mesh = meshes.rotated(nx=8, ny=5, n_ep=12, levels=4, seed=2001)
+    field = meshes.LogNormalField(2101, mesh["xyz"].min(0), mesh["xyz"].max(0), nk=16, sigma=0.5)
+    ctx = W.Context(0)
+    b = W.Basis(ctx, mesh)
+    r = W.Rule(b, comps=[W.COMP_N, W.COMP_X, W.COMP_Y])
+    rp, col = (t.cpu().numpy().astype(np.int64) for t in r.pattern())
+    starts = rp[:-1]
+    kap = torch.tensor(field(r.points().cpu().numpy()), device="cuda")
+    one = torch.ones(r.Q, dtype=torch.float64, device="cuda")
+    xc = b.ctrl()[:, 0]
+    wN, wptr = (t.cpu().numpy() for t in r.weights(W.COMP_N))
+    wX, _ = (t.cpu().numpy() for t in r.weights(W.COMP_X))
+    sumN = np.add.reduceat(wN, wptr[:-1].astype(np.int64))
+    sumX = np.add.reduceat(wX, wptr[:-1].astype(np.int64))
+    worst = {}
+    for name, prec, bar in (("f64", W.PREC_F64, 1e-11), ("f32", W.PREC_F32, 1e-6), ("tc", W.PREC_TC, 1e-6)):
+        K = r.assemble(W.OP_STIFF, kap, prec=prec).cpu().numpy().astype(np.float64)
+        rs = np.add.reduceat(K, starts)
+        sc = np.add.reduceat(np.abs(K), starts)
+        e1 = float(np.max(np.abs(rs) / sc))
+        M = r.assemble(W.OP_MASS, one, prec=prec).cpu().numpy().astype(np.float64)
+        e2 = float(np.max(np.abs(np.add.reduceat(M, starts) - sumN) / np.add.reduceat(np.abs(M), starts)))
+        K1 = r.assemble(W.OP_STIFF, one, prec=prec).cpu().numpy().astype(np.float64)
+        kx = K1 * xc[col]
+        e3 = float(np.max(np.abs(np.add.reduceat(kx, starts) - sumX) / np.add.reduceat(np.abs(kx), starts)))
+        worst[name] = (e1, e2, e3)
+        record_property("every_row_%s" % name, [e1, e2, e3])
+        assert max(e1, e2, e3) < bar, (name, e1, e2, e3)
+    print("every row (row sum, mass partition of unity, x reproduction):",
+          {k: ["%.1e" % v for v in vs] for k, vs in worst.items()})
