@@ -9,7 +9,8 @@
 //  2. Householder QR with column pivoting of A^T (r_i x n_i): A^T P = Q R;
 //  3. one-sided (Hestenes) Jacobi on the n_i rows of R (length n_i), round-robin
 //     pairs, four lanes per pair, accumulating the rotations in Jt (J^T R = S Y^T,
-//     so A = (P Y) S (Q J)^T);  a sweep cap ends it with a status flag;
+//     so A = (P Y) S (Q J)^T): FP32 sweeps on a float copy first, then FP64 sweeps
+//     from the re-orthogonalised FP32 rotations;  a sweep cap ends it with a status flag;
 //  4. s_k = |row k of the rotated R|, keep s_k >= tol s_max;  g = S_t^{-1} U_t^T b;
 //  5. G = Z V_t (columns z * Q j_k), Householder QR G = Q' R', then
 //     w = Z Q' R'^{-T} g  -- the inverse of G^T G = V_t^T Z^2 V_t applied through
@@ -28,10 +29,109 @@ __device__ __forceinline__ double warp_sum(double v) {
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// One-sided Jacobi on the n rows (length n) of A, rotations accumulated in the rows of J,
+// by the whole CTA: groups of JG lanes per rotation pair (8 pairs per warp), round-robin
+// pairs, at most max_sweeps sweeps; returns whether a sweep found nothing to rotate.
+// FP64: zeta = (be - al) / (2 ga) in FP64, the tangent from it in FP32 (hypotf; t =
+// 1/(2 zeta) beyond 1e30), cos/sin in FP64 from that tangent (c = (1 + t^2)^-1/2 by two
+// Newton steps from an FP32 seed, s = c t): every applied rotation is orthogonal to FP64
+// rounding, the FP32 angle only costs convergence speed.  FP32: all in FP32.
+template <typename T>
+__device__ __forceinline__ bool jacobi_rows(T* __restrict__ A, T* __restrict__ J, int n, int max_sweeps, int& nchk,
+                                            int& nrot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    constexpr bool F64 = sizeof(T) == 8;
+    const int np = (n + 1) & ~1;
+    const T tolJ = F64 ? (T)fmax(2.220446049250313e-16 * sqrt((double)n), 1e-15)
+                       : (T)fmaxf(1.1920929e-7f * sqrtf((float)n), 1e-7f);
+    const T tol2 = tolJ * tolJ;
+    constexpr int JG = 4;
+    const int gl = lane & (JG - 1), grp = lane / JG;
+    const int per_pass = nwarp * (32 / JG);
+    const int npairs = np / 2;
+    int converged = (n < 2);
+    for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+        int rotated = 0;
+        for (int rnd = 0; rnd < np - 1; ++rnd) {
+            for (int kb = 0; kb < npairs; kb += per_pass) {
+                const int k = kb + warp * (32 / JG) + grp;
+                int p = 0, q = 0;
+                if (k == 0) {
+                    p = rnd;
+                    q = np - 1;
+                } else {
+                    p = (rnd + k) % (np - 1);
+                    q = (rnd - k + (np - 1)) % (np - 1);
+                }
+                const bool valid = k < npairs && p < n && q < n;
+                T* ap = A + (int64_t)(valid ? p : 0) * n;
+                T* aq = A + (int64_t)(valid ? q : 0) * n;
+                T al = 0, be = 0, ga = 0;
+                if (valid)
+                    for (int x = gl; x < n; x += JG) {
+                        const T u = ap[x], w = aq[x];
+                        al = fma(u, u, al);
+                        be = fma(w, w, be);
+                        ga = fma(u, w, ga);
+                    }
+#pragma unroll
+                for (int o = JG / 2; o >= 1; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                nchk += valid && gl == 0;
+                if (valid && al > (T)0 && be > (T)0 && ga * ga > tol2 * (al * be)) {
+                    nrot += gl == 0;
+                    T c, sn;
+                    if (F64) {
+                        const double z = ((double)be - (double)al) / (2.0 * (double)ga);
+                        double t;
+                        if (fabs(z) < 1e30) {
+                            const float zf = (float)z;
+                            t = (double)(copysignf(1.0f, zf) / (fabsf(zf) + hypotf(1.0f, zf)));
+                        } else {
+                            t = 0.5 / z;
+                        }
+                        const double qq = fma(t, t, 1.0);
+                        double cd = (double)rsqrtf((float)qq);
+                        cd = cd * fma(-0.5 * qq, cd * cd, 1.5);
+                        cd = cd * fma(-0.5 * qq, cd * cd, 1.5);
+                        c = (T)cd;
+                        sn = (T)(cd * t);
+                    } else {
+                        const float z = ((float)be - (float)al) / (2.0f * (float)ga);
+                        const float t = fabsf(z) < 1e18f ? copysignf(1.0f, z) / (fabsf(z) + hypotf(1.0f, z)) : 0.5f / z;
+                        const float cf = rsqrtf(fmaf(t, t, 1.0f));
+                        c = (T)cf;
+                        sn = (T)(cf * t);
+                    }
+                    for (int x = gl; x < n; x += JG) {
+                        const T u = ap[x], w = aq[x];
+                        ap[x] = fma(c, u, -sn * w);
+                        aq[x] = fma(sn, u, c * w);
+                    }
+                    T* jp = J + (int64_t)p * n;
+                    T* jq = J + (int64_t)q * n;
+                    for (int x = gl; x < n; x += JG) {
+                        const T u = jp[x], w = jq[x];
+                        jp[x] = fma(c, u, -sn * w);
+                        jq[x] = fma(sn, u, c * w);
+                    }
+                    rotated = 1;
+                }
+            }
+            __syncthreads();
+        }
+        converged = !__syncthreads_or(rotated);
+    }
+    return converged != 0;
+}
+
 // One system (row i of one component), solved by the whole CTA in the scratch slice S
-// (2 n r + 2 n^2 + 2 r + 7 n doubles).  Returns this thread's share of the FP64
-// operation count: ~4 (n - k)(r - k) per pivoted-QR step, 6 n per pair check and
-// 12 n + 20 per rotation in the Jacobi phase, ~2 r t^2 + 8 r t + 4 r n t for V_t, the
+// (2 n r + 4 n^2 + 2 r + 7 n doubles).  Returns this thread's share of the FP64
+// operation count: ~4 (n - k)(r - k) per pivoted-QR step, 10 n^3 for the
+// re-orthogonalisation, 6 n per pair check and 12 n + 20 per rotation in the FP64 sweeps, ~2 r t^2 + 8 r t + 4 r n t for V_t, the
 // QR of G and the solves.  Every row's result depends on its own data only, so the weights do not
 // depend on which CTA solves which row or in what order.
 __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, const double* __restrict__ table,
@@ -59,6 +159,8 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
         double* htau = tau + n;              // [n]  reflectors of A^T
         int* keep = (int*)(htau + n);        // [n]
         int* perm = keep + n;                // [n]  column pivots of A^T (function order)
+        double* Tm = htau + 2 * n;           // [n][n]  products of the re-orthogonalisation, followed
+                                             //         by the float copies of R and J ([n][n] each)
         for (int64_t k = tid; k < (int64_t)n * r; k += bd) At[k] = 0.0;
         for (int64_t k = tid; k < (int64_t)n * n; k += bd) Jt[k] = (k / n == k % n) ? 1.0 : 0.0;
         for (int k = tid; k < n; k += bd) {
@@ -171,85 +273,56 @@ __device__ __forceinline__ double tsvd_system(const Elems& el, const Rows& rw, c
             Rb[k] = cc >= rr ? At[(int64_t)cc * r + rr] : 0.0;
         }
         __syncthreads();
-        // 3. one-sided Jacobi on the rows of R: groups of JG lanes per rotation pair (8 pairs per warp);
-        //    zeta = (be - al) / (2 ga) in FP64, the tangent from it in FP32 (hypotf; t =
-        //    1/(2 zeta) beyond 1e30), cos/sin in FP64 from that tangent (c = (1 + t^2)^-1/2
-        //    by two Newton steps from an FP32 seed, s = c t): every applied rotation is
-        //    orthogonal to FP64 rounding; the FP32 angle only costs convergence speed.
-        const int np = (n + 1) & ~1;
-        const double tolJ = fmax(2.220446049250313e-16 * sqrt((double)n), 1e-15);
-        const double tol2 = tolJ * tolJ;
-        constexpr int JG = 4;
-        const int gl = lane & (JG - 1), grp = lane / JG;
-        const int per_pass = nwarp * (32 / JG);
-        const int npairs = np / 2;
-        int converged = (n < 2);
-        int nchk = 0, nrot = 0;   // pair checks and rotations of this lane group
-        for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
-            int rotated = 0;
-            for (int rnd = 0; rnd < np - 1; ++rnd) {
-                for (int kb = 0; kb < npairs; kb += per_pass) {
-                    const int k = kb + warp * (32 / JG) + grp;
-                    int p = 0, q = 0;
-                    if (k == 0) {
-                        p = rnd;
-                        q = np - 1;
-                    } else {
-                        p = (rnd + k) % (np - 1);
-                        q = (rnd - k + (np - 1)) % (np - 1);
-                    }
-                    const bool valid = k < npairs && p < n && q < n;
-                    double* ap = Rb + (int64_t)(valid ? p : 0) * n;
-                    double* aq = Rb + (int64_t)(valid ? q : 0) * n;
-                    double al = 0.0, be = 0.0, ga = 0.0;
-                    if (valid)
-                        for (int x = gl; x < n; x += JG) {
-                            const double u = ap[x], w = aq[x];
-                            al = fma(u, u, al);
-                            be = fma(w, w, be);
-                            ga = fma(u, w, ga);
-                        }
-#pragma unroll
-                    for (int o = JG / 2; o >= 1; o >>= 1) {
-                        al += __shfl_xor_sync(0xffffffffu, al, o);
-                        be += __shfl_xor_sync(0xffffffffu, be, o);
-                        ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                    }
-                    nchk += valid && gl == 0;
-                    if (valid && al > 0.0 && be > 0.0 && ga * ga > tol2 * (al * be)) {
-                        nrot += gl == 0;
-                        const double z = (be - al) / (2.0 * ga);
-                        double t;
-                        if (fabs(z) < 1e30) {
-                            const float zf = (float)z;
-                            t = (double)(copysignf(1.0f, zf) / (fabsf(zf) + hypotf(1.0f, zf)));
-                        } else {
-                            t = 0.5 / z;
-                        }
-                        const double qq = fma(t, t, 1.0);
-                        double c = (double)rsqrtf((float)qq);
-                        c = c * fma(-0.5 * qq, c * c, 1.5);
-                        c = c * fma(-0.5 * qq, c * c, 1.5);
-                        const double sn = c * t;
-                        for (int x = gl; x < n; x += JG) {
-                            const double u = ap[x], w = aq[x];
-                            ap[x] = fma(c, u, -sn * w);
-                            aq[x] = fma(sn, u, c * w);
-                        }
-                        double* jp = Jt + (int64_t)p * n;
-                        double* jq = Jt + (int64_t)q * n;
-                        for (int x = gl; x < n; x += JG) {
-                            const double u = jp[x], w = jq[x];
-                            jp[x] = fma(c, u, -sn * w);
-                            jq[x] = fma(sn, u, c * w);
-                        }
-                        rotated = 1;
-                    }
-                }
-                __syncthreads();
-            }
-            converged = !__syncthreads_or(rotated);
+        // 3. one-sided Jacobi on the rows of R, first in FP32 on a float copy (its rotations
+        //    accumulated in Jf), then in FP64 from Jt = the polar factor of Jf (two
+        //    Newton-Schulz steps, Higham, "Functions of Matrices", 2008, Sec. 8.3) and
+        //    R <- Jt R: the FP32 sweeps do most of the rotations at the FP32 pipe's rate,
+        //    the FP64 sweeps (about half as many as from R itself) take the rows to FP64
+        //    orthogonality, and every applied transformation stays orthogonal to FP64
+        //    rounding, so the result is the FP64 SVD of R.
+        float* Rf = reinterpret_cast<float*>(Tm + (int64_t)n * n);   // [n][n]
+        float* Jf = Rf + (int64_t)n * n;                              // [n][n]
+        for (int64_t k = tid; k < (int64_t)n * n; k += bd) {
+            Rf[k] = (float)Rb[k];
+            Jf[k] = (k / n == k % n) ? 1.0f : 0.0f;
         }
+        __syncthreads();
+        int nchk = 0, nrot = 0;   // FP64 pair checks and rotations of this lane group
+        {
+            int c32 = 0, r32 = 0;
+            jacobi_rows<float>(Rf, Jf, n, max_sweeps, c32, r32);
+        }
+        for (int64_t k = tid; k < (int64_t)n * n; k += bd) Jt[k] = (double)Jf[k];
+        __syncthreads();
+        for (int it = 0; it < 2; ++it) {            // Jt <- (3 I - Jt Jt^T) Jt / 2
+            for (int64_t k = tid; k < (int64_t)n * n; k += bd) {
+                const int a = (int)(k / n), c = (int)(k - (int64_t)a * n);
+                double d = 0.0;
+                for (int x = 0; x < n; ++x) d = fma(Jt[(int64_t)a * n + x], Jt[(int64_t)c * n + x], d);
+                G[k] = d;
+            }
+            __syncthreads();
+            for (int64_t k = tid; k < (int64_t)n * n; k += bd) {
+                const int a = (int)(k / n), c = (int)(k - (int64_t)a * n);
+                double d = 0.0;
+                for (int x = 0; x < n; ++x) d = fma(G[(int64_t)a * n + x], Jt[(int64_t)x * n + c], d);
+                Tm[k] = 0.5 * fma(3.0, Jt[k], -d);
+            }
+            __syncthreads();
+            for (int64_t k = tid; k < (int64_t)n * n; k += bd) Jt[k] = Tm[k];
+            __syncthreads();
+        }
+        for (int64_t k = tid; k < (int64_t)n * n; k += bd) {   // R <- Jt R
+            const int a = (int)(k / n), c = (int)(k - (int64_t)a * n);
+            double d = 0.0;
+            for (int x = 0; x <= c; ++x) d = fma(Jt[(int64_t)a * n + x], Rb[(int64_t)x * n + c], d);   // R upper
+            Tm[k] = d;
+        }
+        __syncthreads();
+        for (int64_t k = tid; k < (int64_t)n * n; k += bd) Rb[k] = Tm[k];
+        __syncthreads();
+        if (tid == 0) fl += 10.0 * (double)n * n * n;
+        const bool converged = jacobi_rows<double>(Rb, Jt, n, max_sweeps, nchk, nrot);
         if (!converged && tid == 0) atomicOr(status, ST_NOT_CONVERGED);
         fl += 6.0 * n * nchk + (12.0 * n + 20.0) * nrot;
         // 4. singular values, kept set, g = S_t^-1 U_t^T b with U = P Y (row a of the

@@ -109,7 +109,7 @@ cudaError_t launch_split_rows(const double* W, const int32_t* dst, float2* W2e, 
 // Scratch of one truncated-SVD system (doubles) for rows of at most max_n functions and
 // max_r points, and the CTAs per SM the solver kernels are built for.
 inline int64_t tsvd_scratch_doubles(int64_t max_n, int64_t max_r) {
-    return 2 * max_n * max_r + 2 * max_n * max_n + 2 * max_r + 7 * max_n + 8;
+    return 2 * max_n * max_r + 4 * max_n * max_n + 2 * max_r + 7 * max_n + 8;
 }
 constexpr int TSVD_CTAS_PER_SM = 6;
 cudaError_t launch_tsvd(const Elems& el, const Rows& rw, const double* table, int tc,

@@ -6,7 +6,7 @@
 // for instance a host application that has handed all free device memory to
 // its own pool allocator, or a time-critical loop in which the implicit device
 // synchronisation of cudaMalloc/cudaFree is not acceptable.  The weight solve
-// of wq_rule_build needs a per-CTA workspace of 2 n r + 2 n^2 + 2 r + 7 n doubles
+// of wq_rule_build needs a per-CTA workspace of 2 n r + 4 n^2 + 2 r + 7 n doubles
 // (n = #S_i, r = #points of N_i); here it comes from the fixed array below.
 //
 // The array g_noalloc_scratch is a file-scope __device__ object: every device
