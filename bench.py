@@ -310,11 +310,11 @@ def bench_ours(args, rank, world):
     }
     res["refine"] = refine_measure(wq, basis, mesh, flush, max(args.steps // 20, 20), args.warmup, hbm,
                                    n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:   # CPU baselines: rank 0 at N = 1 only
         a64 = rule.assemble(wq.OP_STIFF, coef, prec=wq.PREC_F64).cpu().numpy()
         g64 = rule.gq_assemble(wq.OP_STIFF, coef_g, prec=wq.PREC_F64).cpu().numpy()
         res["cpu_ref"] = cpu_ref_measure(rule, basis, coef.cpu().numpy(), coef_g.cpu().numpy(), a64, g64)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(args)
     if not args.no_configs and world == 1:
         res["other_configs"] = other_configs(ctx, flush, max(args.steps // 20, 20), args.warmup, hbm)
