@@ -59,6 +59,14 @@ def test_plan_matches_oracle(wq, name):
     assert fc.shape == (r.info.n_coarse_face_xyz, 3)
     if len(fc):
         assert np.max(np.abs(fc - ob.raw_xyz[ob.topo.V:])) <= 1e-15 * scale
+    # the device's term lists of the fine face-based points: 16 points per coarse enriched
+    # face, an even number of (padded) terms each, no more non-zero terms than the dense
+    # coefficients of the 16 points would give with the split folded in (m x 16 per face)
+    I = r.info
+    assert I.n_face_xyz == 16 * I.n_face_jobs
+    assert I.n_face_ell % 32 == 0 and I.n_face_ell >= I.n_face_terms
+    assert (I.n_face_jobs == 0) == (I.n_face_terms == 0)
+    assert I.n_face_terms <= 16 * I.n_face_fns
 
 
 def test_refined_mesh_builds_and_checks_face_points(wq):
